@@ -1,0 +1,284 @@
+"""Pins for the oracle's VEGAS iteration, combination and grid refinement.
+
+Section 2.1: iterations of event sets, all events combined, the grid optimised
+serially after each iteration.  Section 2.2: results independent of the
+number of threads (made bit-exact here).  The refinement steps follow
+Lepage's VEGAS, which the paper cites.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import refs
+from paper_1503_06182_gb300.workloads import DY_PARAMS, EE3J_PARAMS, GAUSS_PARAMS
+
+
+# ---------------------------------------------------------------- combination
+def test_combine_hand_values(oracle_mod):
+    I, e, c = oracle_mod.combine([1.0, 2.0], [1.0, 1.0])
+    assert I == 1.5 and abs(e - 1 / math.sqrt(2)) < 1e-16 and abs(c - 0.5) < 1e-16
+    I, e, c = oracle_mod.combine([1.0, 4.0], [1.0, 2.0])
+    # weights 1 and 1/4: mean = (1 + 1) / 1.25 = 1.6; err = 1/sqrt(1.25)
+    assert abs(I - 1.6) < 1e-15 and abs(e - 1 / math.sqrt(1.25)) < 1e-15
+    assert abs(c - ((1 - 1.6) ** 2 + (4 - 1.6) ** 2 / 4)) < 1e-14
+    I, e, c = oracle_mod.combine([3.0], [0.5])
+    assert (I, e, c) == (3.0, 0.5, 0.0)
+    # zero-variance iterations: plain mean of those, error 0
+    I, e, c = oracle_mod.combine([2.0, 5.0, 4.0], [0.0, 1.0, 0.0])
+    assert (I, e, c) == (3.0, 0.0, 0.0)
+
+
+# ------------------------------------------------------------------ refinement
+def _step_mass(edges_old, r, a, b):
+    """Integral over [a, b] of the density that puts r_i uniformly on old bin i."""
+    tot = 0.0
+    for i in range(len(r)):
+        lo, hi = max(a, edges_old[i]), min(b, edges_old[i + 1])
+        if hi > lo:
+            tot += r[i] * (hi - lo) / (edges_old[i + 1] - edges_old[i])
+    return tot
+
+
+def test_refine_uniform_sums_keep_any_grid(oracle_mod):
+    rng = np.random.default_rng(1)
+    for nbins in (2, 3, 10, 64):
+        e = np.concatenate([[0.0], np.sort(rng.uniform(0, 1, nbins - 1)), [1.0]])[None, :]
+        out = oracle_mod.refine(np.full((1, nbins), 7.25), e)
+        assert np.max(np.abs(out - e)) < 1e-14
+
+
+def test_refine_zero_sums_and_alpha_zero_leave_grid(oracle_mod):
+    rng = np.random.default_rng(2)
+    e = np.concatenate([[0.0], np.sort(rng.uniform(0, 1, 9)), [1.0]])[None, :]
+    assert np.array_equal(oracle_mod.refine(np.zeros((1, 10)), e), e)
+    d = rng.uniform(0.1, 5, (1, 10))
+    assert np.max(np.abs(oracle_mod.refine(d, e, alpha=0.0) - e)) < 1e-14
+
+
+def test_refine_scale_invariant_and_monotone(oracle_mod):
+    rng = np.random.default_rng(4)
+    d = rng.exponential(1.0, (3, 40)) ** 3
+    d[1, 10:20] = 0.0
+    e = oracle_mod.uniform_edges(3, 40)
+    a = oracle_mod.refine(d, e)
+    b = oracle_mod.refine(d * 1024.0, e)
+    assert np.array_equal(a, b)
+    assert np.all(a[:, 0] == 0.0) and np.all(a[:, -1] == 1.0)
+    assert np.all(np.diff(a, axis=1) > 0)
+
+
+def test_refine_equal_share_property(oracle_mod):
+    """Each new bin carries exactly 1/N of the compressed, smoothed mass.  The
+    smoothing and compression are the definitions of the step; the test checks
+    the redistribution (the interpolation) by integrating the step density."""
+    rng = np.random.default_rng(5)
+    N, alpha = 25, 1.5
+    d = rng.gamma(0.5, 1.0, N)
+    d[3] = 0.0
+    d[4] = 0.0
+    d[5] = 0.0
+    e = np.concatenate([[0.0], np.sort(rng.uniform(0, 1, N - 1)), [1.0]])
+    new = oracle_mod.refine(d[None, :], e[None, :], alpha)[0]
+    sm = np.empty(N)
+    sm[0] = (d[0] + d[1]) / 2
+    sm[-1] = (d[-2] + d[-1]) / 2
+    sm[1:-1] = (d[:-2] + d[1:-1] + d[2:]) / 3
+    rho = sm / sm.sum()
+    r = np.where(rho > 0, ((1 - rho) / -np.log(np.where(rho > 0, rho, 0.5))) ** alpha, 0.0)
+    share = r.sum() / N
+    for j in range(N):
+        m = _step_mass(e, r, new[j], new[j + 1])
+        assert abs(m - share) < 1e-12 * r.sum()
+
+
+def test_refine_concentrates_bins_on_peak(oracle_mod):
+    d = np.zeros((1, 20))
+    d[0, 9] = 1.0
+    d[0, 10] = 1.0
+    new = oracle_mod.refine(d, oracle_mod.uniform_edges(1, 20))[0]
+    inside = np.sum((new > 0.39) & (new < 0.61))
+    assert inside >= 15  # almost all edges move into the smoothed peak
+
+
+# ----------------------------------------------------------- VEGAS estimates
+def _two_stage(oracle_mod, ndim, nbins, iid, params, ncall, warm, prod, seed):
+    r = oracle_mod.iterate(ndim, nbins, seed, ncall // 4, warm, iid, params)
+    return oracle_mod.iterate(ndim, nbins, seed, ncall, prod, iid, params,
+                              edges=r.edges, iteration=r.iteration)
+
+
+def test_gauss_pulls_over_seeds(oracle_mod):
+    """20 seeds of the d=4 Gaussian: pulls against the closed form ~ N(0,1)."""
+    exact = refs.gauss_exact(4, GAUSS_PARAMS[0])
+    vals, errs = [], []
+    for seed in range(20):
+        r = _two_stage(oracle_mod, 4, 50, oracle_mod.GAUSS, GAUSS_PARAMS, 40_000, 3, 5, seed)
+        vals.append(r.integral)
+        errs.append(r.error)
+    p = refs.pulls(vals, errs, exact)
+    assert np.all(np.abs(p) < 4.5)
+    assert abs(np.mean(p)) < 1.0
+    assert 0.4 < np.std(p) < 1.8
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 7])
+def test_gauss_other_dims(oracle_mod, ndim):
+    r = _two_stage(oracle_mod, ndim, 30, oracle_mod.GAUSS, GAUSS_PARAMS, 40_000, 3, 5, 99)
+    assert abs(r.integral - refs.gauss_exact(ndim)) < 4.5 * r.error
+
+
+def test_ee3j_closed_form_and_estimate(oracle_mod):
+    y = EE3J_PARAMS[0]
+    exact = refs.ee3j_exact(y)
+    assert abs(exact - refs.ee3j_quadrature(y)) < 1e-10 * exact
+    r = _two_stage(oracle_mod, 5, 100, oracle_mod.EE3J, EE3J_PARAMS, 400_000, 4, 5, 1234)
+    assert abs(r.integral - exact) < 4.5 * r.error
+    assert r.error < 2e-3 * exact
+
+
+def test_ee3j_momenta_and_matrix_element(oracle_mod):
+    """Momenta conserve four-momentum, are massless, carry E_i = x_i Q/2, and
+    |M|^2 evaluated through them equals (x1^2+x2^2)/((1-x1)(1-x2))."""
+    rng = np.random.default_rng(8)
+    Q = EE3J_PARAMS[1]
+    n = 0
+    while n < 200:
+        x = rng.uniform(0, 1, 5)
+        g, mom = oracle_mod.integrand(oracle_mod.EE3J, x, EE3J_PARAMS, mom=True)
+        x1, x2 = x[0], x[1]
+        y = EE3J_PARAMS[0]
+        if not (1 - x1 > y and 1 - x2 > y and x1 + x2 - 1 > y):
+            assert g == 0.0
+            continue
+        n += 1
+        p = mom[:3]
+        tot = p.sum(axis=0)
+        assert np.allclose(tot, [Q, 0, 0, 0], atol=1e-11 * Q)
+        for v in p:
+            assert abs(v[0] ** 2 - v[1] ** 2 - v[2] ** 2 - v[3] ** 2) < 1e-10 * Q * Q
+        assert abs(p[0, 0] - x1 * Q / 2) < 1e-13 * Q and abs(p[1, 0] - x2 * Q / 2) < 1e-13 * Q
+        want = (x1 * x1 + x2 * x2) / ((1 - x1) * (1 - x2))
+        assert abs(g - want) < 1e-10 * want
+
+
+def test_dy_partonic_matches_helicity_amplitudes(oracle_mod):
+    p = DY_PARAMS
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        m = rng.uniform(60, 120)
+        c = rng.uniform(-1, 1)
+        for up, fq in ((1, refs.UP), (0, refs.DOWN)):
+            got = oracle_mod.dy_dsigma_domega(up, m * m, c, p)
+            want = refs.dy_dsigma_domega_helicity(fq, m * m, c, p[1], p[2], p[3], p[4])
+            assert abs(got - want) < 1e-12 * abs(want)
+
+
+def test_dy_forward_backward_sign(oracle_mod):
+    """Above the Z pole the gamma-Z interference makes mu- follow the quark."""
+    p = DY_PARAMS
+    s = 110.0 ** 2
+    assert oracle_mod.dy_dsigma_domega(1, s, 0.5, p) > oracle_mod.dy_dsigma_domega(1, s, -0.5, p)
+    s = 70.0 ** 2
+    assert oracle_mod.dy_dsigma_domega(1, s, 0.5, p) < oracle_mod.dy_dsigma_domega(1, s, -0.5, p)
+
+
+def test_dy_momenta_and_symmetry(oracle_mod):
+    p = DY_PARAMS
+    s = p[0] ** 2
+    rng = np.random.default_rng(10)
+    for _ in range(200):
+        x = rng.uniform(0, 1, 4)
+        g, mom = oracle_mod.integrand(oracle_mod.DY, x, p, mom=True)
+        p1, p2, p3, p4 = mom
+        tot_in, tot_out = p1 + p2, p3 + p4
+        scale = tot_in[0]
+        assert np.allclose(tot_in, tot_out, atol=1e-12 * scale)
+        for v in mom:
+            assert abs(v[0] ** 2 - v[1] ** 2 - v[2] ** 2 - v[3] ** 2) < 1e-9 * v[0] ** 2
+        mll2 = (p3 + p4)[0] ** 2 - np.sum((p3 + p4)[1:] ** 2)
+        tau = (p[5] / p[0]) ** 2 * (p[6] / p[5]) ** (2 * x[0])
+        assert abs(mll2 - tau * s) < 1e-6 * tau * s
+        # pp is symmetric under z -> -z: (y, cos theta) -> (-y, -cos theta)
+        xr = x.copy()
+        xr[1] = 1 - x[1]
+        xr[2] = 1 - x[2]
+        assert abs(oracle_mod.integrand(oracle_mod.DY, xr, p) - g) < 1e-11 * g
+
+
+def test_dy_total_cross_section(oracle_mod):
+    exact = refs.dy_sigma_quadrature(DY_PARAMS)
+    assert abs(exact - 5.5962) < 1e-3
+    r = _two_stage(oracle_mod, 4, 100, oracle_mod.DY, DY_PARAMS, 400_000, 4, 5, 1234)
+    assert abs(r.integral - exact) < 4.5 * r.error
+    assert r.error < 1e-3 * exact
+
+
+# --------------------------------------------------------- thread invariance
+def test_results_independent_of_thread_count(oracle_mod):
+    """Section 2.2's validation invariant, bit-exact: 1, 2, 3 and 8 threads."""
+    outs = []
+    try:
+        for nt in (1, 2, 3, 8):
+            oracle_mod.set_threads(nt)
+            r = oracle_mod.iterate(4, 50, 1234, 30_001, 3, oracle_mod.DY, DY_PARAMS, want_sums=True)
+            outs.append(r)
+    finally:
+        oracle_mod.set_threads(0)
+    for r in outs[1:]:
+        assert np.array_equal(r.per_iter, outs[0].per_iter)
+        assert np.array_equal(r.edges, outs[0].edges)
+        assert np.array_equal(r.sums, outs[0].sums)
+        assert r.integral == outs[0].integral
+
+
+def test_stage_split_is_seamless(oracle_mod):
+    """5 iterations in one call equal 2 + 3 iterations with the grid and the
+    iteration counter carried over (the checkpoint state)."""
+    a = oracle_mod.iterate(4, 50, 7, 20_000, 5, oracle_mod.GAUSS, GAUSS_PARAMS)
+    b = oracle_mod.iterate(4, 50, 7, 20_000, 2, oracle_mod.GAUSS, GAUSS_PARAMS)
+    c = oracle_mod.iterate(4, 50, 7, 20_000, 3, oracle_mod.GAUSS, GAUSS_PARAMS,
+                           edges=b.edges, iteration=b.iteration)
+    assert np.array_equal(a.per_iter, np.concatenate([b.per_iter, c.per_iter]))
+    assert np.array_equal(a.edges, c.edges)
+    assert c.iteration == 5
+
+
+def test_sums_match_direct_event_loop(oracle_mod):
+    """The chunked compensated sums equal a plain math.fsum over the events."""
+    nd, nb, ncall = 3, 10, 9000
+    e = oracle_mod.uniform_edges(nd, nb)
+    r = oracle_mod.iterate(nd, nb, 5, ncall, 1, oracle_mod.GAUSS, GAUSS_PARAMS, adapt=False,
+                           want_sums=True)
+    ws, bins = [], []
+    for ev in range(ncall):
+        w, b, _ = oracle_mod.event(oracle_mod.GAUSS, nd, nb, e, GAUSS_PARAMS, 5, 0, 0, ev)
+        ws.append(w)
+        bins.append(b)
+    ws = np.array(ws)
+    bins = np.array(bins)
+    assert abs(r.sums[0] - math.fsum(ws)) <= 2e-16 * abs(r.sums[0])
+    assert abs(r.sums[1] - math.fsum(ws * ws)) <= 2e-16 * r.sums[1]
+    d = r.sums[2:].reshape(nd, nb)
+    for a in range(nd):
+        for i in range(nb):
+            want = math.fsum(ws[bins[:, a] == i] ** 2)
+            assert abs(d[a, i] - want) <= 4e-16 * want
+    I = r.per_iter[0, 0]
+    assert abs(I - math.fsum(ws) / ncall) <= 2e-16 * I
+    var = (math.fsum(ws * ws) / ncall - I * I) / (ncall - 1)
+    assert abs(r.per_iter[0, 1] - math.sqrt(var)) <= 1e-12 * r.per_iter[0, 1]
+
+
+def test_zero_weight_iteration_keeps_grid(oracle_mod):
+    """y_cut = 0.4 leaves no phase space: every weight is 0, I = 0, grid unchanged."""
+    r = oracle_mod.iterate(5, 20, 3, 5000, 2, oracle_mod.EE3J, (0.4, 91.1876))
+    assert r.integral == 0.0 and r.error == 0.0
+    assert np.array_equal(r.edges, oracle_mod.uniform_edges(5, 20))
+
+
+def test_nonfinite_weights_are_counted(oracle_mod):
+    p = list(DY_PARAMS)
+    p[9] = float("inf")
+    r = oracle_mod.iterate(4, 10, 3, 5000, 1, oracle_mod.DY, p)
+    assert r.nonfinite == 5000
