@@ -1,0 +1,936 @@
+// gv_capi.cu -- host engine behind include/vegas.h.
+//
+// A context owns the device state of one VEGAS integration (grid pack,
+// iteration state, accumulators) and, unless the caller hands it one, the
+// workspace (tile partials, per-iteration records).  A stage of itmx
+// iterations (Section 2.1; the two-stage runs of Section 3.2) is enqueued as
+//   setup -> itmx x [fill -> reduce]
+// and, by default, captured once into a CUDA graph that is replayed by later
+// calls with the same shape; the iteration counter, the parameters and the
+// grid are read from device memory, so a replay needs no re-capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vegas.h"
+#include "gv_fill.cuh"
+
+namespace gv {
+cudaError_t launch_fill_gauss(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_fill_dy(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
+                           cudaStream_t s);
+cudaError_t launch_fill_ee3j(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
+                             cudaStream_t s);
+cudaError_t launch_fill_gauss_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
+                                   long long n, double* w, int* bins, cudaStream_t s);
+cudaError_t launch_fill_dy_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
+                                long long n, double* w, int* bins, cudaStream_t s);
+cudaError_t launch_fill_ee3j_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
+                                  long long n, double* w, int* bins, cudaStream_t s);
+}  // namespace gv
+
+namespace {
+
+#define GV_TRY(expr)                   \
+  do {                                 \
+    cudaError_t _e = (expr);           \
+    if (_e != cudaSuccess) {           \
+      gv_last_cuda_error() = _e;       \
+      return VEGAS_ECUDA;              \
+    }                                  \
+  } while (0)
+
+cudaError_t& gv_last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+cudaError_t launch_fill_any(int ig, int fp32, int ept, const GvFillArgs& a, int n_tiles,
+                            size_t smem, cudaStream_t s) {
+  switch (ig) {
+    case GV_GAUSS: return gv::launch_fill_gauss(fp32, ept, a, n_tiles, smem, s);
+    case GV_DY: return gv::launch_fill_dy(fp32, ept, a, n_tiles, smem, s);
+    case GV_EE3J: return gv::launch_fill_ee3j(fp32, ept, a, n_tiles, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Parameter validation: counts and physical ranges.
+int check_params(int ig, int ndim, const double* p, int np) {
+  if (!p && np > 0) return VEGAS_EINVAL;
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(p[i])) return VEGAS_EINVAL;
+  switch (ig) {
+    case VEGAS_GAUSS:
+      if (np != 1 || ndim < 1 || !(p[0] > 0.0)) return VEGAS_EINVAL;
+      return VEGAS_OK;
+    case VEGAS_DY:
+      if (np != 10 || ndim < 4) return VEGAS_EINVAL;
+      if (!(p[0] > 0 && p[1] > 0 && p[2] > 0 && p[3] > 0 && p[3] < 1 && p[4] > 0 && p[5] > 0 &&
+            p[6] > p[5] && p[6] < p[0] && p[9] > 0))
+        return VEGAS_EINVAL;
+      return VEGAS_OK;
+    case VEGAS_EE3J:
+      if ((np != 1 && np != 2) || ndim < 5 || !(p[0] > 0.0 && p[0] < 1.0)) return VEGAS_EINVAL;
+      if (np == 2 && !(p[1] > 0.0)) return VEGAS_EINVAL;
+      return VEGAS_OK;
+  }
+  return VEGAS_EINVAL;
+}
+
+int maxd_class(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : 16); }
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Autotuner cache: best events-per-thread per (integrand, precision, mode,
+// d class, nbins, log2 tiles).  Results are identical for every choice.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+std::string tune_key(int dev, int ig, int fp32, int mode, int d, int N, int n_tiles) {
+  char buf[160];
+  int lg = 0;
+  while ((1 << (lg + 1)) <= n_tiles && lg < 30) ++lg;
+  snprintf(buf, sizeof buf, "dev%d:ig%d:fp%d:m%d:d%d:N%d:t%d", dev, ig, fp32, mode, maxd_class(d),
+           N, lg);
+  return buf;
+}
+
+}  // namespace
+
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> events;  // 3 per iteration when timed
+};
+
+struct vegas_ctx {
+  int ndim = 0, nbins = 0;
+  uint64_t seed = 0;
+  uint32_t batch = 0;
+  double alpha = 1.5;
+  int fp32 = 0, adapt = 1, ept_opt = 0, nonfinite_policy = 0, use_graph = 1, timing = 0;
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // fixed device memory
+  void* fixed = nullptr;
+  double* grid = nullptr;
+  GvState* st = nullptr;
+  double* params = nullptr;
+  double* kconst = nullptr;
+  unsigned long long* acc = nullptr;
+  double* sums = nullptr;
+  double* scratch = nullptr;
+  int nacc_max = 0;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_external = false;
+  // pinned host staging for results
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  // last launch
+  int last_itmx = 0, last_mode = 0, last_ept = 0;
+  double* last_per_iter = nullptr;
+  bool pending = false;
+  std::vector<cudaEvent_t> pending_events;
+  double t_fill_ms = 0, t_reduce_ms = 0;
+  int64_t n_fill = 0, n_reduce = 0;
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+void clear_graphs(vegas_ctx* c) {
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto e : g.events) cudaEventDestroy(e);
+  }
+  c->graphs.clear();
+  c->pending_events.clear();
+}
+
+size_t grid_doubles(int d, int N) { return GvGridLayout{d, N}.doubles(); }
+
+size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode) {
+  const int64_t n_tiles = (ncall + GV_TILE - 1) / GV_TILE;
+  const int nch = mode ? GV_MAXCH : 1;
+  const int nacc = mode ? 2 * GV_MAXCH : 2 + d * N;
+  size_t b = align256((size_t)n_tiles * nacc * 16);
+  b += align256((size_t)n_tiles * nch * 4);
+  b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
+  return b;
+}
+
+int ensure_workspace(vegas_ctx* c, size_t need) {
+  if (c->ws_bytes >= need && c->ws) return VEGAS_OK;
+  if (c->ws_external) return VEGAS_ENOMEM;
+  if (c->ws) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    clear_graphs(c);
+  }
+  size_t bytes = std::max(need, (size_t)1 << 20);
+  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return VEGAS_ENOMEM;
+  }
+  c->ws_bytes = bytes;
+  return VEGAS_OK;
+}
+
+int ensure_pinned(vegas_ctx* c, size_t need) {
+  if (c->pinned_bytes >= need) return VEGAS_OK;
+  if (c->pinned) cudaFreeHost(c->pinned);
+  c->pinned = nullptr;
+  c->pinned_bytes = 0;
+  if (cudaHostAlloc(&c->pinned, need, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return VEGAS_ENOMEM;
+  }
+  c->pinned_bytes = need;
+  return VEGAS_OK;
+}
+
+struct Plan {
+  int ig, fp32, mode, itmx, n_tiles, nacc, nch, ept, reduce_ctas, tiles_per_cta;
+  int64_t ncall;
+  size_t smem;
+  ulonglong2* part;
+  int* tileE;
+  double* per_iter;
+};
+
+GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
+  GvFillArgs a;
+  a.ndim = c->ndim;
+  a.nbins = c->nbins;
+  a.nch = p.nch;
+  a.nacc = p.nacc;
+  a.ncall = p.ncall;
+  a.seed = c->seed;
+  a.batch = c->batch;
+  a.kconst = c->kconst;
+  a.grid = c->grid;
+  a.st = c->st;
+  a.part = p.part;
+  a.tileE = p.tileE;
+  return a;
+}
+
+GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p) {
+  GvReduceArgs r;
+  r.ndim = c->ndim;
+  r.nbins = c->nbins;
+  r.nch = p.nch;
+  r.nacc = p.nacc;
+  r.has_bins = p.mode == 0;
+  r.adapt = p.mode == 0 ? c->adapt : 0;
+  r.itmx = p.itmx;
+  r.mode = p.mode;
+  r.ncall = p.ncall;
+  r.n_tiles = p.n_tiles;
+  r.tiles_per_cta = p.tiles_per_cta;
+  r.alpha = c->alpha;
+  r.part = p.part;
+  r.tileE = p.tileE;
+  r.st = c->st;
+  r.acc = c->acc;
+  r.sums = c->sums;
+  r.per_iter = p.per_iter;
+  r.grid = c->grid;
+  r.scratch = c->scratch;
+  return r;
+}
+
+cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept) {
+  const GvFillArgs a = fill_args(c, p);
+  if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream);
+  return launch_fill_any(p.ig, p.fp32, ept, a, p.n_tiles, p.smem, c->stream);
+}
+
+// Pick events per thread by timing one fill launch per candidate.  Runs
+// between two setup kernels, so the trial launches leave no trace.
+int autotune(vegas_ctx* c, Plan& p) {
+  const std::string key = tune_key(c->device, p.ig, p.fp32, p.mode, c->ndim, c->nbins, p.n_tiles);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      p.ept = it->second;
+      return VEGAS_OK;
+    }
+  }
+  const int cands_fwd[] = {1, 2, 4, 8};
+  const int cands_adj[] = {1, 2, 4};
+  const int* cands = p.mode ? cands_adj : cands_fwd;
+  const int nc = p.mode ? 3 : 4;
+  cudaEvent_t e0, e1;
+  GV_TRY(cudaEventCreate(&e0));
+  GV_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_ept = 4;
+  for (int i = 0; i < nc; ++i) {
+    const int ept = cands[i];
+    if (c->ndim > 8 && ept == 8) continue;
+    cudaError_t err = launch_fill_plan(c, p, ept);  // warm-up
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float best_i = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      launch_fill_plan(c, p, ept);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_i = std::min(best_i, ms);
+    }
+    if (best_i < best) {
+      best = best_i;
+      best_ept = ept;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  GV_TRY(cudaGetLastError());
+  p.ept = best_ept;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best_ept;
+  return VEGAS_OK;
+}
+
+int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) {
+  p.ig = ig;
+  p.fp32 = c->fp32;
+  p.mode = mode;
+  p.itmx = itmx;
+  p.ncall = ncall;
+  const int64_t nt = (ncall + GV_TILE - 1) / GV_TILE;
+  if (nt > 0x7fffffff) return VEGAS_EINVAL;
+  p.n_tiles = (int)nt;
+  p.nch = mode ? GV_MAXCH : 1;
+  p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins;
+  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0).total;
+  p.tiles_per_cta = std::max(1, (int)((nt + 2LL * c->sm_count - 1) / (2LL * c->sm_count)));
+  p.reduce_ctas = (int)((nt + p.tiles_per_cta - 1) / p.tiles_per_cta);
+  const size_t need = workspace_bytes(c->ndim, c->nbins, ncall, itmx, mode);
+  int st = ensure_workspace(c, need);
+  if (st) return st;
+  char* w = (char*)c->ws;
+  p.part = (ulonglong2*)w;
+  w += align256((size_t)p.n_tiles * p.nacc * 16);
+  p.tileE = (int*)w;
+  w += align256((size_t)p.n_tiles * p.nch * 4);
+  p.per_iter = (double*)w;
+  p.ept = c->ept_opt;
+  return VEGAS_OK;
+}
+
+int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool capture) {
+  GV_TRY(gv::launch_setup(p.ig, c->params, c->kconst, c->st, p.nacc, c->acc, c->stream));
+  const GvReduceArgs r = reduce_args(c, p);
+  const unsigned flags = capture ? cudaEventRecordExternal : 0u;
+  for (int k = 0; k < p.itmx; ++k) {
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
+    GV_TRY(launch_fill_plan(c, p, p.ept));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
+    GV_TRY(gv::launch_reduce(r, p.reduce_ctas, c->stream));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
+  }
+  return VEGAS_OK;
+}
+
+GraphEntry* find_entry(vegas_ctx* c, const std::string& key) {
+  for (auto& g : c->graphs)
+    if (g.key == key) return &g;
+  return nullptr;
+}
+
+int new_events(std::vector<cudaEvent_t>& ev, size_t n) {
+  ev.resize(n);
+  for (auto& e : ev) GV_TRY(cudaEventCreate(&e));
+  return VEGAS_OK;
+}
+
+void drop_oldest_entry(vegas_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  GraphEntry& old = c->graphs.front();
+  if (old.exec) cudaGraphExecDestroy(old.exec);
+  for (auto e : old.events) cudaEventDestroy(e);
+  c->graphs.erase(c->graphs.begin());
+}
+
+int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* params, int np,
+                  int mode) {
+  if (c->pending) {
+    // results of an unfetched launch are dropped; wait so that no work overlaps
+    GV_TRY(cudaStreamSynchronize(c->stream));
+    c->pending = false;
+    c->pending_events.clear();
+  }
+  if (ncall < 2 || ncall > ((int64_t)1 << 40) || itmx < 1 || itmx > 100000) return VEGAS_EINVAL;
+  int st = check_params(ig, c->ndim, params, np);
+  if (st) return st;
+  if (mode && ig != VEGAS_DY) return VEGAS_EINVAL;
+  Plan p;
+  st = make_plan(c, ncall, itmx, ig, mode, p);
+  if (st) return st;
+  // parameters: a pageable copy is staged before cudaMemcpyAsync returns; the
+  // count rides in the last slot
+  double hp[GV_MAXPARAMS] = {0};
+  for (int i = 0; i < np && i < GV_MAXPARAMS - 1; ++i) hp[i] = params[i];
+  hp[GV_MAXPARAMS - 1] = (double)np;
+  GV_TRY(cudaMemcpyAsync(c->params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream));
+  if (p.ept == 0) {
+    GV_TRY(gv::launch_setup(p.ig, c->params, c->kconst, c->st, p.nacc, c->acc, c->stream));
+    st = autotune(c, p);
+    if (st) return st;
+  }
+  c->last_itmx = itmx;
+  c->last_mode = mode;
+  c->last_ept = p.ept;
+  c->last_per_iter = p.per_iter;
+  c->pending_events.clear();
+  const bool graph_ok = c->use_graph && c->stream != nullptr;
+  if (!graph_ok) {
+    std::vector<cudaEvent_t>* evp = nullptr;
+    if (c->timing) {
+      const std::string key = "plain-events:" + std::to_string(itmx);
+      GraphEntry* ge = find_entry(c, key);
+      if (!ge) {
+        if (c->graphs.size() >= 16) drop_oldest_entry(c);
+        GraphEntry g;
+        g.key = key;
+        st = new_events(g.events, 3 * (size_t)itmx);
+        if (st) return st;
+        c->graphs.push_back(g);
+        ge = &c->graphs.back();
+      }
+      evp = &ge->events;
+    }
+    st = enqueue_body(c, p, evp, false);
+    if (st) return st;
+    if (evp) c->pending_events = *evp;
+    c->pending = true;
+    return VEGAS_OK;
+  }
+  char kb[320];
+  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d:%llu:%u:%p:%p", ig, p.fp32, mode,
+           (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing,
+           (unsigned long long)c->seed, c->batch, c->ws, (void*)c->stream);
+  const std::string key(kb);
+  GraphEntry* ge = find_entry(c, key);
+  if (!ge) {
+    if (c->graphs.size() >= 16) drop_oldest_entry(c);
+    GraphEntry g;
+    g.key = key;
+    if (c->timing) {
+      st = new_events(g.events, 3 * (size_t)itmx);
+      if (st) return st;
+    }
+    cudaGraph_t graph;
+    GV_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_body(c, p, c->timing ? &g.events : nullptr, true);
+    const cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+    if (st) {
+      if (ce == cudaSuccess) cudaGraphDestroy(graph);
+      for (auto e : g.events) cudaEventDestroy(e);
+      return st;
+    }
+    GV_TRY(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    GV_TRY(ie);
+    c->graphs.push_back(g);
+    ge = &c->graphs.back();
+  }
+  GV_TRY(cudaGraphLaunch(ge->exec, c->stream));
+  c->pending_events = ge->events;
+  c->pending = true;
+  return VEGAS_OK;
+}
+
+// Wait for the pending stage; copy the state and the per-iteration records.
+int fetch_stage(vegas_ctx* c, GvState* hs, std::vector<double>* per_iter) {
+  if (!c->pending) return VEGAS_EINVAL;
+  const int stride = c->last_mode ? 2 + 2 * GV_NGRAD : 2;
+  const size_t nrec = (size_t)c->last_itmx * stride;
+  const size_t need = sizeof(GvState) + nrec * sizeof(double) + 64;
+  int st = ensure_pinned(c, need);
+  if (st) return st;
+  char* pin = (char*)c->pinned;
+  GV_TRY(cudaMemcpyAsync(pin, c->st, sizeof(GvState), cudaMemcpyDeviceToHost, c->stream));
+  double* pin_rec = (double*)(pin + ((sizeof(GvState) + 63) & ~(size_t)63));
+  GV_TRY(cudaMemcpyAsync(pin_rec, c->last_per_iter, nrec * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream));
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  memcpy(hs, pin, sizeof(GvState));
+  if (per_iter) per_iter->assign(pin_rec, pin_rec + nrec);
+  if (!c->pending_events.empty()) {
+    for (size_t k = 0; k + 2 < c->pending_events.size(); k += 3) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, c->pending_events[k], c->pending_events[k + 1]) ==
+          cudaSuccess) {
+        c->t_fill_ms += a;
+        c->n_fill += 1;
+      }
+      if (cudaEventElapsedTime(&b, c->pending_events[k + 1], c->pending_events[k + 2]) ==
+          cudaSuccess) {
+        c->t_reduce_ms += b;
+        c->n_reduce += 1;
+      }
+    }
+    cudaGetLastError();
+    c->pending_events.clear();
+  }
+  c->pending = false;
+  if (hs->status) return VEGAS_EDEVICE;
+  if (hs->nonfinite && c->nonfinite_policy == 0) return VEGAS_ENONFINITE;
+  return VEGAS_OK;
+}
+
+int valid_grid(const double* e, int d, int N) {
+  for (int a = 0; a < d; ++a) {
+    const double* r = e + (size_t)a * (N + 1);
+    if (r[0] != 0.0 || r[N] != 1.0) return 0;
+    for (int i = 0; i < N; ++i)
+      if (!(r[i + 1] > r[i])) return 0;
+  }
+  return 1;
+}
+
+int upload_grid(vegas_ctx* c, const double* edges) {
+  const size_t n = (size_t)c->ndim * (c->nbins + 1);
+  GV_TRY(cudaMemcpyAsync(c->grid, edges, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  GV_TRY(gv::launch_grid_pack(c->ndim, c->nbins, c->grid, c->stream));
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+struct StateBlob {
+  uint32_t magic, version;
+  int32_t ndim, nbins;
+  uint64_t seed, it;
+  uint32_t batch;
+  int32_t fp32, adapt, nonfinite_policy;
+  double alpha;
+};
+const uint32_t kStateMagic = 0x47564547u;  // "GVEG"
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* vegas_strerror(int status) {
+  switch (status) {
+    case VEGAS_OK: return "ok";
+    case VEGAS_EINVAL: return "invalid argument";
+    case VEGAS_ENOMEM: return "out of memory";
+    case VEGAS_ECUDA: return "CUDA runtime error";
+    case VEGAS_EGRID: return "invalid grid (edges must be 0 = e_0 < ... < e_N = 1)";
+    case VEGAS_ENONFINITE: return "non-finite weights were seen (counted as 0)";
+    case VEGAS_EDEVICE: return "device-side check failed";
+    case VEGAS_ESTATE: return "checkpoint does not match this context";
+  }
+  return "unknown status";
+}
+
+int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
+  if (!out) return VEGAS_EINVAL;
+  *out = nullptr;
+  if (ndim < 1 || ndim > VEGAS_MAX_DIM || nbins < VEGAS_MIN_BINS || nbins > VEGAS_MAX_BINS ||
+      ndim * nbins > VEGAS_MAX_DIM_BINS)
+    return VEGAS_EINVAL;
+  vegas_ctx* c = new vegas_ctx();
+  c->ndim = ndim;
+  c->nbins = nbins;
+  c->seed = seed;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    gv_last_cuda_error() = cudaGetLastError();
+    delete c;
+    return VEGAS_ECUDA;
+  }
+  c->own_stream = true;
+  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins);
+  const size_t gd = grid_doubles(ndim, nbins);
+  size_t off = 0;
+  const size_t o_grid = off;
+  off = align256(off + gd * 8);
+  const size_t o_st = off;
+  off = align256(off + sizeof(GvState));
+  const size_t o_par = off;
+  off = align256(off + GV_MAXPARAMS * 8);
+  const size_t o_k = off;
+  off = align256(off + GV_NCONST * 8);
+  const size_t o_acc = off;
+  off = align256(off + (size_t)c->nacc_max * 3 * 8);
+  const size_t o_sums = off;
+  off = align256(off + (size_t)c->nacc_max * 8);
+  const size_t o_scr = off;
+  off = align256(off + (size_t)3 * ndim * (nbins + 1) * 8);
+  if (cudaMalloc(&c->fixed, off) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(c->stream);
+    delete c;
+    return VEGAS_ENOMEM;
+  }
+  char* b = (char*)c->fixed;
+  c->grid = (double*)(b + o_grid);
+  c->st = (GvState*)(b + o_st);
+  c->params = (double*)(b + o_par);
+  c->kconst = (double*)(b + o_k);
+  c->acc = (unsigned long long*)(b + o_acc);
+  c->sums = (double*)(b + o_sums);
+  c->scratch = (double*)(b + o_scr);
+  int st = VEGAS_OK;
+  if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess) st = VEGAS_ECUDA;
+  if (!st) {
+    std::vector<double> e((size_t)ndim * (nbins + 1));
+    for (int a = 0; a < ndim; ++a)
+      for (int i = 0; i <= nbins; ++i) e[(size_t)a * (nbins + 1) + i] = (double)i / nbins;
+    st = upload_grid(c, e.data());
+  }
+  if (st) {
+    vegas_free(c);
+    return st;
+  }
+  *out = c;
+  return VEGAS_OK;
+}
+
+void vegas_free(vegas_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  clear_graphs(c);
+  if (c->ws && !c->ws_external) cudaFree(c->ws);
+  if (c->fixed) cudaFree(c->fixed);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int vegas_set_option(vegas_ctx* c, int key, double v) {
+  if (!c || !std::isfinite(v)) return VEGAS_EINVAL;
+  switch (key) {
+    case VEGAS_OPT_ALPHA:
+      if (v < 0.0) return VEGAS_EINVAL;
+      c->alpha = v;
+      return VEGAS_OK;
+    case VEGAS_OPT_PRECISION:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->fp32 = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_ADAPT:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->adapt = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_EPT:
+      if (v != 0.0 && v != 1.0 && v != 2.0 && v != 4.0 && v != 8.0) return VEGAS_EINVAL;
+      if (v == 8.0 && c->ndim > 8) return VEGAS_EINVAL;
+      c->ept_opt = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_NONFINITE:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->nonfinite_policy = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_GRAPH:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->use_graph = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_TIMING:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->timing = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_BATCH_ID:
+      if (v < 0.0 || v >= 16777216.0 || v != std::floor(v)) return VEGAS_EINVAL;
+      c->batch = (uint32_t)v;
+      return VEGAS_OK;
+  }
+  return VEGAS_EINVAL;
+}
+
+int vegas_set_stream(vegas_ctx* c, void* stream) {
+  if (!c) return VEGAS_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  c->stream = (cudaStream_t)stream;
+  clear_graphs(c);
+  return VEGAS_OK;
+}
+
+int vegas_workspace_size(const vegas_ctx* c, int64_t ncall, int itmx, size_t* bytes) {
+  if (!c || !bytes || ncall < 2 || itmx < 1) return VEGAS_EINVAL;
+  *bytes = std::max(workspace_bytes(c->ndim, c->nbins, ncall, itmx, 0),
+                    workspace_bytes(c->ndim, c->nbins, ncall, itmx, 1));
+  return VEGAS_OK;
+}
+
+int vegas_set_workspace(vegas_ctx* c, void* ptr, size_t bytes) {
+  if (!c) return VEGAS_EINVAL;
+  if (ptr && ((uintptr_t)ptr % 256 != 0)) return VEGAS_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  clear_graphs(c);
+  if (c->ws && !c->ws_external) cudaFree(c->ws);
+  c->ws = ptr;
+  c->ws_bytes = ptr ? bytes : 0;
+  c->ws_external = ptr != nullptr;
+  return VEGAS_OK;
+}
+
+int vegas_launch(vegas_ctx* c, int64_t ncall, int itmx, int id, const double* params, int np) {
+  if (!c) return VEGAS_EINVAL;
+  return enqueue_stage(c, ncall, itmx, id, params, np, 0);
+}
+
+int vegas_fetch(vegas_ctx* c, double* integral, double* error, double* chi2, double* per_iter,
+                int64_t* nonfinite) {
+  if (!c || c->last_mode != 0) return VEGAS_EINVAL;
+  GvState hs;
+  std::vector<double> rec;
+  const int st = fetch_stage(c, &hs, per_iter ? &rec : nullptr);
+  if (st && st != VEGAS_ENONFINITE) return st;
+  if (integral) *integral = hs.integral;
+  if (error) *error = hs.error;
+  if (chi2) *chi2 = hs.chi2;
+  if (nonfinite) *nonfinite = (int64_t)hs.nonfinite;
+  if (per_iter) memcpy(per_iter, rec.data(), rec.size() * sizeof(double));
+  return st;
+}
+
+int vegas_iterate(vegas_ctx* c, int64_t ncall, int itmx, int id, const double* params, int np,
+                  double* integral, double* error, double* chi2, double* per_iter) {
+  if (!c) return VEGAS_EINVAL;
+  int st = enqueue_stage(c, ncall, itmx, id, params, np, 0);
+  if (st) return st;
+  return vegas_fetch(c, integral, error, chi2, per_iter, nullptr);
+}
+
+int vegas_adjoint(vegas_ctx* c, int64_t ncall, int itmx, int id, const double* params, int np,
+                  double* grad, double* grad_err, double* integral, double* error,
+                  double* per_iter_grad) {
+  if (!c || !grad || !grad_err) return VEGAS_EINVAL;
+  int st = enqueue_stage(c, ncall, itmx, id, params, np, 1);
+  if (st) return st;
+  GvState hs;
+  std::vector<double> rec;
+  st = fetch_stage(c, &hs, per_iter_grad ? &rec : nullptr);
+  if (st && st != VEGAS_ENONFINITE) return st;
+  for (int q = 0; q < GV_NGRAD; ++q) {
+    grad[q] = hs.grad[q];
+    grad_err[q] = hs.grad_err[q];
+  }
+  if (integral) *integral = hs.integral;
+  if (error) *error = hs.error;
+  if (per_iter_grad) {
+    const int stride = 2 + 2 * GV_NGRAD;
+    for (int k = 0; k < itmx; ++k)
+      for (int q = 0; q < GV_NGRAD; ++q) {
+        per_iter_grad[(k * GV_NGRAD + q) * 2] = rec[(size_t)k * stride + 2 + 2 * q];
+        per_iter_grad[(k * GV_NGRAD + q) * 2 + 1] = rec[(size_t)k * stride + 3 + 2 * q];
+      }
+  }
+  return st;
+}
+
+int vegas_grid_get(const vegas_ctx* c, double* edges) {
+  if (!c || !edges) return VEGAS_EINVAL;
+  const size_t n = (size_t)c->ndim * (c->nbins + 1);
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  GV_TRY(cudaMemcpy(edges, c->grid, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return VEGAS_OK;
+}
+
+int vegas_grid_set(vegas_ctx* c, const double* edges) {
+  if (!c || !edges) return VEGAS_EINVAL;
+  if (!valid_grid(edges, c->ndim, c->nbins)) return VEGAS_EGRID;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  return upload_grid(c, edges);
+}
+
+int vegas_state_size(const vegas_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return VEGAS_EINVAL;
+  *bytes = sizeof(StateBlob) + (size_t)c->ndim * (c->nbins + 1) * sizeof(double);
+  return VEGAS_OK;
+}
+
+int vegas_state_get(const vegas_ctx* c, void* buf, size_t bytes) {
+  size_t need = 0;
+  if (!c || !buf || vegas_state_size(c, &need) || bytes < need) return VEGAS_EINVAL;
+  StateBlob h;
+  memset(&h, 0, sizeof h);
+  h.magic = kStateMagic;
+  h.version = 1;
+  h.ndim = c->ndim;
+  h.nbins = c->nbins;
+  h.seed = c->seed;
+  GvState hs;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  GV_TRY(cudaMemcpy(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost));
+  h.it = hs.it;
+  h.batch = c->batch;
+  h.fp32 = c->fp32;
+  h.adapt = c->adapt;
+  h.nonfinite_policy = c->nonfinite_policy;
+  h.alpha = c->alpha;
+  memcpy(buf, &h, sizeof h);
+  return vegas_grid_get(c, (double*)((char*)buf + sizeof h));
+}
+
+int vegas_state_set(vegas_ctx* c, const void* buf, size_t bytes) {
+  size_t need = 0;
+  if (!c || !buf || vegas_state_size(c, &need)) return VEGAS_EINVAL;
+  if (bytes < need) return VEGAS_ESTATE;
+  StateBlob h;
+  memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.version != 1 || h.ndim != c->ndim || h.nbins != c->nbins)
+    return VEGAS_ESTATE;
+  std::vector<double> e((size_t)c->ndim * (c->nbins + 1));
+  memcpy(e.data(), (const char*)buf + sizeof h, e.size() * sizeof(double));
+  if (!valid_grid(e.data(), c->ndim, c->nbins)) return VEGAS_EGRID;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  c->seed = h.seed;
+  c->batch = h.batch;
+  c->fp32 = h.fp32;
+  c->adapt = h.adapt;
+  c->nonfinite_policy = h.nonfinite_policy;
+  c->alpha = h.alpha;
+  GvState hs;
+  GV_TRY(cudaMemcpy(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost));
+  hs.it = h.it;
+  GV_TRY(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));
+  clear_graphs(c);
+  return upload_grid(c, e.data());
+}
+
+int vegas_eval_events(vegas_ctx* c, int id, const double* params, int np, uint32_t iteration,
+                      const int64_t* events, int64_t n, double* w, int32_t* bins) {
+  if (!c || n < 0 || (n > 0 && (!events || !w || !bins))) return VEGAS_EINVAL;
+  int st = check_params(id, c->ndim, params, np);
+  if (st) return st;
+  if (n == 0) return VEGAS_OK;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  double hp[GV_MAXPARAMS] = {0};
+  for (int i = 0; i < np; ++i) hp[i] = params[i];
+  hp[GV_MAXPARAMS - 1] = (double)np;
+  void* dmem = nullptr;
+  const size_t bytes = (size_t)n * (8 + 8 + 4 * c->ndim) + 64;
+  if (cudaMalloc(&dmem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return VEGAS_ENOMEM;
+  }
+  long long* dev = (long long*)dmem;
+  double* dw = (double*)(dev + n);
+  int* db = (int*)(dw + n);
+  st = VEGAS_OK;
+  cudaError_t e = cudaMemcpyAsync(c->params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev, events, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+  // derive the constants without disturbing the iteration state: setup on a
+  // scratch state in the workspace-free fixed area is not needed because
+  // setup only resets stage bookkeeping, which no stage is using now
+  GvState saved;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&saved, c->st, sizeof saved, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = gv::launch_setup(id, c->params, c->kconst, c->st, 0, c->acc, c->stream);
+  if (e == cudaSuccess) {
+    GvFillArgs a;
+    memset(&a, 0, sizeof a);
+    a.ndim = c->ndim;
+    a.nbins = c->nbins;
+    a.seed = c->seed;
+    a.batch = c->batch;
+    a.kconst = c->kconst;
+    a.grid = c->grid;
+    a.st = c->st;
+    switch (id) {
+      case GV_GAUSS: e = gv::launch_fill_gauss_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
+      case GV_DY: e = gv::launch_fill_dy_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
+      default: e = gv::launch_fill_ee3j_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->st, &saved, sizeof saved, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bins, db, (size_t)n * 4 * c->ndim, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dmem);
+  if (e != cudaSuccess) {
+    gv_last_cuda_error() = e;
+    return VEGAS_ECUDA;
+  }
+  return VEGAS_OK;
+}
+
+int vegas_rng_words(uint64_t seed, uint32_t iteration, uint32_t batch, int64_t first, int64_t n,
+                    int ndim, uint32_t* out) {
+  if (n < 0 || first < 0 || ndim < 1 || ndim > VEGAS_MAX_DIM || (n > 0 && !out))
+    return VEGAS_EINVAL;
+  if (n == 0) return VEGAS_OK;
+  uint32_t* d = nullptr;
+  const size_t bytes = (size_t)n * ndim * 4;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return VEGAS_ENOMEM;
+  }
+  cudaError_t e = gv::launch_rng_words(seed, iteration, batch, (unsigned long long)first, n, ndim,
+                                       d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    gv_last_cuda_error() = e;
+    return VEGAS_ECUDA;
+  }
+  return VEGAS_OK;
+}
+
+int vegas_last_sums(const vegas_ctx* c, double* sums) {
+  if (!c || !sums) return VEGAS_EINVAL;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  GV_TRY(cudaMemcpy(sums, c->sums, (size_t)(2 + c->ndim * c->nbins) * sizeof(double),
+                    cudaMemcpyDeviceToHost));
+  return VEGAS_OK;
+}
+
+int vegas_kernel_time(vegas_ctx* c, int kernel, double* total_ms, int64_t* launches, int reset) {
+  if (!c || (kernel != VEGAS_KERNEL_FILL && kernel != VEGAS_KERNEL_REDUCE)) return VEGAS_EINVAL;
+  if (total_ms) *total_ms = kernel == VEGAS_KERNEL_FILL ? c->t_fill_ms : c->t_reduce_ms;
+  if (launches) *launches = kernel == VEGAS_KERNEL_FILL ? c->n_fill : c->n_reduce;
+  if (reset) {
+    c->t_fill_ms = c->t_reduce_ms = 0.0;
+    c->n_fill = c->n_reduce = 0;
+  }
+  return VEGAS_OK;
+}
+
+int vegas_get_ept(const vegas_ctx* c, int* ept) {
+  if (!c || !ept) return VEGAS_EINVAL;
+  *ept = c->last_ept;
+  return VEGAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// gv_common.cuh -- internal definitions shared by the GB300 VEGAS kernels.
+//
+// One VEGAS iteration (Section 2.1: events evaluated independently, all events
+// combined, serial grid optimisation) runs as two kernels:
+//   fill   : one CTA per tile of GV_TILE consecutive events; uniforms from
+//            Philox4x32-10, grid map, integrand, then exact integer
+//            accumulation of sum w, sum w^2 and the per-bin sums of w^2
+//            into a per-tile partial;
+//   reduce : exact integer reduction of the tile partials; the last CTA to
+//            finish converts the sums to FP64, records the iteration and
+//            refines the grid.
+//
+// Exact accumulation.  Every tile takes its scale from its largest |v| (an
+// order-free max): E_t with max|v| < 2^E_t.  Each v is rounded once to an
+// integer multiple of 2^(E_t - GV_FB) (v^2 to 2^(2 E_t - GV_FB)); from then on
+// only integer additions happen, which are associative.  The result is
+// therefore bit-identical for any block size, events per thread, tile-to-CTA
+// schedule and batching -- the paper's "independent of the number of
+// threads" (Section 2.2) made exact -- and it is more accurate than the
+// Kahan sums the paper uses for the same purpose.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define GV_TILE 1024          // canonical events per tile
+#define GV_FB 96              // fixed-point bits below a tile's scale
+#define GV_MAXD 16            // maximum number of axes
+#define GV_NGRAD 5            // Drell-Yan gradient components
+#define GV_MAXCH (1 + GV_NGRAD)
+#define GV_EMPTY (-0x40000000)  // scale of a tile / iteration with no nonzero value
+#define GV_NCONST 48          // derived integrand constants per integration
+#define GV_MAXPARAMS 16
+
+enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2 };
+
+// Device-side state of one integration (one context or one batch member).
+struct GvState {
+  unsigned long long it;         // global iteration counter (Philox counter word)
+  unsigned long long nonfinite;  // non-finite weights seen in this stage
+  int m;                         // iterations done in this stage
+  int done;                      // reduce CTAs finished (last-block ticket)
+  int status;                    // device error word (0 = ok)
+  int E[GV_MAXCH];               // per-channel iteration scale (atomicMax)
+  int pad;
+  double integral, error, chi2;
+  double grad[GV_NGRAD], grad_err[GV_NGRAD];
+};
+
+// Grid pack of one integration (device memory, rewritten by every refine):
+//   e64[d][N+1] | wd64[d][N] | jac[d][N] | e32[d][N+1] | wd32[d][N]
+// wd = e[i+1]-e[i]; jac = N*wd (the axis' Jacobian factor).
+struct GvGridLayout {
+  int d, N;
+  __host__ __device__ size_t off_e64() const { return 0; }
+  __host__ __device__ size_t off_wd64() const { return (size_t)d * (N + 1); }
+  __host__ __device__ size_t off_jac() const { return off_wd64() + (size_t)d * N; }
+  // float parts, counted in doubles from the start of the pack
+  __host__ __device__ size_t off_f32_base() const { return off_jac() + (size_t)d * N; }
+  __host__ __device__ size_t doubles() const {
+    size_t nf = (size_t)d * (N + 1) + (size_t)d * N;  // floats
+    return off_f32_base() + (nf + 1) / 2;
+  }
+};
+
+// Arguments of the fill kernels (forward and adjoint).
+struct GvFillArgs {
+  int ndim, nbins, nch, nacc;
+  long long ncall;
+  unsigned long long seed;
+  unsigned batch;
+  const double* kconst;          // derived integrand constants
+  const double* grid;            // grid pack
+  GvState* st;
+  ulonglong2* part;              // [tile][nacc] 128-bit two's complement sums
+  int* tileE;                    // [tile][nch] scales
+};
+
+// Arguments of the reduce/finalize kernel.
+struct GvReduceArgs {
+  int ndim, nbins, nch, nacc, has_bins, adapt, itmx, mode;  // mode 0 forward, 1 adjoint
+  long long ncall;
+  int n_tiles, tiles_per_cta;
+  double alpha;
+  const ulonglong2* part;
+  const int* tileE;
+  GvState* st;
+  unsigned long long* acc;       // [nacc][3] 192-bit accumulators
+  double* sums;                  // [nacc] FP64 sums of the last iteration
+  double* per_iter;              // forward: [itmx][2]; adjoint: [itmx][2 + 2*NGRAD]
+  double* grid;                  // grid pack (refined in place)
+  double* scratch;               // refine scratch: 3 * d * (N+1) doubles
+};
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplications with a Weyl-bumped key.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint4 gv_philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t a = c.x, b = c.z;
+    const uint32_t h0 = __umulhi(0xD2511F53u, a), l0 = 0xD2511F53u * a;
+    const uint32_t h1 = __umulhi(0xCD9E8D57u, b), l1 = 0xCD9E8D57u * b;
+    c = make_uint4(h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0);
+  }
+  return c;
+}
+
+// Words of one event: Philox block j has counter (ev lo, ev hi, it, batch<<8|j)
+// and key (seed lo, seed hi); its word k drives axis 4j+k.
+template <int MAXD>
+__device__ __forceinline__ void gv_event_words(unsigned long long seed, uint32_t it,
+                                               uint32_t batch, unsigned long long ev,
+                                               int d, uint32_t (&r)[MAXD]) {
+#pragma unroll
+  for (int j = 0; j < (MAXD + 3) / 4; ++j) {
+    if (4 * j < d) {
+      uint4 o = gv_philox(make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), it, (batch << 8) | j),
+                          (uint32_t)seed, (uint32_t)(seed >> 32));
+      if (4 * j + 0 < MAXD) r[4 * j + 0] = o.x;
+      if (4 * j + 1 < MAXD) r[4 * j + 1] = o.y;
+      if (4 * j + 2 < MAXD) r[4 * j + 2] = o.z;
+      if (4 * j + 3 < MAXD) r[4 * j + 3] = o.w;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Exact fixed-point helpers.
+// ----------------------------------------------------------------------------
+struct u128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ u128 add128(u128 a, u128 b) {
+  u128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+
+// Scale exponent of a nonnegative finite double bit pattern: the E with
+// value < 2^E <= 2*value (GV_EMPTY for zero).
+__device__ __forceinline__ int gv_scale_exp(unsigned long long bits) {
+  if (bits == 0) return GV_EMPTY;
+  const int ef = (int)(bits >> 52);
+  if (ef != 0) return ef - 1022;
+  return (64 - __clzll(bits)) - 1074;
+}
+
+// round(|x| * 2^(GV_FB - E)) as a 128-bit two's complement integer with the
+// sign of x.  Requires |x| <= 2^E.  Round half up on the magnitude.
+__device__ __forceinline__ u128 gv_to_fixed(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (b >> 63) != 0;
+  const int ef = (int)((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int e2;
+  if (ef == 0) {
+    e2 = -1074;
+  } else {
+    m |= 1ull << 52;
+    e2 = ef - 1075;
+  }
+  u128 v = {0ull, 0ull};
+  if (m != 0) {
+    const int s = e2 - E + GV_FB;
+    if (s >= 64) {
+      v.hi = m << (s - 64);
+    } else if (s > 0) {
+      v.lo = m << s;
+      v.hi = m >> (64 - s);
+    } else if (s == 0) {
+      v.lo = m;
+    } else if (s > -54) {
+      const int rs = -s;
+      v.lo = (m + (1ull << (rs - 1))) >> rs;
+    }
+  }
+  if (neg) {
+    v.lo = ~v.lo + 1ull;
+    v.hi = ~v.hi + (v.lo == 0 ? 1ull : 0ull);
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+__device__ __forceinline__ u128 warp_sum128(u128 v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    u128 o = {shfl_xor_u64(v.lo, m), shfl_xor_u64(v.hi, m)};
+    v = add128(v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    unsigned long long o = shfl_xor_u64(v, m);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// Host-side launchers (defined in the kernel translation units).
+// ----------------------------------------------------------------------------
+namespace gv {
+cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
+                                size_t smem, cudaStream_t s);
+cudaError_t launch_reduce(const GvReduceArgs& a, int ctas, cudaStream_t s);
+cudaError_t launch_setup(int integrand, const double* params, double* kconst, GvState* st,
+                         int nacc, unsigned long long* acc, cudaStream_t s);
+cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
+cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,
+                             unsigned long long ev0, long long n, int d, uint32_t* out,
+                             cudaStream_t s);
+}  // namespace gv
