@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark: VEGAS events/s on one GB300 (LO Drell-Yan, 4 dims, 100 bins,
+1e6 calls per iteration, FP32 integrand with FP64/exact accumulation).
+
+A step is one VEGAS iteration -- every step of the hot path: Philox uniforms,
+grid map, phase space and matrix element, the combination of all events and
+the grid refinement (Section 2.1) -- over 1e6 events.  Steps are timed with
+CUDA events on the library's launching stream (torch's current stream), the
+L2 cache is flushed between steps, and the whole timed region is bracketed by
+a barrier and a device synchronisation.  See ``--help`` for the options;
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NCALL = 1_000_000
+NDIM, NBINS = 4, 100
+METRIC = "VEGAS events/s (LO Drell-Yan, d=4, 100 bins, 1e6 calls/iteration)"
+UNIT = "events/s"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 floating-point operations per event of the FP32 Drell-Yan fill, counted
+# from the source: grid map 4 x (fma + fma) = 16; integrand 83 arithmetic
+# operations (fma counted as 2) + 8 transcendental calls (3 exp, 4 log, 1 sqrt)
+# counted as 1 each + 3 divisions counted as 1 each.
+FLOPS_PER_EVENT_FP32 = 16 + 83 + 8 + 3
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _fp32_peak_tflops():
+    """Dense FP32 peak from unit counts and the maximum SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, period_ms: int = 50):
+        self.index, self.period = index, period_ms
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        return self
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float):
+        sel = [r for t, r in self.rows if t0 <= t <= t1] or [r for _, r in self.rows[-3:]]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in sel for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(sel)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1503_06182_gb300 import vegas as v
+    from paper_1503_06182_gb300.workloads import DY, DY_PARAMS, SEED
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    seed = SEED + rank  # replicas draw independent events
+    K, W = args.steps, args.warmup
+
+    def make(precision):
+        g = v.Vegas(NDIM, NBINS, seed, precision=precision)
+        v.vegas_set_stream(g.h, stream.cuda_stream)
+        return g
+
+    def timed_steps(g, nsteps, flush_between=True):
+        """Device time (ms) of each of nsteps iterations, L2 flushed in between."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(nsteps)]
+        with torch.cuda.stream(stream):
+            for a, b in evs:
+                if flush_between:
+                    flush.fill_(1)
+                a.record(stream)
+                g.launch(NCALL, 1, DY, DY_PARAMS)
+                b.record(stream)
+        stream.synchronize()
+        res = g.fetch(1)
+        return [a.elapsed_time(b) for a, b in evs], res
+
+    sampler = ClockSampler(torch.cuda.current_device()).start() if rank == 0 else None
+    g32 = make("fp32")
+    # warm-up (also autotunes events per thread and captures the graph)
+    for _ in range(W):
+        g32.iterate(NCALL, 1, DY, DY_PARAMS)
+    barrier()
+    t_wall0 = time.time()
+    step_ms, _ = timed_steps(g32, K)
+    barrier()
+    t_wall1 = time.time()
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * K * NCALL / (tot_ms * 1e-3)
+
+    # end to end through the blocking C ABI: host params in, host results out
+    e2e_ms = []
+    p = np.asarray(DY_PARAMS, dtype=np.float64)
+    for _ in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        g32.iterate(NCALL, 1, DY, p)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_tot = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * K * NCALL / (e2e_tot * 1e-3)
+    t_wall2 = time.time()
+
+    # roofline of the dominant kernel (fill): library-side CUDA events on the
+    # same stream around every fill launch
+    v.vegas_set_option(g32.h, v.VEGAS_OPT_TIMING, 1)
+    kernels = (v.VEGAS_KERNEL_FILL, v.VEGAS_KERNEL_REDUCE, v.VEGAS_KERNEL_REFINE)
+    for kid in kernels:
+        v.vegas_kernel_time(g32.h, kid, reset=True)
+    for _ in range(max(K, 5)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        g32.iterate(NCALL, 1, DY, DY_PARAMS)
+    kavg = []
+    for kid in kernels:
+        ms, n = v.vegas_kernel_time(g32.h, kid)
+        kavg.append(ms / max(n, 1))
+    v.vegas_set_option(g32.h, v.VEGAS_OPT_TIMING, 0)
+    fill_avg = kavg[0]
+    achieved = FLOPS_PER_EVENT_FP32 * NCALL / (fill_avg * 1e-3) / 1e12
+    peak = _fp32_peak_tflops()
+
+    # plain FP64 path and equal-error comparison: one 10-iteration stage of each
+    # form from the same grid and seed (the same events)
+    g64 = make("fp64")
+    for _ in range(max(2, W // 2)):
+        g64.iterate(NCALL, 1, DY, DY_PARAMS)
+    k64 = max(3, min(K, 20))
+    ms64, _ = timed_steps(g64, k64)
+    value64 = world * NCALL / (sum(ms64) / k64 * 1e-3)
+    sig = {}
+    for prec in ("fp32", "fp64"):
+        g = v.Vegas(NDIM, NBINS, 4321, precision=prec)
+        try:
+            g.iterate(NCALL // 10, 5, DY, DY_PARAMS)  # warm-up stage (paper: 4 x 1,000)
+            I, e, c, _, _ = g.iterate(NCALL, 10, DY, DY_PARAMS)
+            sig[prec] = (I, e, c)
+        finally:
+            g.close()
+    t32 = tot_ms / world / K
+    t64 = sum(ms64) / k64
+    eff_ratio = (1.0 / (sig["fp32"][1] ** 2 * t32)) / (1.0 / (sig["fp64"][1] ** 2 * t64))
+    ept = v.vegas_get_ept(g32.h)
+    g32.close()
+    g64.close()
+
+    clocks = sampler.summary(t_wall0 - 0.1, t_wall2 + 0.1) if sampler else None
+    if sampler:
+        sampler.stop()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu_baseline) else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": tot_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": "drell_yan_lo_14tev_d4_n100_1e6calls", "integrand": "drell_yan",
+                   "ndim": NDIM, "nbins": NBINS, "ncall_per_step": NCALL, "itmx_per_step": 1,
+                   "precision": "fp32 integrand, fp64 Jacobian, exact integer sums",
+                   "seed": 1234, "events_per_thread": ept,
+                   "l2": "flushed between steps (256 MiB device write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 128,
+                "d2h_bytes_per_step": 176},
+        "gpu_launches": 3 * K,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "gv_fill_kernel<drell_yan, float>",
+                     "kernel_avg_ms": fill_avg, "reduce_avg_ms": kavg[1], "refine_avg_ms": kavg[2],
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "flops_per_event": FLOPS_PER_EVENT_FP32},
+        "fp64_path": {"value": value64, "unit": UNIT},
+        "equal_error": {"sigma_fp32": sig["fp32"][1], "sigma_fp64": sig["fp64"][1],
+                        "integral_fp32": sig["fp32"][0], "integral_fp64": sig["fp64"][0],
+                        "efficiency_ratio_fp32_over_fp64": eff_ratio},
+        "clocks": clocks,
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def _oracle_rate(seconds_target: float):
+    """The oracle as it stands on this host's cores on a bounded sample of
+    the same workload (whole 1e6-event iterations of the same config)."""
+    import oracle
+    from paper_1503_06182_gb300.workloads import DY, DY_PARAMS, SEED
+
+    oracle.build()
+    # calibrate with one iteration, then run a bounded number of iterations
+    t0 = time.perf_counter()
+    r = oracle.iterate(NDIM, NBINS, SEED, NCALL, 1, DY, DY_PARAMS)
+    t1 = time.perf_counter() - t0
+    n_it = max(1, min(200, int(seconds_target / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.iterate(NDIM, NBINS, SEED, NCALL, n_it, DY, DY_PARAMS, edges=r.edges,
+                   iteration=r.iteration)
+    dt = time.perf_counter() - t0
+    return n_it * NCALL / dt, n_it, dt, oracle.get_threads()
+
+
+def cpu_baseline(args):
+    rate, n_it, dt, cores = _oracle_rate(args.cpu_seconds)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_it} iterations x 1e6 events of the same workload (FP64), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, same config and metric;
+    each step one whole 1e6-event iteration."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1503_06182_gb300.workloads import DY, DY_PARAMS, SEED
+
+    oracle.build()
+    r = oracle.iterate(NDIM, NBINS, SEED, NCALL, max(1, args.warmup), DY, DY_PARAMS)
+    edges, it = r.edges, r.iteration
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.iterate(NDIM, NBINS, SEED, NCALL, 1, DY, DY_PARAMS, edges=edges, iteration=it)
+        times.append(time.perf_counter() - t0)
+        edges, it = r.edges, r.iteration
+    tot = sum(times)
+    value = args.steps * NCALL / tot
+    cores = oracle.get_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64",
+        "data": "synthetic",
+        "config": {"workload": "drell_yan_lo_14tev_d4_n100_1e6calls", "integrand": "drell_yan",
+                   "ndim": NDIM, "nbins": NBINS, "ncall_per_step": NCALL, "itmx_per_step": 1,
+                   "precision": "fp64 oracle (C + OpenMP), compensated sums"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} whole 1e6-event iterations"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gvegas", "reference"], default="gvegas")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="CPU work of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -72,8 +72,9 @@ extern "C" {
 #define VEGAS_OPT_BATCH_ID 7  /* Philox batch word of this context (default 0; < 2^24) */
 
 /* ---- kernel ids for vegas_kernel_time ---- */
-#define VEGAS_KERNEL_FILL 0
-#define VEGAS_KERNEL_REDUCE 1
+#define VEGAS_KERNEL_FILL 0   /* per-event kernel */
+#define VEGAS_KERNEL_REDUCE 1 /* combination of all events (and the iteration record) */
+#define VEGAS_KERNEL_REFINE 2 /* grid optimisation */
 
 typedef struct vegas_ctx vegas_ctx;
 typedef struct vegas_batch vegas_batch;
@@ -180,9 +181,9 @@ int vegas_rng_words(uint64_t seed, uint32_t iteration, uint32_t batch, int64_t f
  * d[a*nbins + i] = sum of w^2 over the events in bin i of axis a. */
 int vegas_last_sums(const vegas_ctx* ctx, double* sums);
 
-/* Accumulated device time of the fill or reduce kernels since the last
- * reset (VEGAS_OPT_TIMING = 1 only); reset != 0 clears the totals after
- * reading. */
+/* Accumulated device time of the VEGAS_KERNEL_* kernels since the last
+ * reset (VEGAS_OPT_TIMING = 1 only); reset != 0 clears that kernel's totals
+ * after reading. */
 int vegas_kernel_time(vegas_ctx* ctx, int kernel, double* total_ms, int64_t* launches, int reset);
 
 /* The events per thread the last stage used (autotuned or forced). */

@@ -4,10 +4,12 @@
 // iteration state, accumulators) and, unless the caller hands it one, the
 // workspace (tile partials, per-iteration records).  A stage of itmx
 // iterations (Section 2.1; the two-stage runs of Section 3.2) is enqueued as
-//   setup -> itmx x [fill -> reduce]
+//   itmx x [fill -> reduce -> refine]
 // and, by default, captured once into a CUDA graph that is replayed by later
-// calls with the same shape; the iteration counter, the parameters and the
-// grid are read from device memory, so a replay needs no re-capture.
+// calls with the same shape; the iteration counter, the derived integrand
+// constants and the grid are read from device memory, so a replay needs no
+// re-capture.  The constants are re-derived (one small kernel, outside the
+// graph) only when the integrand or its parameters change.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -131,6 +133,7 @@ struct vegas_ctx {
   unsigned long long* acc = nullptr;
   double* sums = nullptr;
   double* scratch = nullptr;
+  double* logtab = nullptr;
   int nacc_max = 0;
   // workspace
   void* ws = nullptr;
@@ -139,13 +142,16 @@ struct vegas_ctx {
   // pinned host staging for results
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  // derived constants currently on the device
+  int consts_ig = -1;
+  double consts_params[GV_MAXPARAMS] = {0};
   // last launch
   int last_itmx = 0, last_mode = 0, last_ept = 0;
   double* last_per_iter = nullptr;
   bool pending = false;
   std::vector<cudaEvent_t> pending_events;
-  double t_fill_ms = 0, t_reduce_ms = 0;
-  int64_t n_fill = 0, n_reduce = 0;
+  double t_ms[3] = {0, 0, 0};       // fill, reduce, refine
+  int64_t n_launch[3] = {0, 0, 0};
   std::vector<GraphEntry> graphs;
 };
 
@@ -231,29 +237,60 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   return a;
 }
 
-GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p) {
+GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   GvReduceArgs r;
   r.ndim = c->ndim;
   r.nbins = c->nbins;
   r.nch = p.nch;
   r.nacc = p.nacc;
   r.has_bins = p.mode == 0;
-  r.adapt = p.mode == 0 ? c->adapt : 0;
-  r.itmx = p.itmx;
+  r.k = k;
+  r.last = k == p.itmx - 1;
   r.mode = p.mode;
   r.ncall = p.ncall;
+  r.inv_c = 1.0 / (double)p.ncall;
+  r.inv_cm1 = 1.0 / (double)(p.ncall - 1);
+  r.inv_m1 = k > 0 ? 1.0 / (double)k : 0.0;
   r.n_tiles = p.n_tiles;
   r.tiles_per_cta = p.tiles_per_cta;
-  r.alpha = c->alpha;
   r.part = p.part;
   r.tileE = p.tileE;
   r.st = c->st;
   r.acc = c->acc;
   r.sums = c->sums;
   r.per_iter = p.per_iter;
+  r.inv_total = c->scratch + 4 * (size_t)c->ndim * (c->nbins + 1);
+  return r;
+}
+
+GvRefineArgs refine_args(const vegas_ctx* c) {
+  GvRefineArgs r;
+  r.ndim = c->ndim;
+  r.nbins = c->nbins;
+  r.alpha = c->alpha;
+  r.inv_nbins = 1.0 / (double)c->nbins;
+  r.logtab = c->logtab;
+  r.dsum = c->sums + 2;
+  r.inv_total = c->scratch + 4 * (size_t)c->ndim * (c->nbins + 1);
   r.grid = c->grid;
   r.scratch = c->scratch;
+  r.st = c->st;
   return r;
+}
+
+// Upload the parameters and re-derive the integrand constants if the
+// integrand or a parameter changed since the last derivation.
+int ensure_consts(vegas_ctx* c, int ig, const double* params, int np) {
+  double hp[GV_MAXPARAMS] = {0};
+  for (int i = 0; i < np && i < GV_MAXPARAMS - 1; ++i) hp[i] = params[i];
+  hp[GV_MAXPARAMS - 1] = (double)np;
+  if (c->consts_ig == ig && memcmp(hp, c->consts_params, sizeof hp) == 0) return VEGAS_OK;
+  // a pageable copy is staged before cudaMemcpyAsync returns
+  GV_TRY(cudaMemcpyAsync(c->params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream));
+  GV_TRY(gv::launch_consts(ig, c->params, c->kconst, c->stream));
+  c->consts_ig = ig;
+  memcpy(c->consts_params, hp, sizeof hp);
+  return VEGAS_OK;
 }
 
 cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept) {
@@ -309,6 +346,8 @@ int autotune(vegas_ctx* c, Plan& p) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   GV_TRY(cudaGetLastError());
+  // the trial launches touched the iteration invariants: restore them
+  GV_TRY(gv::launch_reset(c->st, p.nacc, c->acc, c->stream));
   p.ept = best_ept;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best_ept;
@@ -327,8 +366,9 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.nch = mode ? GV_MAXCH : 1;
   p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins;
   p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0).total;
-  p.tiles_per_cta = std::max(1, (int)((nt + 2LL * c->sm_count - 1) / (2LL * c->sm_count)));
-  p.reduce_ctas = (int)((nt + p.tiles_per_cta - 1) / p.tiles_per_cta);
+  int gx = 0, gy = 0;
+  gv::reduce_grid(p.n_tiles, p.nacc, &p.tiles_per_cta, &gx, &gy);
+  p.reduce_ctas = gx * gy;
   const size_t need = workspace_bytes(c->ndim, c->nbins, ncall, itmx, mode);
   int st = ensure_workspace(c, need);
   if (st) return st;
@@ -343,15 +383,18 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
 }
 
 int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool capture) {
-  GV_TRY(gv::launch_setup(p.ig, c->params, c->kconst, c->st, p.nacc, c->acc, c->stream));
-  const GvReduceArgs r = reduce_args(c, p);
   const unsigned flags = capture ? cudaEventRecordExternal : 0u;
+  const GvRefineArgs rf = refine_args(c);
+  const bool refine = p.mode == 0 && c->adapt;
+  if (refine) GV_TRY(gv::prepare_refine(c->ndim, c->nbins));
   for (int k = 0; k < p.itmx; ++k) {
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k], c->stream, flags));
     GV_TRY(launch_fill_plan(c, p, p.ept));
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
-    GV_TRY(gv::launch_reduce(r, p.reduce_ctas, c->stream));
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 1], c->stream, flags));
+    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), c->stream));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 2], c->stream, flags));
+    if (refine) GV_TRY(gv::launch_refine(rf, c->stream));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 3], c->stream, flags));
   }
   return VEGAS_OK;
 }
@@ -391,14 +434,9 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   Plan p;
   st = make_plan(c, ncall, itmx, ig, mode, p);
   if (st) return st;
-  // parameters: a pageable copy is staged before cudaMemcpyAsync returns; the
-  // count rides in the last slot
-  double hp[GV_MAXPARAMS] = {0};
-  for (int i = 0; i < np && i < GV_MAXPARAMS - 1; ++i) hp[i] = params[i];
-  hp[GV_MAXPARAMS - 1] = (double)np;
-  GV_TRY(cudaMemcpyAsync(c->params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream));
+  st = ensure_consts(c, ig, params, np);
+  if (st) return st;
   if (p.ept == 0) {
-    GV_TRY(gv::launch_setup(p.ig, c->params, c->kconst, c->st, p.nacc, c->acc, c->stream));
     st = autotune(c, p);
     if (st) return st;
   }
@@ -417,7 +455,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
         if (c->graphs.size() >= 16) drop_oldest_entry(c);
         GraphEntry g;
         g.key = key;
-        st = new_events(g.events, 3 * (size_t)itmx);
+        st = new_events(g.events, 4 * (size_t)itmx);
         if (st) return st;
         c->graphs.push_back(g);
         ge = &c->graphs.back();
@@ -441,7 +479,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
     GraphEntry g;
     g.key = key;
     if (c->timing) {
-      st = new_events(g.events, 3 * (size_t)itmx);
+      st = new_events(g.events, 4 * (size_t)itmx);
       if (st) return st;
     }
     cudaGraph_t graph;
@@ -483,18 +521,14 @@ int fetch_stage(vegas_ctx* c, GvState* hs, std::vector<double>* per_iter) {
   memcpy(hs, pin, sizeof(GvState));
   if (per_iter) per_iter->assign(pin_rec, pin_rec + nrec);
   if (!c->pending_events.empty()) {
-    for (size_t k = 0; k + 2 < c->pending_events.size(); k += 3) {
-      float a = 0.f, b = 0.f;
-      if (cudaEventElapsedTime(&a, c->pending_events[k], c->pending_events[k + 1]) ==
-          cudaSuccess) {
-        c->t_fill_ms += a;
-        c->n_fill += 1;
-      }
-      if (cudaEventElapsedTime(&b, c->pending_events[k + 1], c->pending_events[k + 2]) ==
-          cudaSuccess) {
-        c->t_reduce_ms += b;
-        c->n_reduce += 1;
-      }
+    for (size_t k = 0; k + 3 < c->pending_events.size(); k += 4) {
+      float t[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < 3; ++q)
+        if (cudaEventElapsedTime(&t[q], c->pending_events[k + q], c->pending_events[k + q + 1]) ==
+            cudaSuccess) {
+          c->t_ms[q] += t[q];
+          c->n_launch[q] += 1;
+        }
     }
     cudaGetLastError();
     c->pending_events.clear();
@@ -585,11 +619,13 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   const size_t o_k = off;
   off = align256(off + GV_NCONST * 8);
   const size_t o_acc = off;
-  off = align256(off + (size_t)c->nacc_max * 3 * 8);
+  off = align256(off + (size_t)c->nacc_max * 4 * 8);
+  const size_t o_log = off;
+  off = align256(off + 258 * 8);
   const size_t o_sums = off;
   off = align256(off + (size_t)c->nacc_max * 8);
   const size_t o_scr = off;
-  off = align256(off + (size_t)3 * ndim * (nbins + 1) * 8);
+  off = align256(off + ((size_t)4 * ndim * (nbins + 1) + GV_MAXD) * 8);
   if (cudaMalloc(&c->fixed, off) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(c->stream);
@@ -604,8 +640,32 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   c->acc = (unsigned long long*)(b + o_acc);
   c->sums = (double*)(b + o_sums);
   c->scratch = (double*)(b + o_scr);
+  c->logtab = (double*)(b + o_log);
   int st = VEGAS_OK;
-  if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess) st = VEGAS_ECUDA;
+  if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess ||
+      gv::launch_reset(c->st, c->nacc_max, c->acc, c->stream) != cudaSuccess)
+    st = VEGAS_ECUDA;
+  if (!st) {
+    // table of the device log: R_j ~ 1/c_j at the centre of each 1/128-wide
+    // interval of [1,2), L_j = -ln R_j, then ln 2 as a 42-bit head and a tail
+    static double tab[258];
+    static std::once_flag once;
+    std::call_once(once, [] {
+      for (int j = 0; j < 128; ++j) {
+        const double cj = 1.0 + (j + 0.5) / 128.0;
+        const double R = 1.0 / cj;
+        tab[2 * j] = R;
+        tab[2 * j + 1] = (double)(-logl((long double)R));
+      }
+      const long double ln2 = logl(2.0L);
+      const double hi = std::ldexp(std::floor(std::ldexp((double)ln2, 42)), -42);
+      tab[256] = hi;
+      tab[257] = (double)(ln2 - (long double)hi);
+    });
+    if (cudaMemcpyAsync(c->logtab, tab, sizeof tab, cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+      st = VEGAS_ECUDA;
+  }
   if (!st) {
     std::vector<double> e((size_t)ndim * (nbins + 1));
     for (int a = 0; a < ndim; ++a)
@@ -832,9 +892,6 @@ int vegas_eval_events(vegas_ctx* c, int id, const double* params, int np, uint32
   if (st) return st;
   if (n == 0) return VEGAS_OK;
   GV_TRY(cudaStreamSynchronize(c->stream));
-  double hp[GV_MAXPARAMS] = {0};
-  for (int i = 0; i < np; ++i) hp[i] = params[i];
-  hp[GV_MAXPARAMS - 1] = (double)np;
   void* dmem = nullptr;
   const size_t bytes = (size_t)n * (8 + 8 + 4 * c->ndim) + 64;
   if (cudaMalloc(&dmem, bytes) != cudaSuccess) {
@@ -844,18 +901,12 @@ int vegas_eval_events(vegas_ctx* c, int id, const double* params, int np, uint32
   long long* dev = (long long*)dmem;
   double* dw = (double*)(dev + n);
   int* db = (int*)(dw + n);
-  st = VEGAS_OK;
-  cudaError_t e = cudaMemcpyAsync(c->params, hp, sizeof hp, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dev, events, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
-  // derive the constants without disturbing the iteration state: setup on a
-  // scratch state in the workspace-free fixed area is not needed because
-  // setup only resets stage bookkeeping, which no stage is using now
-  GvState saved;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&saved, c->st, sizeof saved, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e == cudaSuccess)
-    e = gv::launch_setup(id, c->params, c->kconst, c->st, 0, c->acc, c->stream);
+  st = ensure_consts(c, id, params, np);
+  if (st) {
+    cudaFree(dmem);
+    return st;
+  }
+  cudaError_t e = cudaMemcpyAsync(dev, events, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
     GvFillArgs a;
     memset(&a, 0, sizeof a);
@@ -872,8 +923,6 @@ int vegas_eval_events(vegas_ctx* c, int id, const double* params, int np, uint32
       default: e = gv::launch_fill_ee3j_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
     }
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->st, &saved, sizeof saved, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bins, db, (size_t)n * 4 * c->ndim, cudaMemcpyDeviceToHost, c->stream);
@@ -917,12 +966,12 @@ int vegas_last_sums(const vegas_ctx* c, double* sums) {
 }
 
 int vegas_kernel_time(vegas_ctx* c, int kernel, double* total_ms, int64_t* launches, int reset) {
-  if (!c || (kernel != VEGAS_KERNEL_FILL && kernel != VEGAS_KERNEL_REDUCE)) return VEGAS_EINVAL;
-  if (total_ms) *total_ms = kernel == VEGAS_KERNEL_FILL ? c->t_fill_ms : c->t_reduce_ms;
-  if (launches) *launches = kernel == VEGAS_KERNEL_FILL ? c->n_fill : c->n_reduce;
+  if (!c || kernel < VEGAS_KERNEL_FILL || kernel > VEGAS_KERNEL_REFINE) return VEGAS_EINVAL;
+  if (total_ms) *total_ms = c->t_ms[kernel];
+  if (launches) *launches = c->n_launch[kernel];
   if (reset) {
-    c->t_fill_ms = c->t_reduce_ms = 0.0;
-    c->n_fill = c->n_reduce = 0;
+    c->t_ms[kernel] = 0.0;
+    c->n_launch[kernel] = 0;
   }
   return VEGAS_OK;
 }

@@ -34,13 +34,16 @@
 enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2 };
 
 // Device-side state of one integration (one context or one batch member).
+// E, done, done_refine, nonfinite_iter and the accumulators return to their
+// reset values at the end of every iteration.
 struct GvState {
-  unsigned long long it;         // global iteration counter (Philox counter word)
-  unsigned long long nonfinite;  // non-finite weights seen in this stage
-  int m;                         // iterations done in this stage
-  int done;                      // reduce CTAs finished (last-block ticket)
-  int status;                    // device error word (0 = ok)
-  int E[GV_MAXCH];               // per-channel iteration scale (atomicMax)
+  unsigned long long it;              // global iteration counter (Philox counter word)
+  unsigned long long nonfinite_iter;  // non-finite weights of the running iteration
+  unsigned long long nonfinite;       // non-finite weights of the stage
+  int done;                           // reduce CTAs finished (last-block ticket)
+  int done_refine;                    // refine CTAs finished (last-block ticket)
+  int status;                         // device error word (0 = ok)
+  int E[GV_MAXCH];                    // per-channel iteration scale (atomicMax)
   int pad;
   double integral, error, chi2;
   double grad[GV_NGRAD], grad_err[GV_NGRAD];
@@ -77,18 +80,29 @@ struct GvFillArgs {
 
 // Arguments of the reduce/finalize kernel.
 struct GvReduceArgs {
-  int ndim, nbins, nch, nacc, has_bins, adapt, itmx, mode;  // mode 0 forward, 1 adjoint
+  int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
   long long ncall;
+  double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration
   int n_tiles, tiles_per_cta;
-  double alpha;
   const ulonglong2* part;
   const int* tileE;
   GvState* st;
-  unsigned long long* acc;       // [nacc][3] 192-bit accumulators
+  unsigned long long* acc;       // [nacc][4] accumulator limbs (3 used)
   double* sums;                  // [nacc] FP64 sums of the last iteration
   double* per_iter;              // forward: [itmx][2]; adjoint: [itmx][2 + 2*NGRAD]
+  double* inv_total;             // [ndim] 1 / (sum of the smoothed bin sums), 0 if none
+};
+
+// Arguments of the refine kernel.
+struct GvRefineArgs {
+  int ndim, nbins;
+  double alpha, inv_nbins;
+  const double* logtab;          // table of the FP64 log (see gv_reduce.cu)
+  const double* dsum;            // [ndim][nbins] bin sums of w^2
+  const double* inv_total;       // [ndim] from the reduce kernel
   double* grid;                  // grid pack (refined in place)
-  double* scratch;               // refine scratch: 3 * d * (N+1) doubles
+  double* scratch;               // 4 * d * (N+1) doubles
+  GvState* st;
 };
 
 // ----------------------------------------------------------------------------
@@ -152,40 +166,83 @@ __device__ __forceinline__ int gv_scale_exp(unsigned long long bits) {
   return (64 - __clzll(bits)) - 1074;
 }
 
-// round(|x| * 2^(GV_FB - E)) as a 128-bit two's complement integer with the
-// sign of x.  Requires |x| <= 2^E.  Round half up on the magnitude.
-__device__ __forceinline__ u128 gv_to_fixed(double x, int E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const bool neg = (b >> 63) != 0;
-  const int ef = (int)((b >> 52) & 0x7ff);
-  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+// A finite double as sign, integer mantissa m and exponent e2 (|x| = m 2^e2).
+struct GvDecoded {
+  unsigned long long m;
   int e2;
+  bool neg;
+};
+
+__device__ __forceinline__ GvDecoded gv_decode(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  GvDecoded r;
+  r.neg = (b >> 63) != 0;
+  const int ef = (int)((b >> 52) & 0x7ff);
+  r.m = b & 0xFFFFFFFFFFFFFull;
   if (ef == 0) {
-    e2 = -1074;
+    r.e2 = -1074;
   } else {
-    m |= 1ull << 52;
-    e2 = ef - 1075;
+    r.m |= 1ull << 52;
+    r.e2 = ef - 1075;
   }
-  u128 v = {0ull, 0ull};
-  if (m != 0) {
-    const int s = e2 - E + GV_FB;
+  return r;
+}
+
+// round(m * 2^s) for a 128-bit m = (hi, lo), s of either sign (round half up).
+__device__ __forceinline__ u128 gv_shift_round(u128 v, int s) {
+  if (s > 0) {
     if (s >= 64) {
-      v.hi = m << (s - 64);
-    } else if (s > 0) {
-      v.lo = m << s;
-      v.hi = m >> (64 - s);
-    } else if (s == 0) {
-      v.lo = m;
-    } else if (s > -54) {
-      const int rs = -s;
-      v.lo = (m + (1ull << (rs - 1))) >> rs;
+      v.hi = v.lo << (s - 64);
+      v.lo = 0ull;
+    } else {
+      v.hi = (v.hi << s) | (v.lo >> (64 - s));
+      v.lo <<= s;
     }
+    return v;
   }
+  if (s == 0) return v;
+  const int rs = -s;
+  if (rs > 127) return {0ull, 0ull};
+  // add half a unit of the last kept bit, then shift right
+  u128 h;
+  if (rs - 1 >= 64) {
+    h.lo = 0ull;
+    h.hi = 1ull << (rs - 1 - 64);
+  } else {
+    h.lo = 1ull << (rs - 1);
+    h.hi = 0ull;
+  }
+  v = add128(v, h);
+  if (rs >= 64) {
+    v.lo = v.hi >> (rs - 64);
+    v.hi = 0ull;
+  } else {
+    v.lo = (v.lo >> rs) | (v.hi << (64 - rs));
+    v.hi >>= rs;
+  }
+  return v;
+}
+
+__device__ __forceinline__ u128 gv_negate_if(u128 v, bool neg) {
   if (neg) {
     v.lo = ~v.lo + 1ull;
     v.hi = ~v.hi + (v.lo == 0 ? 1ull : 0ull);
   }
   return v;
+}
+
+// round(x 2^(GV_FB - E)) from a decoded x with |x| < 2^E, two's complement.
+__device__ __forceinline__ u128 gv_fixed_dec(const GvDecoded& d, int E) {
+  u128 v = {d.m, 0ull};
+  v = gv_shift_round(v, d.e2 - E + GV_FB);
+  return gv_negate_if(v, d.neg);
+}
+
+// round(x^2 2^(GV_FB - 2E)), with the square formed exactly in integers
+// (m^2 has at most 106 bits): the sum of squares is then exact too.
+__device__ __forceinline__ u128 gv_square_fixed_dec(const GvDecoded& d, int E) {
+  u128 v = {d.m * d.m, __umul64hi(d.m, d.m)};
+  return gv_shift_round(v, 2 * d.e2 - 2 * E + GV_FB);
 }
 
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
@@ -216,9 +273,13 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 namespace gv {
 cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
                                 size_t smem, cudaStream_t s);
-cudaError_t launch_reduce(const GvReduceArgs& a, int ctas, cudaStream_t s);
-cudaError_t launch_setup(int integrand, const double* params, double* kconst, GvState* st,
-                         int nacc, unsigned long long* acc, cudaStream_t s);
+void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
+cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s);
+cudaError_t prepare_refine(int d, int N);
+cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s);
+size_t refine_smem_bytes(int d, int N);
+cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);
+cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, cudaStream_t s);
 cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
 cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,
                              unsigned long long ev0, long long n, int d, uint32_t* out,

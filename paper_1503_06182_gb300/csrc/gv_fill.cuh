@@ -3,14 +3,20 @@
 // One CTA evaluates one tile of GV_TILE consecutive events (Section 2.1: each
 // event generated and evaluated independently), with EPT events per thread:
 //   pass 1: Philox words -> bins and in-bin positions -> x on the adaptive grid
-//           (edges and Jacobian factors staged in shared memory) -> g(x)
-//           -> w = J g (J in FP64 always); the bins go to shared memory;
+//           ((edge, width) pairs and Jacobian factors staged in shared memory)
+//           -> g(x) -> w = J g (J in FP64 always); the bins stay in registers
+//           (d <= 4) or go to shared memory;
 //   tile scale: block max of |w| (order-free) -> E_t;
-//   pass 2: w and w^2 rounded once to fixed point at the tile scale; sums in
-//           128-bit integer registers (warp-shuffle + block reduction) and
-//           per-bin sums of w^2 as 64-bit integer shared-memory atomics.
+//   pass 2: w and the exact square w^2 rounded once to fixed point at the tile
+//           scale; sums in 128-bit integer registers (warp shuffle + block
+//           reduction); per-bin sums of w^2 at 88 bits below the tile's max^2
+//           as four 22-bit limbs in 32-bit shared-memory atomics (32-bit
+//           shared atomics run several times faster than 64-bit ones here,
+//           and 10 bits of headroom cover the 1024 events of a tile).
 // Integer sums are order-free, so the tile's result is the same for every
-// block size / events-per-thread choice.
+// block size / events-per-thread choice.  Apart from the Jacobian product and
+// w = J g, the bookkeeping runs on the integer pipes: the FP64 pipe of this
+// chip is a small fraction of its FP32 throughput.
 #pragma once
 #include "gv_integrands.cuh"
 
@@ -41,57 +47,79 @@ __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
   }
 }
 
+// One bin of one axis as staged in shared memory.
+struct __align__(16) GvBin32 {
+  float e, w;     // edge and width in FP32
+  double jac;     // N * (e_{i+1} - e_i) in FP64
+};
+struct __align__(16) GvBin64 {
+  double e, w;
+};
+template <typename Real>
+struct GvPair;
+template <>
+struct GvPair<float> {
+  using T = GvBin32;
+};
+template <>
+struct GvPair<double> {
+  using T = GvBin64;
+};
+
 // Shared-memory layout of the fill kernel (bytes), 16-byte aligned pieces:
-//   hist   [d*N][2] u64     per-bin (low 53 bits, high bits) sums
-//   jac    [d*N]    f64     Jacobian factor N*(e_{i+1}-e_i)
-//   edges  [d*(N+1)] Real
-//   width  [d*N]    Real
-//   bins   [d][GV_TILE] u16
+//   hist [4][d*N] u32     per-bin sums of w^2 in four 22-bit limbs (forward only)
+//   jac  [d*N]    f64     Jacobian factor N*(e_{i+1}-e_i) (FP64 form only)
+//   ew   [d*N]    GvBin32 (e, w, jac) in the FP32 form, GvBin64 (e, w) in FP64
+//   bins [d][GV_TILE] u16 (forward with d > 4 only)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 struct GvFillSmem {
-  size_t hist, jac, edges, width, bins, total;
-  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool with_bins) {
+  size_t hist, jac, ew, bins, total;
+  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward) {
     const size_t dN = (size_t)d * N;
     hist = 0;
-    jac = gv_align16(hist + (with_bins ? dN * 16 : 0));
-    edges = gv_align16(jac + dN * 8);
-    width = gv_align16(edges + (size_t)d * (N + 1) * real_bytes);
-    bins = gv_align16(width + dN * real_bytes);
-    total = gv_align16(bins + (with_bins ? (size_t)d * GV_TILE * 2 : 0));
+    jac = gv_align16(hist + (forward ? dN * 16 : 0));
+    ew = gv_align16(jac + (real_bytes == 8 ? dN * 8 : 0));
+    bins = gv_align16(ew + dN * 16);
+    total = gv_align16(bins + ((forward && d > 4) ? (size_t)d * GV_TILE * 2 : 0));
   }
 };
 
 // Stage the grid of one integration into shared memory.
 template <typename Real>
 __device__ __forceinline__ void gv_stage_grid(const double* grid, int d, int N, double* s_jac,
-                                              Real* s_e, Real* s_w, int tid, int nthr) {
+                                              typename GvPair<Real>::T* s_ew, int tid,
+                                              int nthr) {
   const GvGridLayout L{d, N};
   const int dN = d * N;
   const float* g32 = reinterpret_cast<const float*>(grid + L.off_f32_base());
   for (int k = tid; k < dN; k += nthr) {
-    s_jac[k] = grid[L.off_jac() + k];
-    if constexpr (sizeof(Real) == 4)
-      s_w[k] = g32[(size_t)d * (N + 1) + k];
-    else
-      s_w[k] = grid[L.off_wd64() + k];
-  }
-  for (int k = tid; k < d * (N + 1); k += nthr) {
-    if constexpr (sizeof(Real) == 4)
-      s_e[k] = g32[k];
-    else
-      s_e[k] = grid[L.off_e64() + k];
+    const int a = k / N, i = k - a * N;
+    if constexpr (sizeof(Real) == 4) {
+      GvBin32 b;
+      b.e = g32[a * (N + 1) + i];
+      b.w = g32[(size_t)d * (N + 1) + k];
+      b.jac = grid[L.off_jac() + k];
+      s_ew[k] = b;
+    } else {
+      s_jac[k] = grid[L.off_jac() + k];
+      GvBin64 b;
+      b.e = grid[L.off_e64() + a * (N + 1) + i];
+      b.w = grid[L.off_wd64() + k];
+      s_ew[k] = b;
+    }
   }
 }
 
-// Map one event's words through the grid: x, bins (to shared memory) and the
-// FP64 Jacobian.  FP64: x = e_i + f*(e_{i+1}-e_i) with f = (lo + 1/2) 2^-32,
-// rounded as written; FP32: the same with FP32 edges and one fma.
+// Map one event's words through the grid: x, bins and the FP64 Jacobian.
+// FP64: x = e_i + f*(e_{i+1}-e_i) with f = (lo + 1/2) 2^-32, rounded as
+// written; FP32: the same with FP32 edges and one fma.  The Jacobian product
+// starts from the first factor (J = 1 * f0 * f1 ... exactly).
 template <typename Real, int MAXD>
 __device__ __forceinline__ double gv_map_event(const uint32_t (&r)[MAXD], int d, int N,
-                                               const double* s_jac, const Real* s_e,
-                                               const Real* s_w, Real (&x)[MAXD],
-                                               unsigned short* s_bin, int local) {
+                                               const double* s_jac,
+                                               const typename GvPair<Real>::T* s_ew,
+                                               Real (&x)[MAXD], int (&bin)[MAXD]) {
   double J = 1.0;
 #pragma unroll
   for (int a = 0; a < MAXD; ++a) {
@@ -99,15 +127,19 @@ __device__ __forceinline__ double gv_map_event(const uint32_t (&r)[MAXD], int d,
       const unsigned long long v = (unsigned long long)r[a] * (unsigned)N;
       const int i = (int)(v >> 32);
       const uint32_t lo = (uint32_t)v;
+      const auto ew = s_ew[a * N + i];
+      double jf;
       if constexpr (sizeof(Real) == 4) {
         const float f = fmaf(__uint2float_rn(lo), 0x1p-32f, 0x1p-33f);
-        x[a] = fmaf(f, s_w[a * N + i], s_e[a * (N + 1) + i]);
+        x[a] = fmaf(f, ew.w, ew.e);
+        jf = ew.jac;
       } else {
         const double f = ((double)lo + 0.5) * 0x1p-32;
-        x[a] = __dadd_rn(s_e[a * (N + 1) + i], __dmul_rn(f, s_w[a * N + i]));
+        x[a] = __dadd_rn(ew.e, __dmul_rn(f, ew.w));
+        jf = s_jac[a * N + i];
       }
-      J = __dmul_rn(J, s_jac[a * N + i]);
-      if (s_bin) s_bin[a * GV_TILE + local] = (unsigned short)i;
+      J = (a == 0) ? jf : __dmul_rn(J, jf);
+      bin[a] = i;
     }
   }
   return J;
@@ -141,6 +173,63 @@ __device__ __forceinline__ u128 gv_block_sum128(u128 v, u128* scratch) {
   return s;
 }
 
+// Bins of one event between the two passes: packed u16 pairs in registers for
+// d <= 4, shared memory otherwise.
+template <int MAXD>
+struct GvBinStore {
+  static constexpr bool REG = MAXD <= 4;
+  uint32_t q[REG ? 2 : 1];
+  __device__ __forceinline__ void put(const int (&bin)[MAXD], int d, unsigned short* s_bin,
+                                      int local) {
+    if constexpr (REG) {
+      q[0] = (uint32_t)bin[0] | ((MAXD > 1 && d > 1 ? (uint32_t)bin[1] : 0u) << 16);
+      q[1] = (MAXD > 2 && d > 2 ? (uint32_t)bin[2] : 0u) |
+             ((MAXD > 3 && d > 3 ? (uint32_t)bin[3] : 0u) << 16);
+    } else {
+#pragma unroll
+      for (int a = 0; a < MAXD; ++a)
+        if (a < d) s_bin[a * GV_TILE + local] = (unsigned short)bin[a];
+    }
+  }
+  __device__ __forceinline__ int get(int a, const unsigned short* s_bin, int local) const {
+    if constexpr (REG)
+      return (int)((q[a >> 1] >> ((a & 1) * 16)) & 0xFFFFu);
+    else
+      return s_bin[a * GV_TILE + local];
+  }
+};
+
+// A float widened to double by integer operations (exact; the FP64 pipe of
+// this chip is scarce).  Zero, subnormal and non-finite inputs are handled.
+__device__ __forceinline__ double gv_widen(float g) {
+  const unsigned u = __float_as_uint(g);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned ef = (u >> 23) & 0xFFu;
+  unsigned long long m = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (ef == 0xFFu) {
+    bits = sign | 0x7FF0000000000000ull | (m << 29);
+  } else if (ef != 0u) {
+    bits = sign | ((unsigned long long)(ef + 896u) << 52) | (m << 29);
+  } else if (m == 0ull) {
+    bits = sign;
+  } else {  // subnormal float m 2^-149, leading one at bit p = 23 - lz
+    const int lz = __clzll((long long)m) - 40;
+    m = (m << lz) & 0x7FFFFFull;
+    bits = sign | ((unsigned long long)(897 - lz) << 52) | (m << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double gv_widen(double g) { return g; }
+
+// |x| bits of a double, and its finiteness, on the integer pipes.
+__device__ __forceinline__ unsigned long long gv_abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
+  return absbits < 0x7FF0000000000000ull;
+}
+
 // ---------------------------------------------------------------------------
 // Forward fill: channel 0 = w, with per-bin sums of w^2.
 // ---------------------------------------------------------------------------
@@ -149,20 +238,20 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
+  using Pair = typename GvPair<Real>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins, dN = d * N;
   const GvFillSmem lay(d, N, (int)sizeof(Real), true);
-  unsigned long long* hist = reinterpret_cast<unsigned long long*>(smem + lay.hist);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);  // [4][dN]
   double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
-  Real* s_e = reinterpret_cast<Real*>(smem + lay.edges);
-  Real* s_w = reinterpret_cast<Real*>(smem + lay.width);
+  Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
   unsigned short* s_bin = reinterpret_cast<unsigned short*>(smem + lay.bins);
   const int tid = threadIdx.x;
 
-  for (int k = tid; k < 2 * dN; k += B) hist[k] = 0ull;
-  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_e, s_w, tid, B);
+  for (int k = tid; k < 4 * dN; k += B) hist[k] = 0u;
+  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
   const uint32_t it = (uint32_t)a.st->it;
@@ -171,6 +260,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   const long long tile = blockIdx.x;
   const long long tile0 = tile * GV_TILE;
   double w[EPT];
+  GvBinStore<MAXD> bs[EPT];
   unsigned long long mx = 0ull;
   unsigned long long nbad = 0ull;
 #pragma unroll
@@ -182,16 +272,18 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       uint32_t r[MAXD];
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
       Real x[MAXD];
-      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_e, s_w, x, s_bin, local);
+      int bin[MAXD];
+      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
+      bs[k].put(bin, d, s_bin, local);
       const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
-      double wv = __dmul_rn(J, (double)g);
-      if (!isfinite(wv)) {
-        ++nbad;
-        wv = 0.0;
+      const double wv = __dmul_rn(J, gv_widen(g));
+      const unsigned long long ab = gv_abs_bits(wv);
+      if (gv_finite_bits(ab)) {
+        w[k] = wv;
+        mx = ab > mx ? ab : mx;
+      } else {
+        ++nbad;  // counted, contributes nothing
       }
-      w[k] = wv;
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(wv));
-      mx = bits > mx ? bits : mx;
     }
   }
   const unsigned long long M = gv_block_max<NW>(mx, red_u64);
@@ -201,21 +293,26 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   if (E != GV_EMPTY) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      if (w[k] != 0.0) {
+      if (gv_abs_bits(w[k]) != 0ull) {
         const int local = k * B + tid;
-        const u128 v1 = gv_to_fixed(w[k], E);
-        const u128 v2 = gv_to_fixed(__dmul_rn(w[k], w[k]), 2 * E);
-        s1 = add128(s1, v1);
+        const GvDecoded dw = gv_decode(w[k]);
+        const u128 v2 = gv_square_fixed_dec(dw, E);
+        s1 = add128(s1, gv_fixed_dec(dw, E));
         s2 = add128(s2, v2);
-        const unsigned long long lo53 = v2.lo & 0x1FFFFFFFFFFFFFull;
-        const unsigned long long hi = (v2.lo >> 53) | (v2.hi << 11);
+        // bins: round(v2 / 2^8), an 88-bit value, as four 22-bit limbs
+        const u128 vb = gv_shift_round(v2, -8);
+        const unsigned l0 = (unsigned)(vb.lo & 0x3FFFFFull);
+        const unsigned l1 = (unsigned)((vb.lo >> 22) & 0x3FFFFFull);
+        const unsigned l2 = (unsigned)(((vb.lo >> 44) | (vb.hi << 20)) & 0x3FFFFFull);
+        const unsigned l3 = (unsigned)((vb.hi >> 2) & 0x3FFFFFull);
 #pragma unroll
         for (int ax = 0; ax < MAXD; ++ax) {
           if (ax < d) {
-            const int i = s_bin[ax * GV_TILE + local];
-            unsigned long long* h = hist + 2 * (ax * N + i);
-            atomicAdd(h, lo53);
-            if (hi) atomicAdd(h + 1, hi);
+            const int bi = ax * N + bs[k].get(ax, s_bin, local);
+            if (l0) atomicAdd(hist + bi, l0);
+            if (l1) atomicAdd(hist + dN + bi, l1);
+            if (l2) atomicAdd(hist + 2 * dN + bi, l2);
+            if (l3) atomicAdd(hist + 3 * dN + bi, l3);
           }
         }
       }
@@ -230,12 +327,16 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     a.tileE[tile] = E;
     if (E != GV_EMPTY) atomicMax(&a.st->E[0], E);
   }
-  if (nbad) atomicAdd(&a.st->nonfinite, nbad);
+  if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
   for (int k = tid; k < dN; k += B) {
-    const unsigned long long lo = hist[2 * k], hi = hist[2 * k + 1];
-    u128 v;
-    v.lo = lo + (hi << 53);
-    v.hi = (hi >> 11) + (v.lo < lo ? 1ull : 0ull);
+    // (l0 + l1 2^22 + l2 2^44 + l3 2^66) 2^8 at the scale of the sum of w^2
+    const unsigned long long l0 = hist[k], l1 = hist[dN + k], l2 = hist[2 * dN + k],
+                             l3 = hist[3 * dN + k];
+    u128 v = {l0, 0ull};
+    v = add128(v, u128{l1 << 22, 0ull});
+    v = add128(v, u128{l2 << 44, l2 >> 20});
+    v = add128(v, u128{0ull, l3 << 2});
+    v = gv_shift_round(v, 8);
     out[2 + k] = make_ulonglong2(v.lo, v.hi);
   }
 }
@@ -250,16 +351,16 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
   constexpr int NCH = GV_MAXCH;
+  using Pair = typename GvPair<Real>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
   const GvFillSmem lay(d, N, (int)sizeof(Real), false);
   double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
-  Real* s_e = reinterpret_cast<Real*>(smem + lay.edges);
-  Real* s_w = reinterpret_cast<Real*>(smem + lay.width);
+  Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
   const int tid = threadIdx.x;
-  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_e, s_w, tid, B);
+  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
   GvConst<Real, 22> K;
   K.load(a.kconst);
   const uint32_t it = (uint32_t)a.st->it;
@@ -274,30 +375,29 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   unsigned long long nbad = 0ull;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int local = k * B + tid;
-    const long long ev = tile0 + local;
+    const long long ev = tile0 + k * B + tid;
 #pragma unroll
     for (int c = 0; c < NCH; ++c) v[k][c] = 0.0;
     if (ev < a.ncall) {
       uint32_t r[MAXD];
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
       Real x[MAXD];
-      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_e, s_w, x, nullptr, local);
+      int bin[MAXD];
+      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
       Real gr[GV_NGRAD];
       const Real g = gv_drell_yan<Real, true>(x, K, gr);
       double vals[NCH];
-      vals[0] = __dmul_rn(J, (double)g);
+      vals[0] = __dmul_rn(J, gv_widen(g));
 #pragma unroll
-      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = __dmul_rn(J, (double)gr[p]);
+      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = __dmul_rn(J, gv_widen(gr[p]));
       bool finite = true;
 #pragma unroll
-      for (int c = 0; c < NCH; ++c) finite &= (bool)isfinite(vals[c]);
+      for (int c = 0; c < NCH; ++c) finite &= gv_finite_bits(gv_abs_bits(vals[c]));
       if (!finite) ++nbad;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         v[k][c] = finite ? vals[c] : 0.0;
-        const unsigned long long bits =
-            (unsigned long long)__double_as_longlong(fabs(v[k][c]));
+        const unsigned long long bits = gv_abs_bits(v[k][c]);
         mx[c] = bits > mx[c] ? bits : mx[c];
       }
     }
@@ -311,9 +411,10 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     if (E != GV_EMPTY) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        if (v[k][c] != 0.0) {
-          s1 = add128(s1, gv_to_fixed(v[k][c], E));
-          s2 = add128(s2, gv_to_fixed(__dmul_rn(v[k][c], v[k][c]), 2 * E));
+        if (gv_abs_bits(v[k][c]) != 0ull) {
+          const GvDecoded dv = gv_decode(v[k][c]);
+          s1 = add128(s1, gv_fixed_dec(dv, E));
+          s2 = add128(s2, gv_square_fixed_dec(dv, E));
         }
       }
     }
@@ -326,11 +427,11 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       if (E != GV_EMPTY) atomicMax(&a.st->E[c], E);
     }
   }
-  if (nbad) atomicAdd(&a.st->nonfinite, nbad);
+  if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
 }
 
 // Single-event diagnostics (no shared memory): weight and bins of the given
-// events at iteration `it`.
+// events at iteration `it`, with the same map and integrand code as the fill.
 template <int IG, typename Real>
 __global__ void gv_eval_events_kernel(const GvFillArgs a, uint32_t it, const long long* events,
                                       long long n, double* w, int* bins) {
@@ -364,11 +465,10 @@ __global__ void gv_eval_events_kernel(const GvFillArgs a, uint32_t it, const lon
         const double f = ((double)lo + 0.5) * 0x1p-32;
         x[ax] = __dadd_rn(e64[ax * (N + 1) + i], __dmul_rn(f, wd64[ax * N + i]));
       }
-      J = __dmul_rn(J, jac[ax * N + i]);
+      J = (ax == 0) ? jac[i] : __dmul_rn(J, jac[ax * N + i]);
       bins[j * d + ax] = i;
     }
   }
   const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
-  double wv = __dmul_rn(J, (double)g);
-  w[j] = wv;
+  w[j] = __dmul_rn(J, gv_widen(g));
 }

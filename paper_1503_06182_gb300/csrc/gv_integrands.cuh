@@ -51,13 +51,16 @@
 template <typename T>
 struct GvMath;
 
+// The FP32 form uses the MUFU-based intrinsics (ex2/lg2/rsqrt/rcp/sin/cos
+// with a few ulp of error); the FP64 form the correctly rounded library.
 template <>
 struct GvMath<float> {
-  __device__ static __forceinline__ float exp(float x) { return expf(x); }
-  __device__ static __forceinline__ float log(float x) { return logf(x); }
-  __device__ static __forceinline__ float sqrt(float x) { return sqrtf(x); }
+  __device__ static __forceinline__ float exp(float x) { return __expf(x); }
+  __device__ static __forceinline__ float log(float x) { return __logf(x); }
+  __device__ static __forceinline__ float sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   __device__ static __forceinline__ void sincospi(float x, float* s, float* c) {
-    sincospif(x, s, c);
+    __sincosf(3.14159265358979f * x, s, c);
   }
   __device__ static __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 };
@@ -67,6 +70,7 @@ struct GvMath<double> {
   __device__ static __forceinline__ double exp(double x) { return ::exp(x); }
   __device__ static __forceinline__ double log(double x) { return ::log(x); }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __device__ static __forceinline__ double div(double a, double b) { return a / b; }
   __device__ static __forceinline__ void sincospi(double x, double* s, double* c) {
     ::sincospi(x, s, c);
   }
@@ -127,7 +131,7 @@ __device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 
   const Real omc = two * (one - x[2]);  // 1 - cos theta
   const Real rt = Mt::sqrt(tau);
   const Real ey = Mt::exp(y);
-  const Real emy = one / ey;
+  const Real emy = Mt::div(one, ey);
   const Real x1 = rt * ey, x2 = rt * emy;
   const Real omx1 = one - x1, omx2 = one - x2;
   if (!(omx1 > (Real)0) || !(omx2 > (Real)0)) {
@@ -149,7 +153,7 @@ __device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 
   const Real shat = p1p * p2m;          // 2 p1.p2
   const Real that = -p1p * p3m;         // -2 p1.p3
   const Real uhat = -p2m * p3p;         // -2 p2.p3
-  const Real inv_shat = one / shat;
+  const Real inv_shat = Mt::div(one, shat);
   const Real c = (that - uhat) * inv_shat;
   const Real opc2 = Mt::fma(c, c, one);
   // parton luminosities: f_q f_qbar(x2) and f_qbar(x1) f_q(x2)
@@ -162,7 +166,7 @@ __device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 
   // gamma/Z propagator factors
   const Real D = shat - K[DK_MZ2];
   const Real den = Mt::fma(D, D, K[DK_GM2]);
-  const Real inv_den = one / den;
+  const Real inv_den = Mt::div(one, den);
   const Real chi1 = K[DK_KAPPA] * shat * D * inv_den;
   const Real chi2 = K[DK_KAPPA] * K[DK_KAPPA] * shat * shat * inv_den;
   const Real A = Mt::fma(K[DK_CA2], chi2, Mt::fma(K[DK_CA1], chi1, K[DK_CA0]));
@@ -216,7 +220,7 @@ __device__ __forceinline__ Real gv_ee3j(const Real* x, const GvConst<Real, 3>& K
   const Real x3 = two - x1 - x2;
   const Real Q = K[EK_Q];
   const Real E1 = half * Q * x1, E2 = half * Q * x2, E3 = half * Q * x3;
-  const Real c12 = one - two * (one - x3) / (x1 * x2);
+  const Real c12 = one - Mt::div(two * (one - x3), x1 * x2);
   const Real s12 = Mt::sqrt(fmax(Mt::fma(-c12, c12, one), (Real)0));
   // event plane: p1 along z, p2 in the x-z plane, p3 balances
   const Real p1[3] = {(Real)0, (Real)0, E1};
@@ -247,6 +251,6 @@ __device__ __forceinline__ Real gv_ee3j(const Real* x, const GvConst<Real, 3>& K
   const Real dot23 = Mt::fma(q2[2], q3[2], Mt::fma(q2[1], q3[1], q2[0] * q3[0]));
   const Real y13 = two * Mt::fma(E1, E3, -dot13) * inv_q2;
   const Real y23 = two * Mt::fma(E2, E3, -dot23) * inv_q2;
-  const Real xm1 = two * E1 / Q, xm2 = two * E2 / Q;
-  return Mt::fma(xm1, xm1, xm2 * xm2) / (y23 * y13);
+  const Real xm1 = x1, xm2 = x2;  // 2 E_i / Q
+  return Mt::div(Mt::fma(xm1, xm1, xm2 * xm2), y23 * y13);
 }

@@ -2,16 +2,30 @@
 // grid optimisation (Section 2.1: "the grid optimization is not parallelized,
 // so that all the results can be combined").
 //
-// gv_reduce_kernel: each CTA sums the 128-bit tile partials of a contiguous
-// range of tiles, aligned to the iteration's scale (max over tiles of E_t,
-// an order-free reduction done by the fill kernel), into 192-bit integers and
-// adds them to the iteration's accumulators with integer atomics.  Integer
-// addition is associative, so the totals do not depend on the number of
-// CTAs or their order.  The last CTA to finish (ticket counter, no waiting)
-// rounds the totals to FP64, records I_k and sigma_k, updates the stage's
-// inverse-variance combination and refines the grid (Lepage's VEGAS, cited
-// in Section 2.1): 3-point smoothing, normalisation, compression
-// ((1-rho)/(-ln rho))^alpha, redistribution into N equal shares.
+// gv_reduce_kernel sums the 128-bit tile partials exactly.  Its grid is
+// (accumulator blocks of 32) x (tile ranges): each CTA owns 32 accumulators
+// and a range of tiles, its 8 warps stride over the tiles, the warps' sums
+// are combined in shared memory, and the CTA adds the result to the
+// iteration's accumulators with one fire-and-forget integer atomic per limb
+// (a handful of CTAs per cache line, so no line becomes a hot spot).  Every
+// tile partial is first aligned to the iteration's scale (the max over tiles,
+// formed by the fill kernel with an order-free atomicMax).  Integer addition
+// is associative: the totals do not depend on the grid or on timing.  The
+// last CTA to finish (a ticket, no waiting) rounds the totals to FP64 once,
+// records I_k and sigma_k, combines the stage and forms the per-axis totals
+// of the smoothed bin sums exactly.
+//
+// gv_refine_kernel then refines the grid (Lepage's VEGAS, cited in Section
+// 2.1): smoothing, normalisation, compression ((1-rho)/(-ln rho))^alpha and
+// redistribution into N equal shares.  The compression (an FP64 log per bin)
+// is spread over CTAs; the last one places the new edges from shared memory.
+//
+// On this chip an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles
+// and the FP64 library log takes ~2000 cycles: the serial code here keeps its
+// FP64 chains short (reciprocals passed in, a table-driven log, one warp per
+// independent task).
+#include <algorithm>
+
 #include "gv_integrands.cuh"
 
 struct u192 {
@@ -49,20 +63,45 @@ __device__ __forceinline__ u192 sar192(u192 v, int s) {
   return v;
 }
 
-__device__ __forceinline__ void atomic_add192(unsigned long long* p, const u192& v) {
-  const unsigned long long old0 = atomicAdd(p, v.l0);
-  const unsigned long long c0 = (old0 + v.l0 < old0) ? 1ull : 0ull;
-  const unsigned long long a1 = v.l1 + c0;
-  unsigned long long c1 = (a1 < c0) ? 1ull : 0ull;
-  if (a1 != 0ull) {
-    const unsigned long long old1 = atomicAdd(p + 1, a1);
-    c1 += (old1 + a1 < old1) ? 1ull : 0ull;
-  }
-  const unsigned long long a2 = v.l2 + c1;
-  if (a2 != 0ull) atomicAdd(p + 2, a2);
+// Accumulators: three 64-bit limbs holding bits [0,43), [43,86) and [86,...)
+// (the last one signed), 32 bytes apart.  The two low limbs have 21 bits of
+// headroom (up to 2^21 adds), so no carry travels between limbs until the
+// final conversion and no atomic waits for a returned value.
+#define GV_LIMB 43
+#define GV_LIMB_MASK ((1ull << GV_LIMB) - 1ull)
+#define GV_ACC_STRIDE 4
+
+__device__ __forceinline__ void red_add_limbs(unsigned long long* p, const u192& v) {
+  const unsigned long long l0 = v.l0 & GV_LIMB_MASK;
+  const unsigned long long l1 = ((v.l0 >> GV_LIMB) | (v.l1 << (64 - GV_LIMB))) & GV_LIMB_MASK;
+  // bits 86.. as a signed 64-bit number (|v| < 2^149 always)
+  const unsigned long long l2 = (v.l1 >> (2 * GV_LIMB - 64)) | (v.l2 << (128 - 2 * GV_LIMB));
+  if (l0) atomicAdd(p, l0);
+  if (l1) atomicAdd(p + 1, l1);
+  if (l2) atomicAdd(p + 2, l2);
 }
 
-// value * 2^q, rounded to nearest (the 192-bit integer is two's complement).
+// l0 + l1 2^43 + l2 2^86 (l2 signed) as a 192-bit two's complement integer.
+__device__ __forceinline__ u192 limbs_to_u192(unsigned long long l0, unsigned long long l1,
+                                              unsigned long long l2) {
+  u192 r = {l0, 0ull, 0ull};
+  u192 a = {l1 << GV_LIMB, l1 >> (64 - GV_LIMB), 0ull};
+  add192(r, a);
+  const unsigned long long ext = (unsigned long long)((long long)l2 >> 63);
+  u192 b = {0ull, l2 << (2 * GV_LIMB - 64),
+            (l2 >> (128 - 2 * GV_LIMB)) | (ext << (2 * GV_LIMB - 64))};
+  add192(r, b);
+  return r;
+}
+
+__device__ __forceinline__ u192 load_acc(const unsigned long long* acc, int k) {
+  const unsigned long long* p = acc + GV_ACC_STRIDE * k;
+  return limbs_to_u192(__ldcg(p), __ldcg(p + 1), __ldcg(p + 2));
+}
+
+// value * 2^q rounded to nearest-even, assembled with integer operations only
+// (the 192-bit integer is two's complement; results stay in the normal range
+// for every sum this library forms).
 __device__ double u192_to_double(u192 v, int q) {
   const bool neg = (long long)v.l2 < 0;
   if (neg) {
@@ -83,12 +122,12 @@ __device__ double u192_to_double(u192 v, int q) {
     top = 63 - __clzll((long long)v.l0);
   else
     return 0.0;
+  // 64-bit window with the leading one at bit 63, plus a sticky bit
   unsigned long long window;
+  bool sticky = false;
   if (top >= 63) {
-    const int sh = top - 63;  // bits below the 64-bit window
-    const u192 w = sar192(v, sh);
-    window = w.l0;
-    bool sticky = false;
+    const int sh = top - 63;
+    window = sar192(v, sh).l0;
     if (sh >= 128) {
       sticky = v.l0 != 0ull || v.l1 != 0ull || (sh > 128 && (v.l2 << (192 - sh)) != 0ull);
     } else if (sh >= 64) {
@@ -96,236 +135,211 @@ __device__ double u192_to_double(u192 v, int q) {
     } else if (sh > 0) {
       sticky = (v.l0 << (64 - sh)) != 0ull;
     }
-    window |= sticky ? 1ull : 0ull;
   } else {
     window = v.l0 << (63 - top);
   }
-  const double m = __ull2double_rn(window);
-  const double r = scalbn(m, top - 63 + q);
+  // round the 64-bit window to 53 bits (nearest, ties to even)
+  unsigned long long mant = window >> 11;
+  const unsigned long long rest = window & 0x7FFull;
+  const bool half = (rest & 0x400ull) != 0ull;
+  const bool above = (rest & 0x3FFull) != 0ull || sticky;
+  if (half && (above || (mant & 1ull))) ++mant;
+  int e = top + q;  // value = mant * 2^(e - 52)
+  if (mant >> 53) {
+    mant >>= 1;
+    ++e;
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  const double r = __longlong_as_double((long long)bits);
   return neg ? -r : r;
 }
 
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// Smoothed bin sum: (d_{i-1} + d_i + d_{i+1})/3 inside, 2-point means at the ends.
+__device__ __forceinline__ double smoothed(const double* da, int i, int N) {
+  if (i == 0) return (da[0] + da[1]) * 0.5;
+  if (i == N - 1) return (da[N - 2] + da[N - 1]) * 0.5;
+  return (da[i - 1] + da[i] + da[i + 1]) * (1.0 / 3.0);
+}
+
 // ---------------------------------------------------------------------------
-// Iteration record and stage combination (thread 0 of the last CTA).
+// Natural log of a positive double, table-driven (P. T. P. Tang,
+// "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16 (1990)): x = 2^k m, m in [1,2);
+// with R_j ~ 1/c_j for the 1/128-wide interval of m, r = m R_j - 1 (one fma,
+// one rounding, |r| < 2^-7) and ln x = k ln2 + L_j + log1p(r), L_j = -ln R_j,
+// log1p(r) by its Taylor series to r^7 (truncation below 2^-59 relative).
+// The table (R_j, L_j for j < 128, then ln2 split into a 42-bit head and a
+// tail) is built by the host from its libm when a context is created.
 // ---------------------------------------------------------------------------
-__device__ void mean_sigma(double s1, double s2, long long ncall, double* mean, double* sigma) {
-  const double C = (double)ncall;
-  const double I = s1 / C;
-  const double var = (s2 / C - I * I) / (C - 1.0);
+__device__ __forceinline__ double gv_log1p_series(double r) {
+  double p = 1.0 / 7.0;
+  p = fma(p, r, -1.0 / 6.0);
+  p = fma(p, r, 1.0 / 5.0);
+  p = fma(p, r, -1.0 / 4.0);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  p = fma(p, r, 1.0);
+  return p * r;
+}
+
+__device__ double gv_log_pos(double x, const double* __restrict__ tab) {
+  // near 1 the reduction would cancel: r = x - 1 is exact there (Sterbenz)
+  if (fabs(x - 1.0) <= 0x1p-7) return gv_log1p_series(x - 1.0);
+  long long b = __double_as_longlong(x);
+  int k = 0;
+  if (b < (1ll << 52)) {  // subnormal: scale by 2^54
+    x *= 0x1p54;
+    b = __double_as_longlong(x);
+    k = -54;
+  }
+  k += (int)(b >> 52) - 1023;
+  const int j = (int)((b >> 45) & 127);
+  const double m = __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  const double R = __ldg(tab + 2 * j), L = __ldg(tab + 2 * j + 1);
+  const double p = gv_log1p_series(fma(m, R, -1.0));
+  const double kd = (double)k;
+  return fma(kd, __ldg(tab + 256), L) + fma(kd, __ldg(tab + 257), p);
+}
+
+// ---------------------------------------------------------------------------
+// Iteration record and stage combination.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mean_sigma(double s1, double s2, double inv_c, double inv_cm1,
+                                           double* mean, double* sigma) {
+  const double I = s1 * inv_c;
+  const double var = (s2 * inv_c - I * I) * inv_cm1;
   *mean = I;
   *sigma = var > 0.0 ? sqrt(var) : 0.0;
 }
 
-__device__ void combine_stage(const double* per_iter, int stride, int m, GvState* st,
-                              bool adjoint) {
-  int nzero = 0;
-  double zsum = 0.0;
-  for (int k = 0; k < m; ++k) {
-    const double s = per_iter[k * stride + 1];
-    if (!(s > 0.0)) {
-      ++nzero;
-      zsum += per_iter[k * stride];
+// Inverse-variance combination of the iterations 0..m-1 of a stage by one
+// warp (lanes stride over the iterations, fixed butterfly sums); if any
+// iteration has zero variance, those alone are averaged with error 0.
+__device__ void combine_stage_warp(const double* per_iter, int stride, int m, double inv_m1,
+                                   GvState* st, bool adjoint) {
+  const int lane = threadIdx.x & 31;
+  if (m == 1 && !adjoint) {
+    if (lane == 0) {
+      st->integral = per_iter[0];
+      st->error = per_iter[1];
+      st->chi2 = 0.0;
     }
+    return;
   }
+  double nz = 0.0;
+  for (int k = lane; k < m; k += 32) nz += (per_iter[k * stride + 1] > 0.0) ? 0.0 : 1.0;
+  nz = warp_sum_f64(nz);
   double swt = 0.0, swi = 0.0;
-  if (nzero == 0) {
-    for (int k = 0; k < m; ++k) {
-      const double s = per_iter[k * stride + 1];
-      const double wt = 1.0 / (s * s);
-      swt += wt;
-      swi += wt * per_iter[k * stride];
-    }
-    const double mean = swi / swt;
-    double chi2 = 0.0;
-    for (int k = 0; k < m; ++k) {
+  for (int k = lane; k < m; k += 32) {
+    const double s = per_iter[k * stride + 1];
+    const double wt = nz > 0.0 ? (s > 0.0 ? 0.0 : 1.0) : __drcp_rn(s * s);
+    swt += wt;
+    swi = fma(wt, per_iter[k * stride], swi);
+  }
+  swt = warp_sum_f64(swt);
+  swi = warp_sum_f64(swi);
+  const double inv_swt = __drcp_rn(swt);
+  const double mean = swi * inv_swt;
+  double chi2 = 0.0;
+  if (nz == 0.0)
+    for (int k = lane; k < m; k += 32) {
       const double s = per_iter[k * stride + 1];
       const double dev = per_iter[k * stride] - mean;
-      chi2 += dev * dev / (s * s);
+      chi2 = fma(dev * dev, __drcp_rn(s * s), chi2);
     }
+  chi2 = warp_sum_f64(chi2);
+  if (lane == 0) {
     st->integral = mean;
-    st->error = 1.0 / sqrt(swt);
-    st->chi2 = m > 1 ? chi2 / (m - 1) : 0.0;
-  } else {
-    st->integral = zsum / nzero;
-    st->error = 0.0;
-    st->chi2 = 0.0;
+    st->error = nz > 0.0 ? 0.0 : rsqrt(swt);
+    st->chi2 = (nz > 0.0 || m < 2) ? 0.0 : chi2 * inv_m1;
   }
   if (adjoint) {
     for (int p = 0; p < GV_NGRAD; ++p) {
-      double num = 0.0, den = 0.0, var = 0.0;
-      for (int k = 0; k < m; ++k) {
+      double num = 0.0, var = 0.0;
+      for (int k = lane; k < m; k += 32) {
         const double s = per_iter[k * stride + 1];
-        const double wt = nzero ? ((s > 0.0) ? 0.0 : 1.0) : 1.0 / (s * s);
-        const double G = per_iter[k * stride + 2 + 2 * p];
+        const double wt = nz > 0.0 ? (s > 0.0 ? 0.0 : 1.0) : __drcp_rn(s * s);
         const double sG = per_iter[k * stride + 3 + 2 * p];
-        num += wt * G;
-        den += wt;
-        var += wt * wt * sG * sG;
+        num = fma(wt, per_iter[k * stride + 2 + 2 * p], num);
+        var = fma(wt * wt, sG * sG, var);
       }
-      st->grad[p] = num / den;
-      st->grad_err[p] = sqrt(var) / den;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Grid refinement by the whole CTA.  d: bin sums [ndim][N]; scratch holds
-// smoothed/compressed values and cumulative sums.
-// ---------------------------------------------------------------------------
-__device__ void pack_axis_tables(double* grid, int d, int N, int a_first, int a_last, int tid,
-                                 int nthr) {
-  const GvGridLayout L{d, N};
-  double* e64 = grid + L.off_e64();
-  double* wd64 = grid + L.off_wd64();
-  double* jac = grid + L.off_jac();
-  float* e32 = reinterpret_cast<float*>(grid + L.off_f32_base());
-  float* wd32 = e32 + (size_t)d * (N + 1);
-  for (int k = tid; k < (a_last - a_first) * (N + 1); k += nthr) {
-    const int a = a_first + k / (N + 1), i = k % (N + 1);
-    const size_t ie = (size_t)a * (N + 1) + i;
-    e32[ie] = (float)e64[ie];
-    if (i < N) {
-      const double w = e64[ie + 1] - e64[ie];
-      wd64[(size_t)a * N + i] = w;
-      jac[(size_t)a * N + i] = (double)N * w;
-      wd32[(size_t)a * N + i] = (float)w;
-    }
-  }
-}
-
-__device__ void refine_grid(const GvReduceArgs& a, const double* dsum) {
-  const int d = a.ndim, N = a.nbins;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nwarps = nthr >> 5;
-  double* sm = a.scratch;                        // [d][N]  smoothed, then compressed
-  double* cum = a.scratch + (size_t)d * N;       // [d][N+1]
-  double* ne = cum + (size_t)d * (N + 1);        // [d][N+1] new edges
-  __shared__ double s_total[GV_MAXD];
-  double* e64 = a.grid;                          // pack starts with e64
-  // 1. smoothing
-  for (int k = tid; k < d * N; k += nthr) {
-    const int ax = k / N, i = k % N;
-    const double* da = dsum + (size_t)ax * N;
-    double v;
-    if (i == 0)
-      v = (da[0] + da[1]) / 2.0;
-    else if (i == N - 1)
-      v = (da[N - 2] + da[N - 1]) / 2.0;
-    else
-      v = (da[i - 1] + da[i] + da[i + 1]) / 3.0;
-    sm[k] = v;
-  }
-  __syncthreads();
-  // per-axis totals: one warp per axis, fixed lane order, fixed butterfly
-  for (int ax = wid; ax < d; ax += nwarps) {
-    double t = 0.0;
-    for (int i = lane; i < N; i += 32) t += sm[(size_t)ax * N + i];
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-    if (lane == 0) s_total[ax] = t;
-  }
-  __syncthreads();
-  // 2. normalisation and 3. compression
-  for (int k = tid; k < d * N; k += nthr) {
-    const int ax = k / N;
-    const double total = s_total[ax];
-    double r = 0.0;
-    if (total > 0.0) {
-      const double rho = sm[k] / total;
-      if (rho <= 0.0)
-        r = 0.0;
-      else if (rho >= 1.0)
-        r = 1.0;
-      else
-        r = pow((1.0 - rho) / (-log(rho)), a.alpha);
-    }
-    sm[k] = r;
-  }
-  __syncthreads();
-  // cumulative sums, one thread per axis, in bin order
-  for (int ax = tid; ax < d; ax += nthr) {
-    double c = 0.0;
-    cum[(size_t)ax * (N + 1)] = 0.0;
-    for (int i = 0; i < N; ++i) {
-      c += sm[(size_t)ax * N + i];
-      cum[(size_t)ax * (N + 1) + i + 1] = c;
-    }
-  }
-  __syncthreads();
-  // 4. new edges: edge j sits where the cumulative compressed mass reaches j R/N
-  for (int k = tid; k < d * (N + 1); k += nthr) {
-    const int ax = k / (N + 1), j = k % (N + 1);
-    if (!(s_total[ax] > 0.0)) continue;
-    const double* C = cum + (size_t)ax * (N + 1);
-    const double* r = sm + (size_t)ax * N;
-    const double* e = e64 + (size_t)ax * (N + 1);
-    double v;
-    if (j == 0) {
-      v = 0.0;
-    } else if (j == N) {
-      v = 1.0;
-    } else {
-      const double R = C[N];
-      const double target = (R / N) * j;
-      // first bin i in [0, N-1] with C[i+1] > target (N-1 if none)
-      int lo = 0, hi = N - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (C[mid + 1] > target)
-          hi = mid;
-        else
-          lo = mid + 1;
+      num = warp_sum_f64(num);
+      var = warp_sum_f64(var);
+      if (lane == 0) {
+        st->grad[p] = num * inv_swt;
+        st->grad_err[p] = sqrt(var) * inv_swt;
       }
-      const int i = lo;
-      v = e[i] + (target - C[i]) / r[i] * (e[i + 1] - e[i]);
     }
-    ne[k] = v;
   }
-  __syncthreads();
-  for (int k = tid; k < d * (N + 1); k += nthr) {
-    const int ax = k / (N + 1);
-    if (s_total[ax] > 0.0) e64[k] = ne[k];
-  }
-  __syncthreads();
-  pack_axis_tables(a.grid, d, N, 0, d, tid, nthr);
 }
 
+// The last reduce CTA (256 threads).
 __device__ void finalize_iteration(const GvReduceArgs& a) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
   GvState* st = a.st;
-  // totals -> FP64
+  // totals -> FP64 (each rounded once)
   for (int k = tid; k < a.nacc; k += nthr) {
     const int ch = k < 2 * a.nch ? (k >> 1) : 0;
     const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
     const int Eg = st->E[ch];
-    double v = 0.0;
-    if (Eg != GV_EMPTY) {
-      u192 t;
-      t.l0 = __ldcg(a.acc + 3 * k);
-      t.l1 = __ldcg(a.acc + 3 * k + 1);
-      t.l2 = __ldcg(a.acc + 3 * k + 2);
-      v = u192_to_double(t, pw * Eg - GV_FB);
-    }
-    a.sums[k] = v;
+    a.sums[k] = Eg != GV_EMPTY ? u192_to_double(load_acc(a.acc, k), pw * Eg - GV_FB) : 0.0;
   }
   __syncthreads();
-  if (tid == 0) {
-    const int m = st->m;
+  if (wid == 0) {
+    // warp 0: the iteration record (one lane per channel) and the stage
     const int stride = a.mode ? 2 + 2 * GV_NGRAD : 2;
-    double* rec = a.per_iter + (size_t)m * stride;
-    mean_sigma(a.sums[0], a.sums[1], a.ncall, &rec[0], &rec[1]);
-    if (a.mode) {
-      for (int p = 0; p < GV_NGRAD; ++p)
-        mean_sigma(a.sums[2 + 2 * p], a.sums[3 + 2 * p], a.ncall, &rec[2 + 2 * p],
-                   &rec[3 + 2 * p]);
+    if (lane < a.nch) {
+      double* rec = a.per_iter + (size_t)a.k * stride + 2 * lane;
+      mean_sigma(a.sums[2 * lane], a.sums[2 * lane + 1], a.inv_c, a.inv_cm1, &rec[0], &rec[1]);
     }
-    st->m = m + 1;
-    combine_stage(a.per_iter, stride, m + 1, st, a.mode != 0);
+    __syncwarp();
+    if (a.last) combine_stage_warp(a.per_iter, stride, a.k + 1, a.inv_m1, st, a.mode != 0);
+    if (lane == 0) {
+      const unsigned long long nf = __ldcg(&st->nonfinite_iter);
+      st->nonfinite = (a.k == 0 ? 0ull : st->nonfinite) + nf;
+      if (a.k == 0) st->status = 0;
+      st->nonfinite_iter = 0ull;
+    }
+  } else if (a.has_bins) {
+    // warps 1..: per-axis totals of the smoothed bin sums, exactly:
+    // 6 sum_i smoothed_i = sum_j c_j d_j with small integer c_j, on the exact
+    // bin integers; one rounding to FP64, stored as 1/total (0: no change)
+    const int d = a.ndim, N = a.nbins;
+    const int Eg = st->E[0];
+    for (int ax = wid - 1; ax < d; ax += (nthr >> 5) - 1) {
+      u192 t = {0ull, 0ull, 0ull};
+      if (Eg != GV_EMPTY) {
+        for (int j = lane; j < N; j += 32) {
+          const u192 v = load_acc(a.acc, 2 * a.nch + ax * N + j);
+          int c = 0;
+          for (int i = max(0, j - 1); i <= min(N - 1, j + 1); ++i) {
+            const bool inside = (i == 0) ? (j <= 1) : (i == N - 1) ? (j >= N - 2) : true;
+            if (inside) c += (i == 0 || i == N - 1) ? 3 : 2;
+          }
+          for (int r = 0; r < c; ++r) add192(t, v);
+        }
+      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        u192 o = {__shfl_xor_sync(0xffffffffu, t.l0, m), __shfl_xor_sync(0xffffffffu, t.l1, m),
+                  __shfl_xor_sync(0xffffffffu, t.l2, m)};
+        add192(t, o);
+      }
+      if (lane == 0) {
+        const double total = u192_to_double(t, 2 * Eg - GV_FB) * (1.0 / 6.0);
+        a.inv_total[ax] = (Eg != GV_EMPTY && total > 0.0) ? __drcp_rn(total) : 0.0;
+      }
+    }
   }
-  if (a.adapt && a.has_bins) refine_grid(a, a.sums + 2 * a.nch);
-  __syncthreads();
-  // reset the accumulators for the next iteration
-  for (int k = tid; k < 3 * a.nacc; k += nthr) a.acc[k] = 0ull;
+  __syncthreads();  // every read of the accumulators is done
+  for (int k = tid; k < GV_ACC_STRIDE * a.nacc; k += nthr) a.acc[k] = 0ull;
   if (tid == 0) {
     for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
     st->done = 0;
@@ -333,29 +347,57 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
   }
 }
 
+#define GV_RED_TILES_PER_LOAD 8
+
 __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
-  const int t0 = blockIdx.x * a.tiles_per_cta;
+  __shared__ u192 s_part[8][32];
+  __shared__ int is_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = blockIdx.x * 32 + lane;
+  const int t0 = blockIdx.y * a.tiles_per_cta;
   const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
-  for (int k = threadIdx.x; k < a.nacc; k += blockDim.x) {
+  u192 r = {0ull, 0ull, 0ull};
+  if (k < a.nacc) {
     const int ch = k < 2 * a.nch ? (k >> 1) : 0;
     const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
     const int Eg = a.st->E[ch];
-    if (Eg == GV_EMPTY) continue;
-    u192 r = {0ull, 0ull, 0ull};
-    for (int t = t0; t < t1; ++t) {
-      const int Et = a.tileE[(size_t)t * a.nch + ch];
-      if (Et == GV_EMPTY) continue;
-      const ulonglong2 v = a.part[(size_t)t * a.nacc + k];
-      u192 x = {v.x, v.y, (unsigned long long)((long long)v.y >> 63)};
-      x = sar192(x, pw * (Eg - Et));
-      add192(r, x);
+    if (Eg != GV_EMPTY) {
+      constexpr int G = GV_RED_TILES_PER_LOAD;
+      for (int tb = t0 + wid; tb < t1; tb += 8 * G) {
+        ulonglong2 v[G];
+        int Et[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int t = tb + 8 * g;
+          if (t < t1) {
+            Et[g] = a.tileE[(size_t)t * a.nch + ch];
+            v[g] = a.part[(size_t)t * a.nacc + k];
+          } else {
+            Et[g] = GV_EMPTY;
+            v[g] = make_ulonglong2(0ull, 0ull);
+          }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const u192 x = {v[g].x, v[g].y, (unsigned long long)((long long)v[g].y >> 63)};
+          const int sh = Et[g] == GV_EMPTY ? 192 : pw * (Eg - Et[g]);
+          if (x.l0 | x.l1) add192(r, sar192(x, sh));
+        }
+      }
     }
-    if (r.l0 | r.l1 | r.l2) atomic_add192(a.acc + 3 * k, r);
+  }
+  s_part[wid][lane] = r;
+  __syncthreads();
+  if (wid == 0 && k < a.nacc) {
+    u192 t = s_part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) add192(t, s_part[w][lane]);
+    if (t.l0 | t.l1 | t.l2) red_add_limbs(a.acc + GV_ACC_STRIDE * k, t);
   }
   __threadfence();
   __syncthreads();
-  __shared__ int is_last;
-  if (threadIdx.x == 0) is_last = (atomicAdd(&a.st->done, 1) == (int)gridDim.x - 1) ? 1 : 0;
+  if (threadIdx.x == 0)
+    is_last = (atomicAdd(&a.st->done, 1) == (int)(gridDim.x * gridDim.y) - 1) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -363,82 +405,237 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Setup: derived constants of the integrand and a fresh stage.
+// Grid refinement.
 // ---------------------------------------------------------------------------
-// p[GV_MAXPARAMS - 1] carries the number of user parameters.
-__global__ void gv_setup_kernel(int ig, const double* p, double* K, GvState* st, int nacc,
-                                unsigned long long* acc) {
-  if (threadIdx.x == 0) {
-    const int np = (int)p[GV_MAXPARAMS - 1];
-    for (int i = 0; i < GV_NCONST; ++i) K[i] = 0.0;
-    if (ig == GV_GAUSS) {
-      K[GK_INV2S2] = 1.0 / (2.0 * p[0] * p[0]);
-    } else if (ig == GV_DY) {
-      const double sqrt_s = p[0], MZ = p[1], GZ = p[2], sw2 = p[3], alpha = p[4];
-      const double mlo = p[5], mhi = p[6];
-      const double s = sqrt_s * sqrt_s;
-      const double tau_lo = mlo * mlo / s, tau_hi = mhi * mhi / s;
-      const double pi = 3.14159265358979323846;
-      K[DK_SQRTS] = sqrt_s;
-      K[DK_S] = s;
-      K[DK_TAULO] = tau_lo;
-      K[DK_L] = log(tau_hi / tau_lo);
-      K[DK_MZ2] = MZ * MZ;
-      K[DK_GM2] = (GZ * MZ) * (GZ * MZ);
-      const double kappa = 1.0 / (4.0 * sw2 * (1.0 - sw2));
-      K[DK_KAPPA] = kappa;
-      // alpha^2/(4 N_c) * (hbar c)^2 [pb GeV^2] * Jacobians of cos(theta) (2) and phi (2 pi)
-      K[DK_PREF] = alpha * alpha / (4.0 * 3.0) * 0.3893794e9 * 2.0 * (2.0 * pi);
-      // couplings V = T3 - 2 Q sw2, A = T3; muon Q = -1, T3 = -1/2
-      const double Vl = -0.5 + 2.0 * sw2, Al = -0.5, dVl = 2.0;
-      double cA0 = 0, cA1 = 0, cA2 = 0, cB1 = 0, cB2 = 0, dA1 = 0, dA2 = 0, dB2 = 0;
-      for (int t = 0; t < 2; ++t) {
-        const double n = t == 0 ? 2.0 : 3.0;  // u, c  |  d, s, b
-        const double Q = t == 0 ? 2.0 / 3.0 : -1.0 / 3.0;
-        const double T3 = t == 0 ? 0.5 : -0.5;
-        const double Vq = T3 - 2.0 * Q * sw2, Aq = T3, dVq = -2.0 * Q;
-        cA0 += n * Q * Q;
-        cA1 += n * (-2.0 * Q * Vl * Vq);
-        cA2 += n * (Al * Al + Vl * Vl) * (Aq * Aq + Vq * Vq);
-        cB1 += n * (-4.0 * Q * Al * Aq);
-        cB2 += n * (8.0 * Al * Vl * Aq * Vq);
-        dA1 += n * (-2.0 * Q * (dVl * Vq + Vl * dVq));
-        dA2 += n * (2.0 * Vl * dVl * (Aq * Aq + Vq * Vq) + (Al * Al + Vl * Vl) * 2.0 * Vq * dVq);
-        dB2 += n * (8.0 * Al * Aq * (dVl * Vq + Vl * dVq));
-      }
-      K[DK_CA0] = cA0;
-      K[DK_CA1] = cA1;
-      K[DK_CA2] = cA2;
-      K[DK_CB1] = cB1;
-      K[DK_CB2] = cB2;
-      K[DK_A] = p[7];
-      K[DK_B] = p[8];
-      K[DK_NORM] = 0.2 * p[9] * p[9];
-      K[DK_MZ] = MZ;
-      K[DK_GZ] = GZ;
-      K[DK_DKAPPA] = -kappa * (1.0 - 2.0 * sw2) / (sw2 * (1.0 - sw2));
-      K[DK_DCA1] = dA1;
-      K[DK_DCA2] = dA2;
-      K[DK_DCB2] = dB2;
-    } else if (ig == GV_EE3J) {
-      const double Q = np > 1 ? p[1] : 91.1876;
-      K[EK_YCUT] = p[0];
-      K[EK_Q] = Q;
-      K[EK_INVQ2] = 1.0 / (Q * Q);
+// Write the edges e_src (d x (N+1)) into the grid pack with its derived tables.
+__device__ void pack_axis_tables(double* grid, const double* e_src, int d, int N, int tid,
+                                 int nthr) {
+  const GvGridLayout L{d, N};
+  double* e64 = grid + L.off_e64();
+  double* wd64 = grid + L.off_wd64();
+  double* jac = grid + L.off_jac();
+  float* e32 = reinterpret_cast<float*>(grid + L.off_f32_base());
+  float* wd32 = e32 + (size_t)d * (N + 1);
+  for (int k = tid; k < d * (N + 1); k += nthr) {
+    const int a = k / (N + 1), i = k % (N + 1);
+    const size_t ie = (size_t)a * (N + 1) + i;
+    const double e = e_src[ie];
+    e64[ie] = e;
+    e32[ie] = (float)e;
+    if (i < N) {
+      const double w = e_src[ie + 1] - e;
+      wd64[(size_t)a * N + i] = w;
+      jac[(size_t)a * N + i] = (double)N * w;
+      wd32[(size_t)a * N + i] = (float)w;
     }
-    st->m = 0;
-    st->nonfinite = 0ull;
-    st->status = 0;
-    st->done = 0;
-    for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
-    st->integral = st->error = st->chi2 = 0.0;
-    for (int q = 0; q < GV_NGRAD; ++q) st->grad[q] = st->grad_err[q] = 0.0;
   }
-  for (int k = threadIdx.x; k < 3 * nacc; k += blockDim.x) acc[k] = 0ull;
+}
+
+// ((1 - rho)/(-ln rho))^alpha for 0 < rho < 1, with the common exponents
+// evaluated by roots rather than pow.
+__device__ __forceinline__ double compress(double rho, double alpha, const double* tab) {
+  if (rho <= 0.0) return 0.0;
+  if (rho >= 1.0) return 1.0;
+  const double L = -gv_log_pos(rho, tab);
+  const double om = 1.0 - rho;
+  if (alpha == 1.5) {
+    const double y = rsqrt(L);
+    return om * sqrt(om) * (y * y * y);
+  }
+  if (alpha == 1.0) return om * __drcp_rn(L);
+  if (alpha == 0.5) return sqrt(om) * rsqrt(L);
+  if (alpha == 2.0) {
+    const double q = om * __drcp_rn(L);
+    return q * q;
+  }
+  if (alpha == 0.0) return 1.0;
+  return pow(om * __drcp_rn(L), alpha);
+}
+
+#define GV_REFINE_THREADS 512
+#define GV_REFINE_BINS 32
+
+// Phase 1, every CTA: warp 0 computes the compressed value r_i of 32 bins and
+// the slope (e_{i+1}-e_i)/r_i used to place edges.  Phase 2, the last CTA
+// (ticket): per-axis prefix sums C of r (warp scan), new edges where C
+// reaches j R/N -- binary search on the bit patterns of the nonnegative
+// doubles, then e_i + (target - C_i) * slope_i -- and the tables, with r,
+// slope, C and the old edges in shared memory.
+__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRefineArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int d = a.ndim, N = a.nbins, dN = d * N;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NWARP = GV_REFINE_THREADS / 32;
+  __shared__ int is_last;
+  __shared__ double s_step[GV_MAXD];
+  double* gr = a.scratch;                   // [dN] r
+  double* gsl = a.scratch + dN;             // [dN] slope
+  double* ne = a.scratch + 2 * (size_t)dN;  // [d(N+1)] new edges
+  const double* e64 = a.grid;               // the pack starts with e64
+  if (wid == 0) {
+    const int k = blockIdx.x * GV_REFINE_BINS + lane;
+    if (k < dN) {
+      const int ax = k / N, i = k - ax * N;
+      const double it = a.inv_total[ax];
+      double rv = 0.0, sl = 0.0;
+      if (it > 0.0) {
+        rv = compress(smoothed(a.dsum + (size_t)ax * N, i, N) * it, a.alpha, a.logtab);
+        if (rv > 0.0)
+          sl = (e64[ax * (N + 1) + i + 1] - e64[ax * (N + 1) + i]) * __drcp_rn(rv);
+      }
+      gr[k] = rv;
+      gsl[k] = sl;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(&a.st->done_refine, 1) == (int)gridDim.x - 1) ? 1 : 0;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double* r = sm;                 // [dN]
+  double* slope = r + dN;         // [dN]
+  double* cum = slope + dN;       // [d(N+1)]
+  double* e = cum + d * (N + 1);  // [d(N+1)] old edges
+  for (int k = tid; k < dN; k += GV_REFINE_THREADS) {
+    r[k] = __ldcg(gr + k);
+    slope[k] = __ldcg(gsl + k);
+  }
+  for (int k = tid; k < d * (N + 1); k += GV_REFINE_THREADS) e[k] = e64[k];
+  __syncthreads();
+  for (int ax = wid; ax < d; ax += NWARP) {
+    const double* ra = r + ax * N;
+    double* ca = cum + ax * (N + 1);
+    const int chunk = (N + 31) / 32;
+    const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
+    double local = 0.0;
+    for (int i = i0; i < i1; ++i) local += ra[i];
+    double incl = local;
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+      const double o = __shfl_up_sync(0xffffffffu, incl, m);
+      if (lane >= m) incl += o;
+    }
+    double run = incl - local;  // exclusive prefix of this lane's chunk
+    if (lane == 0) ca[0] = 0.0;
+    for (int i = i0; i < i1; ++i) {
+      run += ra[i];
+      ca[i + 1] = run;
+    }
+    __syncwarp();
+    if (lane == 0) s_step[ax] = ca[N] * a.inv_nbins;
+  }
+  __syncthreads();
+  for (int kk = tid; kk < d * (N + 1); kk += GV_REFINE_THREADS) {
+    const int ax = kk / (N + 1), j = kk % (N + 1);
+    double v = e[kk];
+    if (a.inv_total[ax] > 0.0) {
+      if (j == 0) {
+        v = 0.0;
+      } else if (j == N) {
+        v = 1.0;
+      } else {
+        const double* C = cum + ax * (N + 1);
+        const double target = s_step[ax] * j;
+        const long long tb = __double_as_longlong(target);
+        const long long* Cb = reinterpret_cast<const long long*>(C);
+        int lo = 0, hi = N - 1;  // first bin i with C[i+1] > target (N-1 if none)
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (Cb[mid + 1] > tb)
+            hi = mid;
+          else
+            lo = mid + 1;
+        }
+        v = fma(target - C[lo], slope[ax * N + lo], e[ax * (N + 1) + lo]);
+      }
+    }
+    ne[kk] = v;
+  }
+  __syncthreads();
+  pack_axis_tables(a.grid, ne, d, N, tid, GV_REFINE_THREADS);
+  if (tid == 0) a.st->done_refine = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Derived constants of an integrand (launched when the parameters change).
+// p[GV_MAXPARAMS - 1] carries the number of user parameters.
+// ---------------------------------------------------------------------------
+__global__ void gv_consts_kernel(int ig, const double* p, double* K) {
+  if (threadIdx.x != 0) return;
+  const int np = (int)p[GV_MAXPARAMS - 1];
+  for (int i = 0; i < GV_NCONST; ++i) K[i] = 0.0;
+  if (ig == GV_GAUSS) {
+    K[GK_INV2S2] = 1.0 / (2.0 * p[0] * p[0]);
+  } else if (ig == GV_DY) {
+    const double sqrt_s = p[0], MZ = p[1], GZ = p[2], sw2 = p[3], alpha = p[4];
+    const double mlo = p[5], mhi = p[6];
+    const double s = sqrt_s * sqrt_s;
+    const double tau_lo = mlo * mlo / s, tau_hi = mhi * mhi / s;
+    const double pi = 3.14159265358979323846;
+    K[DK_SQRTS] = sqrt_s;
+    K[DK_S] = s;
+    K[DK_TAULO] = tau_lo;
+    K[DK_L] = log(tau_hi / tau_lo);
+    K[DK_MZ2] = MZ * MZ;
+    K[DK_GM2] = (GZ * MZ) * (GZ * MZ);
+    const double kappa = 1.0 / (4.0 * sw2 * (1.0 - sw2));
+    K[DK_KAPPA] = kappa;
+    // alpha^2/(4 N_c) * (hbar c)^2 [pb GeV^2] * Jacobians of cos(theta) (2) and phi (2 pi)
+    K[DK_PREF] = alpha * alpha / (4.0 * 3.0) * 0.3893794e9 * 2.0 * (2.0 * pi);
+    // couplings V = T3 - 2 Q sw2, A = T3; muon Q = -1, T3 = -1/2
+    const double Vl = -0.5 + 2.0 * sw2, Al = -0.5, dVl = 2.0;
+    double cA0 = 0, cA1 = 0, cA2 = 0, cB1 = 0, cB2 = 0, dA1 = 0, dA2 = 0, dB2 = 0;
+    for (int t = 0; t < 2; ++t) {
+      const double n = t == 0 ? 2.0 : 3.0;  // u, c  |  d, s, b
+      const double Q = t == 0 ? 2.0 / 3.0 : -1.0 / 3.0;
+      const double T3 = t == 0 ? 0.5 : -0.5;
+      const double Vq = T3 - 2.0 * Q * sw2, Aq = T3, dVq = -2.0 * Q;
+      cA0 += n * Q * Q;
+      cA1 += n * (-2.0 * Q * Vl * Vq);
+      cA2 += n * (Al * Al + Vl * Vl) * (Aq * Aq + Vq * Vq);
+      cB1 += n * (-4.0 * Q * Al * Aq);
+      cB2 += n * (8.0 * Al * Vl * Aq * Vq);
+      dA1 += n * (-2.0 * Q * (dVl * Vq + Vl * dVq));
+      dA2 += n * (2.0 * Vl * dVl * (Aq * Aq + Vq * Vq) + (Al * Al + Vl * Vl) * 2.0 * Vq * dVq);
+      dB2 += n * (8.0 * Al * Aq * (dVl * Vq + Vl * dVq));
+    }
+    K[DK_CA0] = cA0;
+    K[DK_CA1] = cA1;
+    K[DK_CA2] = cA2;
+    K[DK_CB1] = cB1;
+    K[DK_CB2] = cB2;
+    K[DK_A] = p[7];
+    K[DK_B] = p[8];
+    K[DK_NORM] = 0.2 * p[9] * p[9];
+    K[DK_MZ] = MZ;
+    K[DK_GZ] = GZ;
+    K[DK_DKAPPA] = -kappa * (1.0 - 2.0 * sw2) / (sw2 * (1.0 - sw2));
+    K[DK_DCA1] = dA1;
+    K[DK_DCA2] = dA2;
+    K[DK_DCB2] = dB2;
+  } else if (ig == GV_EE3J) {
+    const double Q = np > 1 ? p[1] : 91.1876;
+    K[EK_YCUT] = p[0];
+    K[EK_Q] = Q;
+    K[EK_INVQ2] = 1.0 / (Q * Q);
+  }
+}
+
+// Reset the per-iteration invariants (at creation and after the autotuner's
+// trial launches).
+__global__ void gv_reset_kernel(GvState* st, int nacc, unsigned long long* acc) {
+  if (threadIdx.x == 0) {
+    st->nonfinite_iter = 0ull;
+    st->done = 0;
+    st->done_refine = 0;
+    for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
+  }
+  for (int k = threadIdx.x; k < GV_ACC_STRIDE * nacc; k += blockDim.x) acc[k] = 0ull;
 }
 
 __global__ void gv_grid_pack_kernel(double* grid, int d, int N) {
-  pack_axis_tables(grid, d, N, 0, d, threadIdx.x, blockDim.x);
+  pack_axis_tables(grid, grid, d, N, threadIdx.x, blockDim.x);
 }
 
 __global__ void gv_rng_words_kernel(unsigned long long seed, uint32_t it, uint32_t batch,
@@ -451,14 +648,47 @@ __global__ void gv_rng_words_kernel(unsigned long long seed, uint32_t it, uint32
 }
 
 namespace gv {
-cudaError_t launch_reduce(const GvReduceArgs& a, int ctas, cudaStream_t s) {
-  gv_reduce_kernel<<<ctas, 256, 0, s>>>(a);
+size_t refine_smem_bytes(int d, int N) {
+  return sizeof(double) * (2 * (size_t)d * N + 2 * (size_t)d * (N + 1));
+}
+
+// Reduce grid: 32 accumulators per CTA; at most 64 tile ranges.
+void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy) {
+  const int tpc = n_tiles <= 64 ? std::max(1, n_tiles) : std::max(64, (n_tiles + 63) / 64);
+  *tiles_per_cta = tpc;
+  *gx = (nacc + 31) / 32;
+  *gy = (n_tiles + tpc - 1) / tpc;
+}
+
+cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s) {
+  int tpc, gx, gy;
+  reduce_grid(a.n_tiles, a.nacc, &tpc, &gx, &gy);
+  if (tpc != a.tiles_per_cta) return cudaErrorInvalidValue;
+  gv_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_setup(int integrand, const double* params, double* kconst, GvState* st,
-                         int nacc, unsigned long long* acc, cudaStream_t s) {
-  gv_setup_kernel<<<1, 256, 0, s>>>(integrand, params, kconst, st, nacc, acc);
+cudaError_t prepare_refine(int d, int N) {
+  const size_t smem = refine_smem_bytes(d, N);
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(gv_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  return cudaSuccess;
+}
+
+cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s) {
+  const int ctas = (a.ndim * a.nbins + GV_REFINE_BINS - 1) / GV_REFINE_BINS;
+  gv_refine_kernel<<<ctas, GV_REFINE_THREADS, refine_smem_bytes(a.ndim, a.nbins), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s) {
+  gv_consts_kernel<<<1, 32, 0, s>>>(integrand, params, kconst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, cudaStream_t s) {
+  gv_reset_kernel<<<1, 256, 0, s>>>(st, nacc, acc);
   return cudaGetLastError();
 }
 
