@@ -70,6 +70,8 @@ extern "C" {
 #define VEGAS_OPT_GRAPH 5     /* 1 = replay the iterations as one CUDA graph (default), 0 = plain launches */
 #define VEGAS_OPT_TIMING 6    /* 1 = time every fill and reduce kernel with CUDA events */
 #define VEGAS_OPT_BATCH_ID 7  /* Philox batch word of this context (default 0; < 2^24) */
+#define VEGAS_OPT_PDL 8       /* 1 = chain the kernels of consecutive iterations with programmatic
+                                 dependent launches (default), 0 = ordinary stream order */
 
 /* ---- kernel ids for vegas_kernel_time ---- */
 #define VEGAS_KERNEL_FILL 0   /* per-event kernel */

@@ -27,11 +27,11 @@
 
 namespace gv {
 cudaError_t launch_fill_gauss(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
-                              cudaStream_t s);
+                              cudaStream_t s, bool pdl);
 cudaError_t launch_fill_dy(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
-                           cudaStream_t s);
+                           cudaStream_t s, bool pdl);
 cudaError_t launch_fill_ee3j(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
-                             cudaStream_t s);
+                             cudaStream_t s, bool pdl);
 cudaError_t launch_fill_gauss_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
                                    long long n, double* w, int* bins, cudaStream_t s);
 cudaError_t launch_fill_dy_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
@@ -57,11 +57,11 @@ cudaError_t& gv_last_cuda_error() {
 }
 
 cudaError_t launch_fill_any(int ig, int fp32, int ept, const GvFillArgs& a, int n_tiles,
-                            size_t smem, cudaStream_t s) {
+                            size_t smem, cudaStream_t s, bool pdl) {
   switch (ig) {
-    case GV_GAUSS: return gv::launch_fill_gauss(fp32, ept, a, n_tiles, smem, s);
-    case GV_DY: return gv::launch_fill_dy(fp32, ept, a, n_tiles, smem, s);
-    case GV_EE3J: return gv::launch_fill_ee3j(fp32, ept, a, n_tiles, smem, s);
+    case GV_GAUSS: return gv::launch_fill_gauss(fp32, ept, a, n_tiles, smem, s, pdl);
+    case GV_DY: return gv::launch_fill_dy(fp32, ept, a, n_tiles, smem, s, pdl);
+    case GV_EE3J: return gv::launch_fill_ee3j(fp32, ept, a, n_tiles, smem, s, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -121,6 +121,7 @@ struct vegas_ctx {
   uint32_t batch = 0;
   double alpha = 1.5;
   int fp32 = 0, adapt = 1, ept_opt = 0, nonfinite_policy = 0, use_graph = 1, timing = 0;
+  int pdl = 1;
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -246,6 +247,7 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.has_bins = p.mode == 0;
   r.k = k;
   r.last = k == p.itmx - 1;
+  r.refine_follows = (p.mode == 0 && c->adapt) ? 1 : 0;
   r.mode = p.mode;
   r.ncall = p.ncall;
   r.inv_c = 1.0 / (double)p.ncall;
@@ -267,6 +269,9 @@ GvRefineArgs refine_args(const vegas_ctx* c) {
   GvRefineArgs r;
   r.ndim = c->ndim;
   r.nbins = c->nbins;
+  r.nch = 1;
+  r.nacc = 2 + c->ndim * c->nbins;
+  r.acc = c->acc;
   r.alpha = c->alpha;
   r.inv_nbins = 1.0 / (double)c->nbins;
   r.logtab = c->logtab;
@@ -293,10 +298,10 @@ int ensure_consts(vegas_ctx* c, int ig, const double* params, int np) {
   return VEGAS_OK;
 }
 
-cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept) {
+cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pdl = false) {
   const GvFillArgs a = fill_args(c, p);
-  if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream);
-  return launch_fill_any(p.ig, p.fp32, ept, a, p.n_tiles, p.smem, c->stream);
+  if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
+  return launch_fill_any(p.ig, p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
 }
 
 // Pick events per thread by timing one fill launch per candidate.  Runs
@@ -387,13 +392,16 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
   const GvRefineArgs rf = refine_args(c);
   const bool refine = p.mode == 0 && c->adapt;
   if (refine) GV_TRY(gv::prepare_refine(c->ndim, c->nbins));
+  // programmatic launches chain the kernels of consecutive iterations; the
+  // first fill follows ordinary work and timed runs keep plain launches
+  const bool pdl = c->pdl && !ev;
   for (int k = 0; k < p.itmx; ++k) {
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k], c->stream, flags));
-    GV_TRY(launch_fill_plan(c, p, p.ept));
+    GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 1], c->stream, flags));
-    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), c->stream));
+    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), c->stream, pdl));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 2], c->stream, flags));
-    if (refine) GV_TRY(gv::launch_refine(rf, c->stream));
+    if (refine) GV_TRY(gv::launch_refine(rf, c->stream, pdl));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 3], c->stream, flags));
   }
   return VEGAS_OK;
@@ -422,8 +430,8 @@ void drop_oldest_entry(vegas_ctx* c) {
 int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* params, int np,
                   int mode) {
   if (c->pending) {
-    // results of an unfetched launch are dropped; wait so that no work overlaps
-    GV_TRY(cudaStreamSynchronize(c->stream));
+    // the results of an unfetched launch are superseded (work stays in stream
+    // order, so nothing overlaps); its timing events are dropped
     c->pending = false;
     c->pending_events.clear();
   }
@@ -469,8 +477,8 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
     return VEGAS_OK;
   }
   char kb[320];
-  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d:%llu:%u:%p:%p", ig, p.fp32, mode,
-           (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing,
+  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d%d:%llu:%u:%p:%p", ig, p.fp32, mode,
+           (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing, c->pdl,
            (unsigned long long)c->seed, c->batch, c->ws, (void*)c->stream);
   const std::string key(kb);
   GraphEntry* ge = find_entry(c, key);
@@ -607,7 +615,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
     return VEGAS_ECUDA;
   }
   c->own_stream = true;
-  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins);
+  // accumulator slots: channel sums, bin sums, per-axis totals
+  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins + ndim);
   const size_t gd = grid_doubles(ndim, nbins);
   size_t off = 0;
   const size_t o_grid = off;
@@ -722,6 +731,11 @@ int vegas_set_option(vegas_ctx* c, int key, double v) {
     case VEGAS_OPT_TIMING:
       if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
       c->timing = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_PDL:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      c->pdl = (int)v;
+      clear_graphs(c);
       return VEGAS_OK;
     case VEGAS_OPT_BATCH_ID:
       if (v < 0.0 || v >= 16777216.0 || v != std::floor(v)) return VEGAS_EINVAL;

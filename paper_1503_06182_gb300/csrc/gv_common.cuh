@@ -44,7 +44,7 @@ struct GvState {
   int done_refine;                    // refine CTAs finished (last-block ticket)
   int status;                         // device error word (0 = ok)
   int E[GV_MAXCH];                    // per-channel iteration scale (atomicMax)
-  int pad;
+  int E0_prev;                        // channel-0 scale of the last finished iteration
   double integral, error, chi2;
   double grad[GV_NGRAD], grad_err[GV_NGRAD];
 };
@@ -79,8 +79,11 @@ struct GvFillArgs {
 };
 
 // Arguments of the reduce/finalize kernel.
+// Accumulator slots: [0, 2*nch) channel sums, then (forward) ndim*nbins bin
+// sums, then (forward) ndim exact per-axis totals of 6 x the smoothed bin sums.
 struct GvReduceArgs {
   int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
+  int refine_follows;            // 1: the refine kernel converts and resets the bin slots
   long long ncall;
   double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration
   int n_tiles, tiles_per_cta;
@@ -90,15 +93,16 @@ struct GvReduceArgs {
   unsigned long long* acc;       // [nacc][4] accumulator limbs (3 used)
   double* sums;                  // [nacc] FP64 sums of the last iteration
   double* per_iter;              // forward: [itmx][2]; adjoint: [itmx][2 + 2*NGRAD]
-  double* inv_total;             // [ndim] 1 / (sum of the smoothed bin sums), 0 if none
+  double* inv_total;             // [ndim] 1 / (6 x sum of the smoothed bin sums), 0 if none
 };
 
 // Arguments of the refine kernel.
 struct GvRefineArgs {
-  int ndim, nbins;
+  int ndim, nbins, nch, nacc;
   double alpha, inv_nbins;
   const double* logtab;          // table of the FP64 log (see gv_reduce.cu)
-  const double* dsum;            // [ndim][nbins] bin sums of w^2
+  unsigned long long* acc;       // accumulator limbs (bin slots are read, then reset)
+  double* dsum;                  // [ndim][nbins] FP64 bin sums (written here)
   const double* inv_total;       // [ndim] from the reduce kernel
   double* grid;                  // grid pack (refined in place)
   double* scratch;               // 4 * d * (N+1) doubles
@@ -141,6 +145,37 @@ __device__ __forceinline__ void gv_event_words(unsigned long long seed, uint32_t
       if (4 * j + 3 < MAXD) r[4 * j + 3] = o.w;
     }
   }
+}
+
+// ----------------------------------------------------------------------------
+// Programmatic dependent launch: the kernels of an iteration (fill -> reduce
+// -> refine -> next fill) are launched with programmatic stream serialisation,
+// so each one is scheduled while its predecessor finishes.  A kernel must wait
+// before it reads anything its predecessor (or earlier work) wrote; it lets its
+// successor launch once the rest of its own work is short.  Both are no-ops
+// for a plain launch.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void gv_wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void gv_allow_next_grid() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t gv_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // ----------------------------------------------------------------------------
@@ -272,11 +307,11 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // ----------------------------------------------------------------------------
 namespace gv {
 cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
-                                size_t smem, cudaStream_t s);
+                                size_t smem, cudaStream_t s, bool pdl);
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
-cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s);
+cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s, bool pdl);
 cudaError_t prepare_refine(int d, int N);
-cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s);
+cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl);
 size_t refine_smem_bytes(int d, int N);
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);
 cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, cudaStream_t s);

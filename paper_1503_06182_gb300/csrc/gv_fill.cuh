@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   const int tid = threadIdx.x;
 
   for (int k = tid; k < 4 * dN; k += B) hist[k] = 0u;
+  gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
   gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   }
   const u128 t1 = gv_block_sum128<NW>(s1, red_128);
   const u128 t2 = gv_block_sum128<NW>(s2, red_128);
+  gv_allow_next_grid();
   ulonglong2* out = a.part + (size_t)tile * a.nacc;
   if (tid == 0) {
     out[0] = make_ulonglong2(t1.lo, t1.hi);
@@ -360,6 +362,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
   Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
   const int tid = threadIdx.x;
+  gv_wait_prior_grid();
   gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
   GvConst<Real, 22> K;
   K.load(a.kconst);
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     }
   }
   ulonglong2* out = a.part + (size_t)tile * a.nacc;
+  gv_allow_next_grid();
 #pragma unroll
   for (int c = 0; c < NCH; ++c) {
     const unsigned long long M = gv_block_max<NW>(mx[c], red_u64);

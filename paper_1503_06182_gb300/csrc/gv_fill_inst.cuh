@@ -11,32 +11,32 @@ static cudaError_t gv_prepare(KernelT k, size_t smem) {
 
 template <int IG, typename Real, int EPT, int MAXD>
 static cudaError_t gv_launch_fill_t(const GvFillArgs& a, int n_tiles, size_t smem,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, bool pdl) {
   auto k = gv_fill_kernel<IG, Real, EPT, MAXD>;
   cudaError_t e = gv_prepare(k, smem);
   if (e != cudaSuccess) return e;
-  k<<<n_tiles, GV_TILE / EPT, smem, s>>>(a);
-  return cudaGetLastError();
+  return gv_launch(k, dim3(n_tiles), dim3(GV_TILE / EPT), smem, s, pdl, a);
 }
 
 template <int IG, typename Real, int MAXD>
 static cudaError_t gv_launch_fill_ept(int ept, const GvFillArgs& a, int n_tiles, size_t smem,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, bool pdl) {
   switch (ept) {
-    case 1: return gv_launch_fill_t<IG, Real, 1, MAXD>(a, n_tiles, smem, s);
-    case 2: return gv_launch_fill_t<IG, Real, 2, MAXD>(a, n_tiles, smem, s);
-    case 4: return gv_launch_fill_t<IG, Real, 4, MAXD>(a, n_tiles, smem, s);
-    case 8: return gv_launch_fill_t<IG, Real, 8, MAXD>(a, n_tiles, smem, s);
+    case 1: return gv_launch_fill_t<IG, Real, 1, MAXD>(a, n_tiles, smem, s, pdl);
+    case 2: return gv_launch_fill_t<IG, Real, 2, MAXD>(a, n_tiles, smem, s, pdl);
+    case 4: return gv_launch_fill_t<IG, Real, 4, MAXD>(a, n_tiles, smem, s, pdl);
+    case 8: return gv_launch_fill_t<IG, Real, 8, MAXD>(a, n_tiles, smem, s, pdl);
   }
   return cudaErrorInvalidValue;
 }
 
 template <int IG, typename Real>
 static cudaError_t gv_launch_fill_maxd(int ept, const GvFillArgs& a, int n_tiles, size_t smem,
-                                       cudaStream_t s) {
-  if (a.ndim <= 4 && IG != GV_EE3J) return gv_launch_fill_ept<IG, Real, 4>(ept, a, n_tiles, smem, s);
-  if (a.ndim <= 8) return gv_launch_fill_ept<IG, Real, 8>(ept, a, n_tiles, smem, s);
-  if (a.ndim <= 16) return gv_launch_fill_ept<IG, Real, 16>(ept, a, n_tiles, smem, s);
+                                       cudaStream_t s, bool pdl) {
+  if (a.ndim <= 4 && IG != GV_EE3J)
+    return gv_launch_fill_ept<IG, Real, 4>(ept, a, n_tiles, smem, s, pdl);
+  if (a.ndim <= 8) return gv_launch_fill_ept<IG, Real, 8>(ept, a, n_tiles, smem, s, pdl);
+  if (a.ndim <= 16) return gv_launch_fill_ept<IG, Real, 16>(ept, a, n_tiles, smem, s, pdl);
   return cudaErrorInvalidValue;
 }
 
@@ -53,9 +53,9 @@ static cudaError_t gv_launch_eval_t(const GvFillArgs& a, uint32_t it, const long
 #define GV_DEFINE_FILL_LAUNCHER(NAME, IG)                                                     \
   namespace gv {                                                                              \
   cudaError_t NAME(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,          \
-                   cudaStream_t s) {                                                          \
-    return fp32 ? gv_launch_fill_maxd<IG, float>(ept, a, n_tiles, smem, s)                    \
-                : gv_launch_fill_maxd<IG, double>(ept, a, n_tiles, smem, s);                  \
+                   cudaStream_t s, bool pdl) {                                                \
+    return fp32 ? gv_launch_fill_maxd<IG, float>(ept, a, n_tiles, smem, s, pdl)               \
+                : gv_launch_fill_maxd<IG, double>(ept, a, n_tiles, smem, s, pdl);             \
   }                                                                                           \
   cudaError_t NAME##_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,    \
                           long long n, double* w, int* bins, cudaStream_t s) {                \

@@ -13,12 +13,13 @@
 // is associative: the totals do not depend on the grid or on timing.  The
 // last CTA to finish (a ticket, no waiting) rounds the totals to FP64 once,
 // records I_k and sigma_k, combines the stage and forms the per-axis totals
-// of the smoothed bin sums exactly.
+// of the smoothed bin sums (accumulated exactly by the reduce CTAs).
 //
 // gv_refine_kernel then refines the grid (Lepage's VEGAS, cited in Section
 // 2.1): smoothing, normalisation, compression ((1-rho)/(-ln rho))^alpha and
-// redistribution into N equal shares.  The compression (an FP64 log per bin)
-// is spread over CTAs; the last one places the new edges from shared memory.
+// redistribution into N equal shares.  Smoothing is done exactly on the bin
+// integers; the compression (an FP64 log per bin) is spread over CTAs; the
+// last one places the new edges from shared memory.
 //
 // On this chip an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles
 // and the FP64 library log takes ~2000 cycles: the serial code here keeps its
@@ -161,13 +162,6 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
   return v;
 }
 
-// Smoothed bin sum: (d_{i-1} + d_i + d_{i+1})/3 inside, 2-point means at the ends.
-__device__ __forceinline__ double smoothed(const double* da, int i, int N) {
-  if (i == 0) return (da[0] + da[1]) * 0.5;
-  if (i == N - 1) return (da[N - 2] + da[N - 1]) * 0.5;
-  return (da[i - 1] + da[i] + da[i + 1]) * (1.0 / 3.0);
-}
-
 // ---------------------------------------------------------------------------
 // Natural log of a positive double, table-driven (P. T. P. Tang,
 // "Table-driven implementation of the logarithm function in IEEE
@@ -280,12 +274,33 @@ __device__ void combine_stage_warp(const double* per_iter, int stride, int m, do
   }
 }
 
+// Integer weight c_j of bin j in 6 x (sum of the smoothed bin sums of an axis):
+// the end entries (d_0+d_1)/2, (d_{N-2}+d_{N-1})/2 weigh 3, the inner entries
+// (d_{i-1}+d_i+d_{i+1})/3 weigh 2.
+__device__ __forceinline__ int smooth_weight(int j, int N) {
+  int c = 0;
+  for (int i = max(0, j - 1); i <= min(N - 1, j + 1); ++i) {
+    const bool inside = (i == 0) ? (j <= 1) : (i == N - 1) ? (j >= N - 2) : true;
+    if (inside) c += (i == 0 || i == N - 1) ? 3 : 2;
+  }
+  return c;
+}
+
+__device__ __forceinline__ u192 mul192_small(u192 v, int c) {
+  u192 r = {0ull, 0ull, 0ull};
+  for (int q = 0; q < c; ++q) add192(r, v);
+  return r;
+}
+
 // The last reduce CTA (256 threads).
 __device__ void finalize_iteration(const GvReduceArgs& a) {
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
   GvState* st = a.st;
-  // totals -> FP64 (each rounded once)
-  for (int k = tid; k < a.nacc; k += nthr) {
+  const int d = a.ndim;
+  // channel sums (and the bin sums unless the refine kernel converts them):
+  // each rounded once to FP64
+  const int nconv = a.refine_follows ? 2 * a.nch : a.nacc;
+  for (int k = tid; k < nconv; k += nthr) {
     const int ch = k < 2 * a.nch ? (k >> 1) : 0;
     const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
     const int Eg = st->E[ch];
@@ -307,40 +322,27 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
       if (a.k == 0) st->status = 0;
       st->nonfinite_iter = 0ull;
     }
-  } else if (a.has_bins) {
-    // warps 1..: per-axis totals of the smoothed bin sums, exactly:
-    // 6 sum_i smoothed_i = sum_j c_j d_j with small integer c_j, on the exact
-    // bin integers; one rounding to FP64, stored as 1/total (0: no change)
-    const int d = a.ndim, N = a.nbins;
+  } else if (a.has_bins && tid - 32 < d) {
+    // per-axis totals (slots after the bins, summed exactly by the reduce
+    // CTAs): one rounding, stored as 1/(6 x total), 0 when the axis is empty
+    const int ax = tid - 32;
     const int Eg = st->E[0];
-    for (int ax = wid - 1; ax < d; ax += (nthr >> 5) - 1) {
-      u192 t = {0ull, 0ull, 0ull};
-      if (Eg != GV_EMPTY) {
-        for (int j = lane; j < N; j += 32) {
-          const u192 v = load_acc(a.acc, 2 * a.nch + ax * N + j);
-          int c = 0;
-          for (int i = max(0, j - 1); i <= min(N - 1, j + 1); ++i) {
-            const bool inside = (i == 0) ? (j <= 1) : (i == N - 1) ? (j >= N - 2) : true;
-            if (inside) c += (i == 0 || i == N - 1) ? 3 : 2;
-          }
-          for (int r = 0; r < c; ++r) add192(t, v);
-        }
-      }
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1) {
-        u192 o = {__shfl_xor_sync(0xffffffffu, t.l0, m), __shfl_xor_sync(0xffffffffu, t.l1, m),
-                  __shfl_xor_sync(0xffffffffu, t.l2, m)};
-        add192(t, o);
-      }
-      if (lane == 0) {
-        const double total = u192_to_double(t, 2 * Eg - GV_FB) * (1.0 / 6.0);
-        a.inv_total[ax] = (Eg != GV_EMPTY && total > 0.0) ? __drcp_rn(total) : 0.0;
-      }
+    double inv = 0.0;
+    if (Eg != GV_EMPTY) {
+      const double t6 = u192_to_double(load_acc(a.acc, a.nacc + ax), 2 * Eg - GV_FB);
+      inv = t6 > 0.0 ? __drcp_rn(t6) : 0.0;
     }
+    a.inv_total[ax] = inv;
   }
-  __syncthreads();  // every read of the accumulators is done
-  for (int k = tid; k < GV_ACC_STRIDE * a.nacc; k += nthr) a.acc[k] = 0ull;
+  __syncthreads();  // every read of the accumulators here is done
+  const int nslots = a.has_bins ? a.nacc + d : a.nacc;
+  for (int k = tid; k < GV_ACC_STRIDE * nslots; k += nthr) {
+    const int slot = k / GV_ACC_STRIDE;
+    const bool bin_slot = a.has_bins && slot >= 2 * a.nch && slot < a.nacc;
+    if (!(bin_slot && a.refine_follows)) a.acc[k] = 0ull;
+  }
   if (tid == 0) {
+    st->E0_prev = st->E[0];
     for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
     st->done = 0;
     st->it = st->it + 1ull;
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
   const int t0 = blockIdx.y * a.tiles_per_cta;
   const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
   u192 r = {0ull, 0ull, 0ull};
+  gv_wait_prior_grid();
   if (k < a.nacc) {
     const int ch = k < 2 * a.nch ? (k >> 1) : 0;
     const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
@@ -388,18 +391,40 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
   }
   s_part[wid][lane] = r;
   __syncthreads();
-  if (wid == 0 && k < a.nacc) {
+  if (wid == 0) {
     u192 t = s_part[0][lane];
 #pragma unroll
     for (int w = 1; w < 8; ++w) add192(t, s_part[w][lane]);
-    if (t.l0 | t.l1 | t.l2) red_add_limbs(a.acc + GV_ACC_STRIDE * k, t);
+    if (k < a.nacc && (t.l0 | t.l1 | t.l2)) red_add_limbs(a.acc + GV_ACC_STRIDE * k, t);
+    if (a.has_bins) {
+      // this CTA's share of 6 x (sum of the smoothed bin sums) of each axis
+      const int N = a.nbins;
+      const int j = k - 2 * a.nch;  // bin index within [0, d*N)
+      const bool is_bin = k < a.nacc && j >= 0;
+      const u192 ct = is_bin ? mul192_small(t, smooth_weight(j % N, N)) : u192{0ull, 0ull, 0ull};
+      const int k0 = blockIdx.x * 32;
+      const int j_first = max(0, k0 - 2 * a.nch);
+      const int j_last = min(a.nacc - 1, k0 + 31) - 2 * a.nch;
+      for (int ax = j_first / N; j_last >= 0 && ax <= j_last / N; ++ax) {
+        u192 v = (is_bin && j / N == ax) ? ct : u192{0ull, 0ull, 0ull};
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+          u192 o = {__shfl_xor_sync(0xffffffffu, v.l0, m), __shfl_xor_sync(0xffffffffu, v.l1, m),
+                    __shfl_xor_sync(0xffffffffu, v.l2, m)};
+          add192(v, o);
+        }
+        if (lane == 0 && (v.l0 | v.l1 | v.l2))
+          red_add_limbs(a.acc + GV_ACC_STRIDE * (a.nacc + ax), v);
+      }
+    }
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0)
     is_last = (atomicAdd(&a.st->done, 1) == (int)(gridDim.x * gridDim.y) - 1) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
+  gv_allow_next_grid();
   __threadfence();
   finalize_iteration(a);
 }
@@ -472,27 +497,54 @@ __global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRe
   double* gsl = a.scratch + dN;             // [dN] slope
   double* ne = a.scratch + 2 * (size_t)dN;  // [d(N+1)] new edges
   const double* e64 = a.grid;               // the pack starts with e64
+  gv_wait_prior_grid();
   if (wid == 0) {
     const int k = blockIdx.x * GV_REFINE_BINS + lane;
     if (k < dN) {
       const int ax = k / N, i = k - ax * N;
+      const int base = 2 * a.nch + ax * N;  // slot of bin 0 of this axis
+      const int Eg = a.st->E0_prev;
+      const u192 z = {0ull, 0ull, 0ull};
+      const u192 dm = i > 0 ? load_acc(a.acc, base + i - 1) : z;
+      const u192 dc = load_acc(a.acc, base + i);
+      const u192 dp = i < N - 1 ? load_acc(a.acc, base + i + 1) : z;
+      // 6 x the smoothed sum, exactly: 3 (d_0 + d_1) at the ends,
+      // 2 (d_{i-1} + d_i + d_{i+1}) inside
+      u192 s6 = dc;
+      if (i == 0) {
+        add192(s6, dp);
+        s6 = mul192_small(s6, 3);
+      } else if (i == N - 1) {
+        add192(s6, dm);
+        s6 = mul192_small(s6, 3);
+      } else {
+        add192(s6, dm);
+        add192(s6, dp);
+        s6 = mul192_small(s6, 2);
+      }
+      const int q = 2 * Eg - GV_FB;
+      a.dsum[k] = Eg != GV_EMPTY ? u192_to_double(dc, q) : 0.0;
       const double it = a.inv_total[ax];
       double rv = 0.0, sl = 0.0;
       if (it > 0.0) {
-        rv = compress(smoothed(a.dsum + (size_t)ax * N, i, N) * it, a.alpha, a.logtab);
+        rv = compress(u192_to_double(s6, q) * it, a.alpha, a.logtab);
         if (rv > 0.0)
           sl = (e64[ax * (N + 1) + i + 1] - e64[ax * (N + 1) + i]) * __drcp_rn(rv);
       }
       gr[k] = rv;
       gsl[k] = sl;
     }
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) is_last = (atomicAdd(&a.st->done_refine, 1) == (int)gridDim.x - 1) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
+  gv_allow_next_grid();
   __threadfence();
+  // every phase-1 CTA has read the bin slots: reset them for the next iteration
+  for (int k = tid; k < GV_ACC_STRIDE * dN; k += GV_REFINE_THREADS)
+    a.acc[GV_ACC_STRIDE * 2 * a.nch + k] = 0ull;
   double* r = sm;                 // [dN]
   double* slope = r + dN;         // [dN]
   double* cum = slope + dN;       // [d(N+1)]
@@ -660,12 +712,11 @@ void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy) {
   *gy = (n_tiles + tpc - 1) / tpc;
 }
 
-cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s) {
+cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s, bool pdl) {
   int tpc, gx, gy;
   reduce_grid(a.n_tiles, a.nacc, &tpc, &gx, &gy);
   if (tpc != a.tiles_per_cta) return cudaErrorInvalidValue;
-  gv_reduce_kernel<<<dim3(gx, gy), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return gv_launch(gv_reduce_kernel, dim3(gx, gy), dim3(256), 0, s, pdl, a);
 }
 
 cudaError_t prepare_refine(int d, int N) {
@@ -676,10 +727,10 @@ cudaError_t prepare_refine(int d, int N) {
   return cudaSuccess;
 }
 
-cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s) {
+cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl) {
   const int ctas = (a.ndim * a.nbins + GV_REFINE_BINS - 1) / GV_REFINE_BINS;
-  gv_refine_kernel<<<ctas, GV_REFINE_THREADS, refine_smem_bytes(a.ndim, a.nbins), s>>>(a);
-  return cudaGetLastError();
+  return gv_launch(gv_refine_kernel, dim3(ctas), dim3(GV_REFINE_THREADS),
+                   refine_smem_bytes(a.ndim, a.nbins), s, pdl, a);
 }
 
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s) {

@@ -22,6 +22,7 @@ VEGAS_ENONFINITE, VEGAS_EDEVICE, VEGAS_ESTATE = -5, -6, -7
 VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J = 0, 1, 2
 VEGAS_OPT_ALPHA, VEGAS_OPT_PRECISION, VEGAS_OPT_ADAPT, VEGAS_OPT_EPT = 0, 1, 2, 3
 VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH, VEGAS_OPT_TIMING, VEGAS_OPT_BATCH_ID = 4, 5, 6, 7
+VEGAS_OPT_PDL = 8
 VEGAS_KERNEL_FILL, VEGAS_KERNEL_REDUCE, VEGAS_KERNEL_REFINE = 0, 1, 2
 VEGAS_NGRAD = 5
 VEGAS_MAX_PARAMS = 16
