@@ -42,6 +42,19 @@ def _fp32_peak_tflops():
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (the whole job is as slow as its
+    slowest replica); the value itself on a single process."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -161,11 +174,7 @@ def run_gpu(args):
     step_ms, _ = timed_steps(g32, K)
     barrier()
     t_wall1 = time.time()
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), dev)
     value = world * K * NCALL / (tot_ms * 1e-3)
 
     # end to end through the blocking C ABI: host params in, host results out
@@ -178,11 +187,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         g32.iterate(NCALL, 1, DY, p)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(t.item())
+    e2e_tot = max_over_ranks(sum(e2e_ms), dev)
     e2e_value = world * K * NCALL / (e2e_tot * 1e-3)
     t_wall2 = time.time()
 

@@ -192,9 +192,12 @@ int vegas_kernel_time(vegas_ctx* ctx, int kernel, double* total_ms, int64_t* lau
 int vegas_get_ept(const vegas_ctx* ctx, int* ept);
 
 /* ---- batched integrations (many independent VEGAS runs per launch) ----
- * n integrations of uneven dimension and call count run as one persistent
- * fill launch per iteration over a work list of (integration, tile), then
- * one reduce launch; the itmx iterations are captured in one CUDA graph.
+ * n integrations of uneven dimension, call count and integrand run as one
+ * persistent fill launch per iteration over a work list of (integration,
+ * tile) items taken largest-first from a device counter, then one reduce and
+ * one refine launch serving every integration; the itmx iterations are
+ * captured in one CUDA graph (Section 2.1: many independent runs, here
+ * sharing one device).  All integrations share nbins and seed.
  * Integration b uses Philox batch word b, so its events are those of a
  * single context with VEGAS_OPT_BATCH_ID = b, and its results are
  * bit-identical to that context's.
@@ -206,12 +209,16 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
                        const double* params, const int* nparams, int nbins, uint64_t seed,
                        int precision, vegas_batch** out);
 void vegas_batch_free(vegas_batch* b);
+/* Keys: VEGAS_OPT_ALPHA, VEGAS_OPT_ADAPT, VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH
+ * as for a context; VEGAS_OPT_EPT 0 (autotune), 4 or 8.  The precision is
+ * fixed at creation (VEGAS_EINVAL otherwise). */
 int vegas_batch_set_option(vegas_batch* b, int key, double value);
 int vegas_batch_set_stream(vegas_batch* b, void* stream);
 /* itmx iterations of every integration; integral/error/chi2_dof: n values;
  * per_iter (nullable): n x itmx x (I_k, sigma_k).  Blocking. */
 int vegas_batch_iterate(vegas_batch* b, int itmx, double* integral, double* error,
                         double* chi2_dof, double* per_iter);
+/* Edges of integration `index`: ndim[index] x (nbins+1) doubles. */
 int vegas_batch_grid_get(const vegas_batch* b, int index, double* edges);
 
 /* Human-readable text of a status code (static storage). */

@@ -1,20 +1,729 @@
-// gv_batch.cu -- batched integrations (persistent fill over a work list).
+// gv_batch.cu -- many independent VEGAS integrations per launch.
+//
+// The paper contrasts one run whose events all feed one grid with many
+// independent runs (Section 2.1); here many *different* integrations (uneven
+// dimension, call count and integrand) share the GPU.  Each iteration is
+//   one persistent fill launch over a work list of (integration, tile) items,
+//   one reduce launch whose CTAs serve all integrations (task table),
+//   one refine launch likewise,
+// and the itmx iterations are captured in one CUDA graph.  The work list
+// orders the integrations by decreasing expected cost (largest first) and
+// CTAs take items from an integer counter; since every tile is summed
+// exactly, the schedule cannot change any result.  Integration b uses Philox
+// batch word b, so its results are bit-identical to those of a single
+// context with VEGAS_OPT_BATCH_ID = b.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
 #include "../../include/vegas.h"
+#include "gv_fill.cuh"
+
+// ---------------------------------------------------------------------------
+// Persistent fill over the work list.
+// ---------------------------------------------------------------------------
+template <typename Real, int EPT>
+__global__ void __launch_bounds__(GV_TILE / EPT)
+    gv_fill_batch_kernel(const GvFillArgs* __restrict__ args, const int* __restrict__ ig_of,
+                         const int* __restrict__ order, const long long* __restrict__ item_start,
+                         int n, long long total, unsigned long long* counter) {
+  constexpr int B = GV_TILE / EPT;
+  constexpr int NW = B / 32;
+  constexpr int MAXD = GV_MAXD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red_u64[NW];
+  __shared__ u128 red_128[NW];
+  __shared__ long long s_item;
+  __shared__ int s_pos;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(counter, 1ull);
+      int pos = 0;
+      if (item < total) {  // last position whose first item is <= item
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (item_start[mid] <= item)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        pos = lo;
+      }
+      s_item = item;
+      s_pos = pos;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= total) break;
+    const int pos = s_pos;
+    const int b = order[pos];
+    const long long tile = item - item_start[pos];
+    const GvFillArgs a = args[b];
+    const GvFillSmem lay(a.ndim, a.nbins, (int)sizeof(Real), true, true);
+    unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
+    for (int k = threadIdx.x; k < 4 * a.ndim * a.nbins; k += B) hist[k] = 0u;
+    if (b != cur) {
+      gv_stage_grid<Real>(a.grid, a.ndim, a.nbins, reinterpret_cast<double*>(smem + lay.jac),
+                          reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew),
+                          threadIdx.x, B);
+      cur = b;
+    }
+    const uint32_t it = (uint32_t)a.st->it;
+    __syncthreads();
+    switch (ig_of[b]) {
+      case GV_GAUSS:
+        gv_fill_tile<GV_GAUSS, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+      case GV_DY:
+        gv_fill_tile<GV_DY, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+      default:
+        gv_fill_tile<GV_EE3J, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Real, int EPT>
+static cudaError_t gv_fill_batch_launch(int ctas, size_t smem, cudaStream_t s,
+                                        const GvFillArgs* args, const int* ig_of,
+                                        const int* order, const long long* item_start, int n,
+                                        long long total, unsigned long long* counter) {
+  auto k = gv_fill_batch_kernel<Real, EPT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<ctas, GV_TILE / EPT, smem, s>>>(args, ig_of, order, item_start, n, total, counter);
+  return cudaGetLastError();
+}
+
+template <typename Real, int EPT>
+static int gv_fill_batch_occupancy(size_t smem) {
+  auto k = gv_fill_batch_kernel<Real, EPT>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, GV_TILE / EPT, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return blocks;
+}
+
+namespace {
+
+#define GB_TRY(expr)                 \
+  do {                               \
+    if ((expr) != cudaSuccess) {     \
+      cudaGetLastError();            \
+      return VEGAS_ECUDA;            \
+    }                                \
+  } while (0)
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int batch_check_params(int ig, int ndim, const double* p, int np) {
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(p[i])) return VEGAS_EINVAL;
+  switch (ig) {
+    case VEGAS_GAUSS: return (np == 1 && ndim >= 1 && p[0] > 0.0) ? VEGAS_OK : VEGAS_EINVAL;
+    case VEGAS_DY:
+      return (np == 10 && ndim >= 4 && p[0] > 0 && p[1] > 0 && p[2] > 0 && p[3] > 0 && p[3] < 1 &&
+              p[4] > 0 && p[5] > 0 && p[6] > p[5] && p[6] < p[0] && p[9] > 0)
+                 ? VEGAS_OK
+                 : VEGAS_EINVAL;
+    case VEGAS_EE3J:
+      return ((np == 1 || np == 2) && ndim >= 5 && p[0] > 0.0 && p[0] < 1.0 &&
+              (np == 1 || p[1] > 0.0))
+                 ? VEGAS_OK
+                 : VEGAS_EINVAL;
+  }
+  return VEGAS_EINVAL;
+}
+
+// Rough relative cost of one tile, for the largest-first order only.
+double tile_cost(int ig, int d) {
+  switch (ig) {
+    case VEGAS_GAUSS: return 1.0 + 0.25 * d;
+    case VEGAS_DY: return 3.0 + 0.25 * d;
+    default: return 2.5 + 0.25 * d;
+  }
+}
+
+struct Member {
+  int ig, d, np, n_tiles, nacc, nslots;
+  int64_t ncall;
+  double params[GV_MAXPARAMS];
+  double* grid;
+  GvState* st;
+  double* par;
+  double* kconst;
+  unsigned long long* acc;
+  double* sums;
+  double* scratch;
+  ulonglong2* part;
+  int* tileE;
+  int* binE;
+};
+
+}  // namespace
+
+struct vegas_batch {
+  int n = 0, N = 0;
+  uint64_t seed = 0;
+  int fp32 = 1, adapt = 1, ept_opt = 0, nonfinite_policy = 0, use_graph = 1;
+  double alpha = 1.5;
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Member> m;
+  void* dmem = nullptr;
+  // per-iteration records [n][cap][2]
+  double* per_iter = nullptr;
+  int per_iter_cap = 0;
+  // launch tables
+  GvFillArgs* d_fill = nullptr;
+  GvReduceArgs* d_red = nullptr;
+  GvRefineArgs* d_ref = nullptr;
+  int4* d_red_tasks = nullptr;
+  int4* d_ref_tasks = nullptr;
+  int n_red_tasks = 0, n_ref_tasks = 0;
+  int* d_ig = nullptr;
+  int* d_order = nullptr;
+  long long* d_item_start = nullptr;
+  long long total_items = 0;
+  unsigned long long* d_counter = nullptr;
+  double* logtab = nullptr;
+  size_t fill_smem = 0, refine_smem = 0;
+  int ept = 0, fill_ctas = 0;
+  // graph cache
+  std::string graph_key;
+  cudaGraphExec_t graph = nullptr;
+  // pinned results
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+};
+
+namespace {
+
+cudaError_t fill_batch(vegas_batch* B, int ept) {
+  const int n = B->n;
+  switch (ept * 2 + B->fp32) {
+    case 8 * 2 + 1:
+      return gv_fill_batch_launch<float, 8>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
+                                            B->d_ig, B->d_order, B->d_item_start, n,
+                                            B->total_items, B->d_counter);
+    case 4 * 2 + 1:
+      return gv_fill_batch_launch<float, 4>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
+                                            B->d_ig, B->d_order, B->d_item_start, n,
+                                            B->total_items, B->d_counter);
+    case 8 * 2 + 0:
+      return gv_fill_batch_launch<double, 8>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
+                                             B->d_ig, B->d_order, B->d_item_start, n,
+                                             B->total_items, B->d_counter);
+    case 4 * 2 + 0:
+      return gv_fill_batch_launch<double, 4>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
+                                             B->d_ig, B->d_order, B->d_item_start, n,
+                                             B->total_items, B->d_counter);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int occupancy(vegas_batch* B, int ept) {
+  if (ept == 8)
+    return B->fp32 ? gv_fill_batch_occupancy<float, 8>(B->fill_smem)
+                   : gv_fill_batch_occupancy<double, 8>(B->fill_smem);
+  return B->fp32 ? gv_fill_batch_occupancy<float, 4>(B->fill_smem)
+                 : gv_fill_batch_occupancy<double, 4>(B->fill_smem);
+}
+
+int reset_all(vegas_batch* B) {
+  for (const Member& x : B->m)
+    GB_TRY(gv::launch_reset(x.st, x.nslots, x.acc, x.binE, x.d * B->N, B->stream));
+  return VEGAS_OK;
+}
+
+// (Re)build the device argument tables; per_iter must be allocated.
+int upload_tables(vegas_batch* B) {
+  const int n = B->n;
+  std::vector<GvFillArgs> fa(n);
+  std::vector<GvReduceArgs> ra(n);
+  std::vector<GvRefineArgs> fr(n);
+  std::vector<int4> rt, ft;
+  for (int b = 0; b < n; ++b) {
+    const Member& x = B->m[b];
+    GvFillArgs& a = fa[b];
+    memset(&a, 0, sizeof a);
+    a.ndim = x.d;
+    a.nbins = B->N;
+    a.nch = 1;
+    a.nacc = x.nacc;
+    a.ncall = x.ncall;
+    a.seed = B->seed;
+    a.batch = (unsigned)b;
+    a.kconst = x.kconst;
+    a.grid = x.grid;
+    a.st = x.st;
+    a.part = x.part;
+    a.tileE = x.tileE;
+    a.binE = x.binE;
+    GvReduceArgs& r = ra[b];
+    memset(&r, 0, sizeof r);
+    r.ndim = x.d;
+    r.nbins = B->N;
+    r.nch = 1;
+    r.nacc = x.nacc;
+    r.has_bins = 1;
+    r.refine_follows = B->adapt;
+    r.mode = 0;
+    r.ncall = x.ncall;
+    r.inv_c = 1.0 / (double)x.ncall;
+    r.inv_cm1 = 1.0 / (double)(x.ncall - 1);
+    r.n_tiles = x.n_tiles;
+    int gx = 0, gy = 0;
+    gv::reduce_grid(x.n_tiles, x.nacc, &r.tiles_per_cta, &gx, &gy);
+    r.part = x.part;
+    r.tileE = x.tileE;
+    r.st = x.st;
+    r.acc = x.acc;
+    r.sums = x.sums;
+    r.per_iter = B->per_iter + (size_t)b * B->per_iter_cap * 2;
+    r.inv_total = x.scratch + 4 * (size_t)x.d * (B->N + 1);
+    r.binE = x.binE;
+    for (int yy = 0; yy < gy; ++yy)
+      for (int xx = 0; xx < gx; ++xx) rt.push_back(make_int4(b, xx, yy, gx * gy));
+    GvRefineArgs& f = fr[b];
+    memset(&f, 0, sizeof f);
+    f.ndim = x.d;
+    f.nbins = B->N;
+    f.nch = 1;
+    f.nacc = x.nacc;
+    f.alpha = B->alpha;
+    f.inv_nbins = 1.0 / (double)B->N;
+    f.logtab = B->logtab;
+    f.acc = x.acc;
+    f.dsum = x.sums + 2;
+    f.inv_total = r.inv_total;
+    f.grid = x.grid;
+    f.scratch = x.scratch;
+    f.st = x.st;
+    f.binE = x.binE;
+    const int nr = gv::refine_ctas(x.d, B->N);
+    for (int xx = 0; xx < nr; ++xx) ft.push_back(make_int4(b, xx, 0, nr));
+  }
+  // tables live in one allocation, reallocated when the task counts change
+  cudaFree(B->d_fill);
+  B->d_fill = nullptr;
+  const size_t bytes = a256(sizeof(GvFillArgs) * n) + a256(sizeof(GvReduceArgs) * n) +
+                       a256(sizeof(GvRefineArgs) * n) + a256(sizeof(int4) * rt.size()) +
+                       a256(sizeof(int4) * ft.size());
+  void* t = nullptr;
+  GB_TRY(cudaMalloc(&t, bytes));
+  char* c = (char*)t;
+  B->d_fill = (GvFillArgs*)c;
+  c += a256(sizeof(GvFillArgs) * n);
+  B->d_red = (GvReduceArgs*)c;
+  c += a256(sizeof(GvReduceArgs) * n);
+  B->d_ref = (GvRefineArgs*)c;
+  c += a256(sizeof(GvRefineArgs) * n);
+  B->d_red_tasks = (int4*)c;
+  c += a256(sizeof(int4) * rt.size());
+  B->d_ref_tasks = (int4*)c;
+  B->n_red_tasks = (int)rt.size();
+  B->n_ref_tasks = (int)ft.size();
+  GB_TRY(cudaMemcpy(B->d_fill, fa.data(), sizeof(GvFillArgs) * n, cudaMemcpyHostToDevice));
+  GB_TRY(cudaMemcpy(B->d_red, ra.data(), sizeof(GvReduceArgs) * n, cudaMemcpyHostToDevice));
+  GB_TRY(cudaMemcpy(B->d_ref, fr.data(), sizeof(GvRefineArgs) * n, cudaMemcpyHostToDevice));
+  GB_TRY(cudaMemcpy(B->d_red_tasks, rt.data(), sizeof(int4) * rt.size(), cudaMemcpyHostToDevice));
+  GB_TRY(cudaMemcpy(B->d_ref_tasks, ft.data(), sizeof(int4) * ft.size(), cudaMemcpyHostToDevice));
+  return VEGAS_OK;
+}
+
+int ensure_per_iter(vegas_batch* B, int itmx) {
+  if (itmx <= B->per_iter_cap) return VEGAS_OK;
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    B->graph_key.clear();
+  }
+  cudaFree(B->per_iter);
+  B->per_iter = nullptr;
+  const int cap = std::max(itmx, 16);
+  if (cudaMalloc(&B->per_iter, sizeof(double) * 2 * cap * B->n) != cudaSuccess) {
+    cudaGetLastError();
+    B->per_iter_cap = 0;
+    return VEGAS_ENOMEM;
+  }
+  B->per_iter_cap = cap;
+  return upload_tables(B);
+}
+
+int enqueue_iterations(vegas_batch* B, int itmx) {
+  for (int k = 0; k < itmx; ++k) {
+    GB_TRY(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), B->stream));
+    GB_TRY(fill_batch(B, B->ept));
+    GB_TRY(gv::launch_reduce_batch(B->d_red, B->d_red_tasks, B->n_red_tasks, k, k == itmx - 1,
+                                   k > 0 ? 1.0 / (double)k : 0.0, B->stream));
+    if (B->adapt)
+      GB_TRY(gv::launch_refine_batch(B->d_ref, B->d_ref_tasks, B->n_ref_tasks, B->refine_smem,
+                                     B->stream));
+  }
+  return VEGAS_OK;
+}
+
+// Choose events per thread by timing one fill per candidate (between resets).
+int autotune_batch(vegas_batch* B) {
+  if (B->ept_opt) {
+    B->ept = B->ept_opt;
+  } else {
+    cudaEvent_t e0, e1;
+    GB_TRY(cudaEventCreate(&e0));
+    GB_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_ept = 4;
+    for (int ept : {4, 8}) {
+      B->fill_ctas = std::max(1, occupancy(B, ept)) * B->sm_count;
+      float t = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        GB_TRY(cudaMemsetAsync(B->d_counter, 0, 8, B->stream));
+        GB_TRY(cudaEventRecord(e0, B->stream));
+        GB_TRY(fill_batch(B, ept));
+        GB_TRY(cudaEventRecord(e1, B->stream));
+        GB_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, ms);
+      }
+      if (t < best) {
+        best = t;
+        best_ept = ept;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->ept = best_ept;
+    int st = reset_all(B);
+    if (st) return st;
+  }
+  B->fill_ctas = std::max(1, occupancy(B, B->ept)) * B->sm_count;
+  return VEGAS_OK;
+}
+
+}  // namespace
 
 extern "C" {
-struct vegas_batch {
-  int unused;
-};
-int vegas_batch_create(int, const int*, const int64_t*, const int*, const double*, const int*, int,
-                       uint64_t, int, vegas_batch** out) {
-  if (out) *out = nullptr;
-  return VEGAS_EINVAL;
+
+int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* integrand_id,
+                       const double* params, const int* nparams, int nbins, uint64_t seed,
+                       int precision, vegas_batch** out) {
+  if (!out) return VEGAS_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n > (1 << 20) || !ndim || !ncall || !integrand_id || !params || !nparams ||
+      nbins < VEGAS_MIN_BINS || nbins > VEGAS_MAX_BINS || (precision != 0 && precision != 1))
+    return VEGAS_EINVAL;
+  for (int b = 0; b < n; ++b) {
+    if (ndim[b] < 1 || ndim[b] > VEGAS_MAX_DIM || ndim[b] * nbins > VEGAS_MAX_DIM_BINS ||
+        ncall[b] < 2 || ncall[b] > ((int64_t)1 << 40) || nparams[b] < 0 ||
+        nparams[b] > VEGAS_MAX_PARAMS - 1)
+      return VEGAS_EINVAL;
+    if (batch_check_params(integrand_id[b], ndim[b], params + (size_t)b * VEGAS_MAX_PARAMS,
+                           nparams[b]))
+      return VEGAS_EINVAL;
+  }
+  vegas_batch* B = new vegas_batch();
+  B->n = n;
+  B->N = nbins;
+  B->seed = seed;
+  B->fp32 = precision;
+  if (cudaGetDevice(&B->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete B;
+    return VEGAS_ECUDA;
+  }
+  B->own_stream = true;
+  B->m.resize(n);
+  // one allocation for every member's state, grid, accumulators and partials
+  size_t off = 0;
+  std::vector<size_t> o(n * 10);  // 10 sub-allocations per member
+  for (int b = 0; b < n; ++b) {
+    Member& x = B->m[b];
+    x.ig = integrand_id[b];
+    x.d = ndim[b];
+    x.ncall = ncall[b];
+    x.np = nparams[b];
+    for (int i = 0; i < GV_MAXPARAMS; ++i)
+      x.params[i] = i < x.np ? params[(size_t)b * VEGAS_MAX_PARAMS + i] : 0.0;
+    x.params[GV_MAXPARAMS - 1] = (double)x.np;
+    x.n_tiles = (int)((x.ncall + GV_TILE - 1) / GV_TILE);
+    x.nacc = 2 + x.d * nbins;
+    x.nslots = x.nacc + x.d;
+    size_t* q = &o[b * 10];
+    q[0] = off;
+    off = a256(off + GvGridLayout{x.d, nbins}.doubles() * 8);
+    q[1] = off;
+    off = a256(off + sizeof(GvState));
+    q[2] = off;
+    off = a256(off + GV_MAXPARAMS * 8);
+    q[3] = off;
+    off = a256(off + GV_NCONST * 8);
+    q[4] = off;
+    off = a256(off + (size_t)x.nslots * 4 * 8);
+    q[5] = off;
+    off = a256(off + (size_t)x.nacc * 8);
+    q[6] = off;
+    off = a256(off + ((size_t)4 * x.d * (nbins + 1) + GV_MAXD) * 8);
+    q[7] = off;
+    off = a256(off + (size_t)x.n_tiles * x.nacc * 16);
+    q[8] = off;
+    off = a256(off + (size_t)x.n_tiles * 4);
+    q[9] = off;
+    off = a256(off + (size_t)x.d * nbins * 4);
+  }
+  const size_t o_counter = off;
+  off = a256(off + 8);
+  const size_t o_log = off;
+  off = a256(off + 258 * 8);
+  const size_t o_ig = off;
+  off = a256(off + (size_t)n * 4);
+  const size_t o_order = off;
+  off = a256(off + (size_t)n * 4);
+  const size_t o_start = off;
+  off = a256(off + (size_t)(n + 1) * 8);
+  if (cudaMalloc(&B->dmem, off) != cudaSuccess) {
+    cudaGetLastError();
+    vegas_batch_free(B);
+    return VEGAS_ENOMEM;
+  }
+  char* base = (char*)B->dmem;
+  for (int b = 0; b < n; ++b) {
+    Member& x = B->m[b];
+    const size_t* q = &o[b * 10];
+    x.grid = (double*)(base + q[0]);
+    x.st = (GvState*)(base + q[1]);
+    x.par = (double*)(base + q[2]);
+    x.kconst = (double*)(base + q[3]);
+    x.acc = (unsigned long long*)(base + q[4]);
+    x.sums = (double*)(base + q[5]);
+    x.scratch = (double*)(base + q[6]);
+    x.part = (ulonglong2*)(base + q[7]);
+    x.tileE = (int*)(base + q[8]);
+    x.binE = (int*)(base + q[9]);
+  }
+  B->d_counter = (unsigned long long*)(base + o_counter);
+  B->logtab = (double*)(base + o_log);
+  B->d_ig = (int*)(base + o_ig);
+  B->d_order = (int*)(base + o_order);
+  B->d_item_start = (long long*)(base + o_start);
+  int st = VEGAS_OK;
+  if (cudaMemsetAsync(B->dmem, 0, off, B->stream) != cudaSuccess) st = VEGAS_ECUDA;
+  if (!st && cudaMemcpy(B->logtab, gv::host_log_table(), 258 * sizeof(double),
+                        cudaMemcpyHostToDevice) != cudaSuccess)
+    st = VEGAS_ECUDA;
+  // uniform grids, constants, reset state
+  for (int b = 0; b < n && !st; ++b) {
+    Member& x = B->m[b];
+    std::vector<double> e((size_t)x.d * (nbins + 1));
+    for (int a = 0; a < x.d; ++a)
+      for (int i = 0; i <= nbins; ++i) e[(size_t)a * (nbins + 1) + i] = (double)i / nbins;
+    if (cudaMemcpy(x.grid, e.data(), e.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(x.par, x.params, sizeof x.params, cudaMemcpyHostToDevice) != cudaSuccess ||
+        gv::launch_grid_pack(x.d, nbins, x.grid, B->stream) != cudaSuccess ||
+        gv::launch_consts(x.ig, x.par, x.kconst, B->stream) != cudaSuccess ||
+        gv::launch_reset(x.st, x.nslots, x.acc, x.binE, x.d * nbins, B->stream) != cudaSuccess)
+      st = VEGAS_ECUDA;
+  }
+  // work list: largest expected cost first
+  if (!st) {
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+      return B->m[p].n_tiles * tile_cost(B->m[p].ig, B->m[p].d) >
+             B->m[q].n_tiles * tile_cost(B->m[q].ig, B->m[q].d);
+    });
+    std::vector<long long> start(n + 1, 0);
+    std::vector<int> ig(n);
+    for (int p = 0; p < n; ++p) start[p + 1] = start[p] + B->m[order[p]].n_tiles;
+    for (int b = 0; b < n; ++b) ig[b] = B->m[b].ig;
+    B->total_items = start[n];
+    if (cudaMemcpy(B->d_order, order.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B->d_item_start, start.data(), (n + 1) * 8, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(B->d_ig, ig.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = VEGAS_ECUDA;
+  }
+  if (!st) {
+    size_t fs = 0, rs = 0;
+    for (const Member& x : B->m) {
+      fs = std::max(fs, GvFillSmem(x.d, nbins, B->fp32 ? 4 : 8, true, true).total);
+      rs = std::max(rs, gv::refine_smem_bytes(x.d, nbins));
+    }
+    B->fill_smem = fs;
+    B->refine_smem = rs;
+    st = ensure_per_iter(B, 16);
+  }
+  if (!st && cudaStreamSynchronize(B->stream) != cudaSuccess) st = VEGAS_ECUDA;
+  if (st) {
+    vegas_batch_free(B);
+    return st;
+  }
+  *out = B;
+  return VEGAS_OK;
 }
-void vegas_batch_free(vegas_batch*) {}
-int vegas_batch_set_option(vegas_batch*, int, double) { return VEGAS_EINVAL; }
-int vegas_batch_set_stream(vegas_batch*, void*) { return VEGAS_EINVAL; }
-int vegas_batch_iterate(vegas_batch*, int, double*, double*, double*, double*) {
-  return VEGAS_EINVAL;
+
+void vegas_batch_free(vegas_batch* B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  cudaFree(B->d_fill);
+  cudaFree(B->per_iter);
+  cudaFree(B->dmem);
+  if (B->pinned) cudaFreeHost(B->pinned);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  delete B;
 }
-int vegas_batch_grid_get(const vegas_batch*, int, double*) { return VEGAS_EINVAL; }
+
+int vegas_batch_set_option(vegas_batch* B, int key, double v) {
+  if (!B || !std::isfinite(v)) return VEGAS_EINVAL;
+  switch (key) {
+    case VEGAS_OPT_ALPHA:
+      if (v < 0.0) return VEGAS_EINVAL;
+      B->alpha = v;
+      break;
+    case VEGAS_OPT_PRECISION:
+      return VEGAS_EINVAL;  // fixed at creation (it sizes shared memory)
+    case VEGAS_OPT_ADAPT:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      B->adapt = (int)v;
+      break;
+    case VEGAS_OPT_EPT:
+      if (v != 0.0 && v != 4.0 && v != 8.0) return VEGAS_EINVAL;
+      B->ept_opt = (int)v;
+      B->ept = 0;
+      break;
+    case VEGAS_OPT_NONFINITE:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      B->nonfinite_policy = (int)v;
+      return VEGAS_OK;
+    case VEGAS_OPT_GRAPH:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      B->use_graph = (int)v;
+      break;
+    default:
+      return VEGAS_EINVAL;
+  }
+  if (B->graph) {
+    cudaStreamSynchronize(B->stream);
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    B->graph_key.clear();
+  }
+  return upload_tables(B);
 }
+
+int vegas_batch_set_stream(vegas_batch* B, void* stream) {
+  if (!B) return VEGAS_EINVAL;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  B->own_stream = false;
+  B->stream = (cudaStream_t)stream;
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+    B->graph_key.clear();
+  }
+  return VEGAS_OK;
+}
+
+int vegas_batch_iterate(vegas_batch* B, int itmx, double* integral, double* error,
+                        double* chi2_dof, double* per_iter) {
+  if (!B || itmx < 1 || itmx > 100000 || !integral || !error || !chi2_dof) return VEGAS_EINVAL;
+  int st = ensure_per_iter(B, itmx);
+  if (st) return st;
+  if (!B->ept) {
+    st = autotune_batch(B);
+    if (st) return st;
+  }
+  const bool graph_ok = B->use_graph && B->stream != nullptr;
+  if (graph_ok) {
+    const std::string key = std::to_string(itmx) + ":" + std::to_string(B->ept) + ":" +
+                            std::to_string(B->adapt);
+    if (!B->graph || B->graph_key != key) {
+      if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+      }
+      cudaGraph_t g;
+      GB_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+      st = enqueue_iterations(B, itmx);
+      const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+      if (st) {
+        if (ce == cudaSuccess) cudaGraphDestroy(g);
+        return st;
+      }
+      GB_TRY(ce);
+      const cudaError_t ie = cudaGraphInstantiate(&B->graph, g, 0);
+      cudaGraphDestroy(g);
+      GB_TRY(ie);
+      B->graph_key = key;
+    }
+    GB_TRY(cudaGraphLaunch(B->graph, B->stream));
+  } else {
+    st = enqueue_iterations(B, itmx);
+    if (st) return st;
+  }
+  // results: every member's state and per-iteration records
+  const size_t need = sizeof(GvState) * B->n + sizeof(double) * 2 * B->per_iter_cap * B->n + 64;
+  if (B->pinned_bytes < need) {
+    if (B->pinned) cudaFreeHost(B->pinned);
+    B->pinned = nullptr;
+    B->pinned_bytes = 0;
+    if (cudaHostAlloc(&B->pinned, need, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return VEGAS_ENOMEM;
+    }
+    B->pinned_bytes = need;
+  }
+  GvState* hs = (GvState*)B->pinned;
+  double* hp = (double*)((char*)B->pinned + ((sizeof(GvState) * B->n + 63) & ~(size_t)63));
+  for (int b = 0; b < B->n; ++b)
+    GB_TRY(cudaMemcpyAsync(hs + b, B->m[b].st, sizeof(GvState), cudaMemcpyDeviceToHost,
+                           B->stream));
+  GB_TRY(cudaMemcpyAsync(hp, B->per_iter, sizeof(double) * 2 * B->per_iter_cap * B->n,
+                         cudaMemcpyDeviceToHost, B->stream));
+  GB_TRY(cudaStreamSynchronize(B->stream));
+  unsigned long long bad = 0;
+  for (int b = 0; b < B->n; ++b) {
+    integral[b] = hs[b].integral;
+    error[b] = hs[b].error;
+    chi2_dof[b] = hs[b].chi2;
+    bad += hs[b].nonfinite;
+    if (per_iter)
+      memcpy(per_iter + (size_t)b * itmx * 2, hp + (size_t)b * B->per_iter_cap * 2,
+             sizeof(double) * 2 * itmx);
+  }
+  if (bad && B->nonfinite_policy == 0) return VEGAS_ENONFINITE;
+  return VEGAS_OK;
+}
+
+int vegas_batch_grid_get(const vegas_batch* B, int index, double* edges) {
+  if (!B || !edges || index < 0 || index >= B->n) return VEGAS_EINVAL;
+  const Member& x = B->m[index];
+  GB_TRY(cudaStreamSynchronize(B->stream));
+  GB_TRY(cudaMemcpy(edges, x.grid, sizeof(double) * x.d * (B->N + 1), cudaMemcpyDeviceToHost));
+  return VEGAS_OK;
+}
+
+}  // extern "C"

@@ -135,6 +135,7 @@ struct vegas_ctx {
   double* sums = nullptr;
   double* scratch = nullptr;
   double* logtab = nullptr;
+  int* binE = nullptr;  // [ndim*nbins] bin exponents of the running iteration
   int nacc_max = 0;
   // workspace
   void* ws = nullptr;
@@ -235,6 +236,7 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   a.st = c->st;
   a.part = p.part;
   a.tileE = p.tileE;
+  a.binE = c->binE;
   return a;
 }
 
@@ -262,6 +264,7 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.sums = c->sums;
   r.per_iter = p.per_iter;
   r.inv_total = c->scratch + 4 * (size_t)c->ndim * (c->nbins + 1);
+  r.binE = c->binE;
   return r;
 }
 
@@ -280,6 +283,7 @@ GvRefineArgs refine_args(const vegas_ctx* c) {
   r.grid = c->grid;
   r.scratch = c->scratch;
   r.st = c->st;
+  r.binE = c->binE;
   return r;
 }
 
@@ -352,7 +356,7 @@ int autotune(vegas_ctx* c, Plan& p) {
   cudaEventDestroy(e1);
   GV_TRY(cudaGetLastError());
   // the trial launches touched the iteration invariants: restore them
-  GV_TRY(gv::launch_reset(c->st, p.nacc, c->acc, c->stream));
+  GV_TRY(gv::launch_reset(c->st, p.nacc, c->acc, c->binE, c->ndim * c->nbins, c->stream));
   p.ept = best_ept;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best_ept;
@@ -370,7 +374,7 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.n_tiles = (int)nt;
   p.nch = mode ? GV_MAXCH : 1;
   p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins;
-  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0).total;
+  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4).total;
   int gx = 0, gy = 0;
   gv::reduce_grid(p.n_tiles, p.nacc, &p.tiles_per_cta, &gx, &gy);
   p.reduce_ctas = gx * gy;
@@ -580,6 +584,28 @@ const uint32_t kStateMagic = 0x47564547u;  // "GVEG"
 // ============================================================================
 // C ABI
 // ============================================================================
+namespace gv {
+// Table of the device log: R_j ~ 1/c_j at the centre of each 1/128-wide
+// interval of [1,2), L_j = -ln R_j, then ln 2 as a 42-bit head and a tail.
+const double* host_log_table() {
+  static double tab[258];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int j = 0; j < 128; ++j) {
+      const double cj = 1.0 + (j + 0.5) / 128.0;
+      const double R = 1.0 / cj;
+      tab[2 * j] = R;
+      tab[2 * j + 1] = (double)(-logl((long double)R));
+    }
+    const long double ln2 = logl(2.0L);
+    const double hi = std::ldexp(std::floor(std::ldexp((double)ln2, 42)), -42);
+    tab[256] = hi;
+    tab[257] = (double)(ln2 - (long double)hi);
+  });
+  return tab;
+}
+}  // namespace gv
+
 extern "C" {
 
 const char* vegas_strerror(int status) {
@@ -635,6 +661,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   off = align256(off + (size_t)c->nacc_max * 8);
   const size_t o_scr = off;
   off = align256(off + ((size_t)4 * ndim * (nbins + 1) + GV_MAXD) * 8);
+  const size_t o_bine = off;
+  off = align256(off + (size_t)ndim * nbins * 4);
   if (cudaMalloc(&c->fixed, off) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(c->stream);
@@ -650,31 +678,15 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   c->sums = (double*)(b + o_sums);
   c->scratch = (double*)(b + o_scr);
   c->logtab = (double*)(b + o_log);
+  c->binE = (int*)(b + o_bine);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess ||
-      gv::launch_reset(c->st, c->nacc_max, c->acc, c->stream) != cudaSuccess)
+      gv::launch_reset(c->st, c->nacc_max, c->acc, c->binE, ndim * nbins, c->stream) !=
+          cudaSuccess)
     st = VEGAS_ECUDA;
-  if (!st) {
-    // table of the device log: R_j ~ 1/c_j at the centre of each 1/128-wide
-    // interval of [1,2), L_j = -ln R_j, then ln 2 as a 42-bit head and a tail
-    static double tab[258];
-    static std::once_flag once;
-    std::call_once(once, [] {
-      for (int j = 0; j < 128; ++j) {
-        const double cj = 1.0 + (j + 0.5) / 128.0;
-        const double R = 1.0 / cj;
-        tab[2 * j] = R;
-        tab[2 * j + 1] = (double)(-logl((long double)R));
-      }
-      const long double ln2 = logl(2.0L);
-      const double hi = std::ldexp(std::floor(std::ldexp((double)ln2, 42)), -42);
-      tab[256] = hi;
-      tab[257] = (double)(ln2 - (long double)hi);
-    });
-    if (cudaMemcpyAsync(c->logtab, tab, sizeof tab, cudaMemcpyHostToDevice, c->stream) !=
-        cudaSuccess)
-      st = VEGAS_ECUDA;
-  }
+  if (!st && cudaMemcpyAsync(c->logtab, gv::host_log_table(), 258 * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    st = VEGAS_ECUDA;
   if (!st) {
     std::vector<double> e((size_t)ndim * (nbins + 1));
     for (int a = 0; a < ndim; ++a)

@@ -18,6 +18,17 @@
 // schedule and batching -- the paper's "independent of the number of
 // threads" (Section 2.2) made exact -- and it is more accurate than the
 // Kahan sums the paper uses for the same purpose.
+//
+// Bin sums carry their own scale.  The grid refinement compresses every
+// bin's share rho through ((1-rho)/(-ln rho))^alpha, which stays far from 0
+// even for rho = 1e-100, so a bin's sum needs relative, not absolute,
+// precision.  Each bin therefore has its own exponent: F_b with w^2 < 2^(2 F_b)
+// for every event of the bin (an order-free max, per tile and then over the
+// iteration).  A tile rounds each w^2 once to a multiple of 2^(2 F_tb - 56);
+// the iteration's sum aligns the tile sums to 2^(2 F_b - 88).  Alignment
+// truncates only bits ~2^-86 below the bin's largest w^2, in a fixed way, so
+// the bin sums stay launch-shape independent; one w^2 is rounded to 2^-56 of
+// its bin's scale, so a bin sum is relatively exact to 2^-45 at worst.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -30,6 +41,10 @@
 #define GV_EMPTY (-0x40000000)  // scale of a tile / iteration with no nonzero value
 #define GV_NCONST 48          // derived integrand constants per integration
 #define GV_MAXPARAMS 16
+#define GV_BINE_OFF 1100      // stored bin exponent F + GV_BINE_OFF (0: no nonzero weight)
+#define GV_BIN_QBITS 56       // bits of one w^2 below its bin's scale in a tile
+#define GV_BIN_XBITS 32       // extra low bits of the iteration's bin sums
+#define GV_BIN_FB (GV_BIN_QBITS + GV_BIN_XBITS)  // bin sums in units of 2^(2F - GV_BIN_FB)
 
 enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2 };
 
@@ -76,6 +91,7 @@ struct GvFillArgs {
   GvState* st;
   ulonglong2* part;              // [tile][nacc] 128-bit two's complement sums
   int* tileE;                    // [tile][nch] scales
+  int* binE;                     // [ndim*nbins] iteration bin exponents (atomicMax)
 };
 
 // Arguments of the reduce/finalize kernel.
@@ -94,6 +110,7 @@ struct GvReduceArgs {
   double* sums;                  // [nacc] FP64 sums of the last iteration
   double* per_iter;              // forward: [itmx][2]; adjoint: [itmx][2 + 2*NGRAD]
   double* inv_total;             // [ndim] 1 / (6 x sum of the smoothed bin sums), 0 if none
+  int* binE;                     // [ndim*nbins] bin exponents of the iteration
 };
 
 // Arguments of the refine kernel.
@@ -107,6 +124,7 @@ struct GvRefineArgs {
   double* grid;                  // grid pack (refined in place)
   double* scratch;               // 4 * d * (N+1) doubles
   GvState* st;
+  int* binE;                     // [ndim*nbins] bin exponents (read, then reset)
 };
 
 // ----------------------------------------------------------------------------
@@ -280,6 +298,18 @@ __device__ __forceinline__ u128 gv_square_fixed_dec(const GvDecoded& d, int E) {
   return gv_shift_round(v, 2 * d.e2 - 2 * E + GV_FB);
 }
 
+// x^2 2^(GV_BIN_QBITS - 2F) for |x| = m 2^e2 < 2^F, from the high word
+// P = floor(m^2 2^-42) of the square of m 2^11 (the 64 bits below the leading
+// ones of m^2, so the truncation is below 2^-62 relative): rounded half up,
+// with rs = 2F - 2 e2 - 98 >= 8, below 2^GV_BIN_QBITS.  Each value is formed
+// on its own, so the tile's sum does not depend on the event order.
+__device__ __forceinline__ unsigned long long gv_square_hi(unsigned long long m) {
+  return __umul64hi(m << 11, m << 11);
+}
+__device__ __forceinline__ unsigned long long gv_square_bin(unsigned long long P, int rs) {
+  return rs <= 64 ? ((P >> (rs - 1)) + 1ull) >> 1 : 0ull;
+}
+
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
   return __shfl_xor_sync(0xffffffffu, v, m);
 }
@@ -313,9 +343,16 @@ cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s, bool pdl);
 cudaError_t prepare_refine(int d, int N);
 cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl);
 size_t refine_smem_bytes(int d, int N);
+int refine_ctas(int d, int N);
+cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
+                                int last, double inv_m1, cudaStream_t s);
+cudaError_t launch_refine_batch(const GvRefineArgs* args, const int4* tasks, int ntasks,
+                                size_t smem, cudaStream_t s);
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);
-cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, cudaStream_t s);
+cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, int* binE, int dN,
+                         cudaStream_t s);
 cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
+const double* host_log_table();  // 258 doubles, see gv_log_pos
 cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,
                              unsigned long long ev0, long long n, int d, uint32_t* out,
                              cudaStream_t s);

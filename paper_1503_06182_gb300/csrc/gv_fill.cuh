@@ -67,21 +67,22 @@ struct GvPair<double> {
 };
 
 // Shared-memory layout of the fill kernel (bytes), 16-byte aligned pieces:
-//   hist [4][d*N] u32     per-bin sums of w^2 in four 22-bit limbs (forward only)
+//   hist [4][d*N] u32     per-bin sums of w^2 in three 22-bit limbs, then the
+//                         tile's bin exponents F_tb + GV_BINE_OFF (forward only)
 //   jac  [d*N]    f64     Jacobian factor N*(e_{i+1}-e_i) (FP64 form only)
 //   ew   [d*N]    GvBin32 (e, w, jac) in the FP32 form, GvBin64 (e, w) in FP64
-//   bins [d][GV_TILE] u16 (forward with d > 4 only)
+//   bins [d][GV_TILE] u16 (forward kernels of the d > 4 classes only)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 struct GvFillSmem {
   size_t hist, jac, ew, bins, total;
-  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward) {
+  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem) {
     const size_t dN = (size_t)d * N;
     hist = 0;
     jac = gv_align16(hist + (forward ? dN * 16 : 0));
     ew = gv_align16(jac + (real_bytes == 8 ? dN * 8 : 0));
     bins = gv_align16(ew + dN * 16);
-    total = gv_align16(bins + ((forward && d > 4) ? (size_t)d * GV_TILE * 2 : 0));
+    total = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
   }
 };
 
@@ -231,34 +232,30 @@ __device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward fill: channel 0 = w, with per-bin sums of w^2.
+// Forward fill of one tile: channel 0 = w, with per-bin sums of w^2.  The grid
+// of the integration must be staged and the histogram zeroed (both followed
+// by a barrier) before the call.  Used by the per-integration kernel and by
+// the persistent batched kernel, so that a tile's partial is the same
+// whichever kernel computes it.
 // ---------------------------------------------------------------------------
 template <int IG, typename Real, int EPT, int MAXD>
-__global__ void __launch_bounds__(GV_TILE / EPT)
-    gv_fill_kernel(const GvFillArgs a) {
+__device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile,
+                                             unsigned char* smem, unsigned long long* red_u64,
+                                             u128* red_128, uint32_t it) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
   using Pair = typename GvPair<Real>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red_u64[NW];
-  __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins, dN = d * N;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true);
-  unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);  // [4][dN]
-  double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
-  Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);  // [3][dN] limbs
+  int* ebin = reinterpret_cast<int*>(hist + 3 * dN);               // [dN] exponents
+  const double* s_jac = reinterpret_cast<const double*>(smem + lay.jac);
+  const Pair* s_ew = reinterpret_cast<const Pair*>(smem + lay.ew);
   unsigned short* s_bin = reinterpret_cast<unsigned short*>(smem + lay.bins);
   const int tid = threadIdx.x;
-
-  for (int k = tid; k < 4 * dN; k += B) hist[k] = 0u;
-  gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
-  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
-  const uint32_t it = (uint32_t)a.st->it;
-  __syncthreads();
 
-  const long long tile = blockIdx.x;
   const long long tile0 = tile * GV_TILE;
   double w[EPT];
   GvBinStore<MAXD> bs[EPT];
@@ -282,12 +279,18 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       if (gv_finite_bits(ab)) {
         w[k] = wv;
         mx = ab > mx ? ab : mx;
+        if (ab != 0ull) {
+          const int F = gv_scale_exp(ab) + GV_BINE_OFF;
+#pragma unroll
+          for (int ax = 0; ax < MAXD; ++ax)
+            if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
+        }
       } else {
         ++nbad;  // counted, contributes nothing
       }
     }
   }
-  const unsigned long long M = gv_block_max<NW>(mx, red_u64);
+  const unsigned long long M = gv_block_max<NW>(mx, red_u64);  // also orders ebin
   const int E = gv_scale_exp(M);
 
   u128 s1 = {0ull, 0ull}, s2 = {0ull, 0ull};
@@ -297,23 +300,22 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       if (gv_abs_bits(w[k]) != 0ull) {
         const int local = k * B + tid;
         const GvDecoded dw = gv_decode(w[k]);
-        const u128 v2 = gv_square_fixed_dec(dw, E);
         s1 = add128(s1, gv_fixed_dec(dw, E));
-        s2 = add128(s2, v2);
-        // bins: round(v2 / 2^8), an 88-bit value, as four 22-bit limbs
-        const u128 vb = gv_shift_round(v2, -8);
-        const unsigned l0 = (unsigned)(vb.lo & 0x3FFFFFull);
-        const unsigned l1 = (unsigned)((vb.lo >> 22) & 0x3FFFFFull);
-        const unsigned l2 = (unsigned)(((vb.lo >> 44) | (vb.hi << 20)) & 0x3FFFFFull);
-        const unsigned l3 = (unsigned)((vb.hi >> 2) & 0x3FFFFFull);
+        s2 = add128(s2, gv_square_fixed_dec(dw, E));
+        // bins: w^2 at its bin's scale, a 56-bit value, as three 22-bit limbs
+        const unsigned long long P = gv_square_hi(dw.m);
+        const int c = 2 * dw.e2 + 98 + 2 * GV_BINE_OFF;
 #pragma unroll
         for (int ax = 0; ax < MAXD; ++ax) {
           if (ax < d) {
             const int bi = ax * N + bs[k].get(ax, s_bin, local);
+            const unsigned long long q = gv_square_bin(P, 2 * ebin[bi] - c);
+            const unsigned l0 = (unsigned)(q & 0x3FFFFFull);
+            const unsigned l1 = (unsigned)((q >> 22) & 0x3FFFFFull);
+            const unsigned l2 = (unsigned)(q >> 44);
             if (l0) atomicAdd(hist + bi, l0);
             if (l1) atomicAdd(hist + dN + bi, l1);
             if (l2) atomicAdd(hist + 2 * dN + bi, l2);
-            if (l3) atomicAdd(hist + 3 * dN + bi, l3);
           }
         }
       }
@@ -331,16 +333,37 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   }
   if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
   for (int k = tid; k < dN; k += B) {
-    // (l0 + l1 2^22 + l2 2^44 + l3 2^66) 2^8 at the scale of the sum of w^2
-    const unsigned long long l0 = hist[k], l1 = hist[dN + k], l2 = hist[2 * dN + k],
-                             l3 = hist[3 * dN + k];
+    // Q = l0 + l1 2^22 + l2 2^44 (< 2^67) in units of 2^(2 F_tb - GV_BIN_QBITS),
+    // with F_tb + GV_BINE_OFF in bits 96.. of the partial
+    const unsigned long long l0 = hist[k], l1 = hist[dN + k], l2 = hist[2 * dN + k];
     u128 v = {l0, 0ull};
-    v = add128(v, u128{l1 << 22, 0ull});
+    v = add128(v, u128{l1 << 22, l1 >> 42});
     v = add128(v, u128{l2 << 44, l2 >> 20});
-    v = add128(v, u128{0ull, l3 << 2});
-    v = gv_shift_round(v, 8);
-    out[2 + k] = make_ulonglong2(v.lo, v.hi);
+    const int f = ebin[k];
+    out[2 + k] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)f << 32));
+    // the iteration's bin exponents: a max, so a stale read costs one atomic
+    if (f > __ldcg(a.binE + k)) atomicMax(a.binE + k, f);
   }
+}
+
+template <int IG, typename Real, int EPT, int MAXD>
+__global__ void __launch_bounds__(GV_TILE / EPT)
+    gv_fill_kernel(const GvFillArgs a) {
+  constexpr int B = GV_TILE / EPT;
+  constexpr int NW = B / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red_u64[NW];
+  __shared__ u128 red_128[NW];
+  const int d = a.ndim, N = a.nbins;
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4);
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
+  for (int k = threadIdx.x; k < 4 * d * N; k += B) hist[k] = 0u;
+  gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
+  gv_stage_grid<Real>(a.grid, d, N, reinterpret_cast<double*>(smem + lay.jac),
+                      reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew), threadIdx.x, B);
+  const uint32_t it = (uint32_t)a.st->it;
+  __syncthreads();
+  gv_fill_tile<IG, Real, EPT, MAXD>(a, blockIdx.x, smem, red_u64, red_128, it);
 }
 
 // ---------------------------------------------------------------------------
@@ -358,7 +381,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), false);
+  const GvFillSmem lay(d, N, (int)sizeof(Real), false, false);
   double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
   Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
   const int tid = threadIdx.x;

@@ -64,6 +64,15 @@ __device__ __forceinline__ u192 sar192(u192 v, int s) {
   return v;
 }
 
+// Left shift by 0 <= s < 64 (callers keep the result below 2^149).
+__device__ __forceinline__ u192 shl192(u192 v, int s) {
+  if (s <= 0) return v;
+  v.l2 = (v.l2 << s) | (v.l1 >> (64 - s));
+  v.l1 = (v.l1 << s) | (v.l0 >> (64 - s));
+  v.l0 <<= s;
+  return v;
+}
+
 // Accumulators: three 64-bit limbs holding bits [0,43), [43,86) and [86,...)
 // (the last one signed), 32 bytes apart.  The two low limbs have 21 bits of
 // headroom (up to 2^21 adds), so no carry travels between limbs until the
@@ -150,10 +159,34 @@ __device__ double u192_to_double(u192 v, int q) {
     mant >>= 1;
     ++e;
   }
-  const unsigned long long bits =
-      ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  const double r = __longlong_as_double((long long)bits);
+  double r;
+  if (e > 1023) {
+    r = __longlong_as_double(0x7FF0000000000000ll);  // beyond FP64, as a sum of doubles would be
+  } else if (e >= -1022) {
+    r = __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) |
+                                         (mant & 0xFFFFFFFFFFFFFull)));
+  } else if (e >= -1022 - 600) {
+    // below the normal range: scale into it, then one multiply by 2^-600
+    // (the product rounds to the subnormal grid; rare, and on the FP64 pipe)
+    r = __longlong_as_double((long long)(((unsigned long long)(e + 600 + 1023) << 52) |
+                                         (mant & 0xFFFFFFFFFFFFFull))) *
+        0x1p-600;
+  } else {
+    r = 0.0;
+  }
   return neg ? -r : r;
+}
+
+// Stored bin exponent (GV_BINE_OFF-offset, 0 = empty) -> q of u192_to_double.
+__device__ __forceinline__ int bin_q(int g) { return 2 * (g - GV_BINE_OFF) - GV_BIN_FB; }
+
+// Max of the stored bin exponents of one axis, by one warp (all lanes get it).
+__device__ __forceinline__ int axis_bin_exp(const int* binE, int N) {
+  int g = 0;
+  for (int i = threadIdx.x & 31; i < N; i += 32) g = max(g, __ldcg(binE + i));
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) g = max(g, __shfl_xor_sync(0xffffffffu, g, m));
+  return g;
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -301,10 +334,14 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
   // each rounded once to FP64
   const int nconv = a.refine_follows ? 2 * a.nch : a.nacc;
   for (int k = tid; k < nconv; k += nthr) {
-    const int ch = k < 2 * a.nch ? (k >> 1) : 0;
-    const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
-    const int Eg = st->E[ch];
-    a.sums[k] = Eg != GV_EMPTY ? u192_to_double(load_acc(a.acc, k), pw * Eg - GV_FB) : 0.0;
+    if (k < 2 * a.nch) {
+      const int Eg = st->E[k >> 1];
+      a.sums[k] =
+          Eg != GV_EMPTY ? u192_to_double(load_acc(a.acc, k), ((k & 1) + 1) * Eg - GV_FB) : 0.0;
+    } else {  // a bin, at its own scale
+      const int g = __ldcg(a.binE + (k - 2 * a.nch));
+      a.sums[k] = g ? u192_to_double(load_acc(a.acc, k), bin_q(g)) : 0.0;
+    }
   }
   __syncthreads();
   if (wid == 0) {
@@ -322,17 +359,21 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
       if (a.k == 0) st->status = 0;
       st->nonfinite_iter = 0ull;
     }
-  } else if (a.has_bins && tid - 32 < d) {
-    // per-axis totals (slots after the bins, summed exactly by the reduce
-    // CTAs): one rounding, stored as 1/(6 x total), 0 when the axis is empty
-    const int ax = tid - 32;
-    const int Eg = st->E[0];
-    double inv = 0.0;
-    if (Eg != GV_EMPTY) {
-      const double t6 = u192_to_double(load_acc(a.acc, a.nacc + ax), 2 * Eg - GV_FB);
-      inv = t6 > 0.0 ? __drcp_rn(t6) : 0.0;
+  } else if (a.has_bins) {
+    // per-axis totals (slots after the bins, at the axis' largest bin scale,
+    // summed by the reduce CTAs): one rounding, stored as 1/(6 x total), 0
+    // when the axis is empty.  One warp per axis.
+    for (int ax = wid - 1; ax < d; ax += (nthr >> 5) - 1) {
+      const int g = axis_bin_exp(a.binE + ax * a.nbins, a.nbins);
+      if (lane == 0) {
+        double inv = 0.0;
+        if (g) {
+          const double t6 = u192_to_double(load_acc(a.acc, a.nacc + ax), bin_q(g));
+          inv = t6 > 0.0 ? __drcp_rn(t6) : 0.0;
+        }
+        a.inv_total[ax] = inv;
+      }
     }
-    a.inv_total[ax] = inv;
   }
   __syncthreads();  // every read of the accumulators here is done
   const int nslots = a.has_bins ? a.nacc + d : a.nacc;
@@ -341,6 +382,8 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
     const bool bin_slot = a.has_bins && slot >= 2 * a.nch && slot < a.nacc;
     if (!(bin_slot && a.refine_follows)) a.acc[k] = 0ull;
   }
+  if (a.has_bins && !a.refine_follows)
+    for (int k = tid; k < d * a.nbins; k += nthr) a.binE[k] = 0;
   if (tid == 0) {
     st->E0_prev = st->E[0];
     for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
@@ -351,18 +394,44 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
 
 #define GV_RED_TILES_PER_LOAD 8
 
-__global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
-  __shared__ u192 s_part[8][32];
-  __shared__ int is_last;
+// One reduce CTA (256 threads) of one integration: accumulator block bx, tile
+// range by, of nblk CTAs in total for that integration.
+__device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
+                               u192 (*s_part)[32], int* is_last_s) {
+  int& is_last = *is_last_s;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = blockIdx.x * 32 + lane;
-  const int t0 = blockIdx.y * a.tiles_per_cta;
+  const int k = bx * 32 + lane;
+  const int t0 = by * a.tiles_per_cta;
   const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
   u192 r = {0ull, 0ull, 0ull};
   gv_wait_prior_grid();
-  if (k < a.nacc) {
-    const int ch = k < 2 * a.nch ? (k >> 1) : 0;
-    const int pw = k < 2 * a.nch ? ((k & 1) + 1) : 2;
+  const bool bin_slot = a.has_bins && k >= 2 * a.nch && k < a.nacc;
+  const int gb = bin_slot ? __ldcg(a.binE + (k - 2 * a.nch)) : 0;
+  if (bin_slot) {
+    // Q 2^(2 F_tb - GV_BIN_QBITS) aligned to 2^(2 G_b - GV_BIN_FB)
+    if (gb) {
+      constexpr int G = GV_RED_TILES_PER_LOAD;
+      for (int tb = t0 + wid; tb < t1; tb += 8 * G) {
+        ulonglong2 v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int t = tb + 8 * g;
+          v[g] = t < t1 ? a.part[(size_t)t * a.nacc + k] : make_ulonglong2(0ull, 0ull);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int f = (int)(v[g].y >> 32);
+          if (f) {
+            const u192 x = {v[g].x, v[g].y & 0xFFFFFFFFull, 0ull};
+            const int sh = 2 * (gb - f) - GV_BIN_XBITS;
+            add192(r, sh < 0 ? shl192(x, -sh) : sar192(x, sh));
+          }
+        }
+      }
+    }
+  } else if (k < a.nacc) {
+    const int ch = k >> 1;
+    const int pw = (k & 1) + 1;
     const int Eg = a.st->E[ch];
     if (Eg != GV_EMPTY) {
       constexpr int G = GV_RED_TILES_PER_LOAD;
@@ -401,12 +470,16 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
       const int N = a.nbins;
       const int j = k - 2 * a.nch;  // bin index within [0, d*N)
       const bool is_bin = k < a.nacc && j >= 0;
-      const u192 ct = is_bin ? mul192_small(t, smooth_weight(j % N, N)) : u192{0ull, 0ull, 0ull};
-      const int k0 = blockIdx.x * 32;
+      const u192 ct = (is_bin && gb) ? mul192_small(t, smooth_weight(j % N, N))
+                                      : u192{0ull, 0ull, 0ull};
+      const int k0 = bx * 32;
       const int j_first = max(0, k0 - 2 * a.nch);
       const int j_last = min(a.nacc - 1, k0 + 31) - 2 * a.nch;
       for (int ax = j_first / N; j_last >= 0 && ax <= j_last / N; ++ax) {
-        u192 v = (is_bin && j / N == ax) ? ct : u192{0ull, 0ull, 0ull};
+        // at the axis' largest bin scale (a fixed truncation of the small bins)
+        const int gax = axis_bin_exp(a.binE + ax * N, N);
+        u192 v = (is_bin && gb && j / N == ax) ? sar192(ct, 2 * (gax - gb))
+                                                : u192{0ull, 0ull, 0ull};
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) {
           u192 o = {__shfl_xor_sync(0xffffffffu, v.l0, m), __shfl_xor_sync(0xffffffffu, v.l1, m),
@@ -420,13 +493,33 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
     __threadfence();
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    is_last = (atomicAdd(&a.st->done, 1) == (int)(gridDim.x * gridDim.y) - 1) ? 1 : 0;
+  if (threadIdx.x == 0) is_last = (atomicAdd(&a.st->done, 1) == nblk - 1) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
   gv_allow_next_grid();
   __threadfence();
   finalize_iteration(a);
+}
+
+__global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
+  __shared__ u192 s_part[8][32];
+  __shared__ int is_last;
+  gv_reduce_task(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y, s_part, &is_last);
+}
+
+// Batched: one launch reduces many integrations; task i names the
+// integration and the block coordinates of CTA i.
+__global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs* args,
+                                                              const int4* tasks, int k, int last,
+                                                              double inv_m1) {
+  __shared__ u192 s_part[8][32];
+  __shared__ int is_last;
+  const int4 t = tasks[blockIdx.x];
+  GvReduceArgs a = args[t.x];
+  a.k = k;
+  a.last = last;
+  a.inv_m1 = inv_m1;
+  gv_reduce_task(a, t.y, t.z, t.w, s_part, &is_last);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,29 +579,33 @@ __device__ __forceinline__ double compress(double rho, double alpha, const doubl
 // reaches j R/N -- binary search on the bit patterns of the nonnegative
 // doubles, then e_i + (target - C_i) * slope_i -- and the tables, with r,
 // slope, C and the old edges in shared memory.
-__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRefineArgs a) {
-  extern __shared__ __align__(16) double sm[];
+__device__ void gv_refine_task(const GvRefineArgs& a, int bx, int nblk, double* sm,
+                               int* is_last_s, double* s_step) {
+  int& is_last = *is_last_s;
   const int d = a.ndim, N = a.nbins, dN = d * N;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int NWARP = GV_REFINE_THREADS / 32;
-  __shared__ int is_last;
-  __shared__ double s_step[GV_MAXD];
   double* gr = a.scratch;                   // [dN] r
   double* gsl = a.scratch + dN;             // [dN] slope
   double* ne = a.scratch + 2 * (size_t)dN;  // [d(N+1)] new edges
   const double* e64 = a.grid;               // the pack starts with e64
   gv_wait_prior_grid();
   if (wid == 0) {
-    const int k = blockIdx.x * GV_REFINE_BINS + lane;
+    const int k = bx * GV_REFINE_BINS + lane;
     if (k < dN) {
       const int ax = k / N, i = k - ax * N;
       const int base = 2 * a.nch + ax * N;  // slot of bin 0 of this axis
-      const int Eg = a.st->E0_prev;
+      const int* G = a.binE + ax * N;
       const u192 z = {0ull, 0ull, 0ull};
-      const u192 dm = i > 0 ? load_acc(a.acc, base + i - 1) : z;
-      const u192 dc = load_acc(a.acc, base + i);
-      const u192 dp = i < N - 1 ? load_acc(a.acc, base + i + 1) : z;
-      // 6 x the smoothed sum, exactly: 3 (d_0 + d_1) at the ends,
+      const int gm = i > 0 ? __ldcg(G + i - 1) : 0, gc = __ldcg(G + i),
+                gp = i < N - 1 ? __ldcg(G + i + 1) : 0;
+      const int gx = max(gm, max(gc, gp));
+      // the three bins at the largest of their scales (empty bins hold 0)
+      const u192 dc0 = load_acc(a.acc, base + i);
+      const u192 dm = gm ? sar192(load_acc(a.acc, base + i - 1), 2 * (gx - gm)) : z;
+      const u192 dc = gc ? sar192(dc0, 2 * (gx - gc)) : z;
+      const u192 dp = gp ? sar192(load_acc(a.acc, base + i + 1), 2 * (gx - gp)) : z;
+      // 6 x the smoothed sum: 3 (d_0 + d_1) at the ends,
       // 2 (d_{i-1} + d_i + d_{i+1}) inside
       u192 s6 = dc;
       if (i == 0) {
@@ -522,12 +619,11 @@ __global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRe
         add192(s6, dp);
         s6 = mul192_small(s6, 2);
       }
-      const int q = 2 * Eg - GV_FB;
-      a.dsum[k] = Eg != GV_EMPTY ? u192_to_double(dc, q) : 0.0;
+      a.dsum[k] = gc ? u192_to_double(dc0, bin_q(gc)) : 0.0;
       const double it = a.inv_total[ax];
       double rv = 0.0, sl = 0.0;
-      if (it > 0.0) {
-        rv = compress(u192_to_double(s6, q) * it, a.alpha, a.logtab);
+      if (it > 0.0 && gx) {
+        rv = compress(u192_to_double(s6, bin_q(gx)) * it, a.alpha, a.logtab);
         if (rv > 0.0)
           sl = (e64[ax * (N + 1) + i + 1] - e64[ax * (N + 1) + i]) * __drcp_rn(rv);
       }
@@ -537,7 +633,7 @@ __global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRe
     __threadfence();
   }
   __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(&a.st->done_refine, 1) == (int)gridDim.x - 1) ? 1 : 0;
+  if (tid == 0) is_last = (atomicAdd(&a.st->done_refine, 1) == nblk - 1) ? 1 : 0;
   __syncthreads();
   if (!is_last) return;
   gv_allow_next_grid();
@@ -545,6 +641,7 @@ __global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRe
   // every phase-1 CTA has read the bin slots: reset them for the next iteration
   for (int k = tid; k < GV_ACC_STRIDE * dN; k += GV_REFINE_THREADS)
     a.acc[GV_ACC_STRIDE * 2 * a.nch + k] = 0ull;
+  for (int k = tid; k < dN; k += GV_REFINE_THREADS) a.binE[k] = 0;
   double* r = sm;                 // [dN]
   double* slope = r + dN;         // [dN]
   double* cum = slope + dN;       // [d(N+1)]
@@ -607,6 +704,23 @@ __global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRe
   __syncthreads();
   pack_axis_tables(a.grid, ne, d, N, tid, GV_REFINE_THREADS);
   if (tid == 0) a.st->done_refine = 0;
+}
+
+__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRefineArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int is_last;
+  __shared__ double s_step[GV_MAXD];
+  gv_refine_task(a, blockIdx.x, gridDim.x, sm, &is_last, s_step);
+}
+
+__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_batch_kernel(
+    const GvRefineArgs* args, const int4* tasks) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int is_last;
+  __shared__ double s_step[GV_MAXD];
+  const int4 t = tasks[blockIdx.x];
+  const GvRefineArgs a = args[t.x];
+  gv_refine_task(a, t.y, t.w, sm, &is_last, s_step);
 }
 
 // ---------------------------------------------------------------------------
@@ -676,7 +790,9 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
 
 // Reset the per-iteration invariants (at creation and after the autotuner's
 // trial launches).
-__global__ void gv_reset_kernel(GvState* st, int nacc, unsigned long long* acc) {
+__global__ void gv_reset_kernel(GvState* st, int nacc, unsigned long long* acc, int* binE,
+                                int dN) {
+  for (int k = threadIdx.x; k < dN; k += blockDim.x) binE[k] = 0;
   if (threadIdx.x == 0) {
     st->nonfinite_iter = 0ull;
     st->done = 0;
@@ -733,13 +849,33 @@ cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl) {
                    refine_smem_bytes(a.ndim, a.nbins), s, pdl, a);
 }
 
+cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
+                                int last, double inv_m1, cudaStream_t s) {
+  gv_reduce_batch_kernel<<<ntasks, 256, 0, s>>>(args, tasks, k, last, inv_m1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_batch(const GvRefineArgs* args, const int4* tasks, int ntasks,
+                                size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(gv_refine_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  gv_refine_batch_kernel<<<ntasks, GV_REFINE_THREADS, smem, s>>>(args, tasks);
+  return cudaGetLastError();
+}
+
+int refine_ctas(int d, int N) { return (d * N + GV_REFINE_BINS - 1) / GV_REFINE_BINS; }
+
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s) {
   gv_consts_kernel<<<1, 32, 0, s>>>(integrand, params, kconst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, cudaStream_t s) {
-  gv_reset_kernel<<<1, 256, 0, s>>>(st, nacc, acc);
+cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, int* binE, int dN,
+                         cudaStream_t s) {
+  gv_reset_kernel<<<1, 256, 0, s>>>(st, nacc, acc, binE, dN);
   return cudaGetLastError();
 }
 

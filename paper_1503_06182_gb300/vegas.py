@@ -376,3 +376,44 @@ class Vegas:
             self.close()
         except Exception:
             pass
+
+
+class VegasBatch:
+    """Many independent VEGAS integrations advanced together (owns a batch).
+
+    ``members`` is a list of ``(ndim, ncall, integrand_id, params)``; member b
+    draws its events with Philox batch word b."""
+
+    def __init__(self, members, nbins: int, seed: int = 1234, *, precision: str = "fp64",
+                 alpha: float = 1.5):
+        self.members = [(int(d), int(c), int(i), tuple(p)) for d, c, i, p in members]
+        self.nbins, self.seed = nbins, seed
+        self.h = vegas_batch_create([m[0] for m in self.members], [m[1] for m in self.members],
+                                    [m[2] for m in self.members], [m[3] for m in self.members],
+                                    nbins, seed, 1 if precision == "fp32" else 0)
+        self.set(VEGAS_OPT_ALPHA, alpha)
+
+    def __len__(self) -> int:
+        return len(self.members)
+
+    def set(self, key: int, value: float) -> "VegasBatch":
+        vegas_batch_set_option(self.h, key, value)
+        return self
+
+    def iterate(self, itmx: int):
+        """(integral[n], error[n], chi2_dof[n], per_iter[n, itmx, 2])."""
+        return vegas_batch_iterate(self.h, len(self.members), itmx)
+
+    def grid(self, index: int) -> np.ndarray:
+        return vegas_batch_grid_get(self.h, index, self.members[index][0], self.nbins)
+
+    def close(self) -> None:
+        if self.h:
+            vegas_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
