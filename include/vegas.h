@@ -179,6 +179,22 @@ int vegas_eval_events(vegas_ctx* ctx, int integrand_id, const double* params, in
 int vegas_rng_words(uint64_t seed, uint32_t iteration, uint32_t batch, int64_t first_event,
                     int64_t n, int ndim, uint32_t* out);
 
+/* No-allocation variant of vegas_rng_words (the paper has no counterpart:
+ * it is for callers that cannot allocate device memory, e.g. while another
+ * thread captures a CUDA graph in global mode, or when a caching allocator
+ * holds the device's memory).  Same arguments, same words, but written
+ * through a fixed buffer of VEGAS_NOALLOC_MAX_WORDS uint32 words (1 MiB)
+ * inside the library; out is host memory owned by the caller.
+ * n * ndim > VEGAS_NOALLOC_MAX_WORDS: VEGAS_EINVAL, nothing launched.
+ * The first call on a device looks up the buffer's device address (a call
+ * with n = 0 does only that); make it before any stream capture begins.
+ * The buffer is shared by every caller on a device: calls that overlap on
+ * one device race on it, so the caller must serialise them.  Nothing in the
+ * buffer has to start at zero.  Blocking; runs on the legacy default stream. */
+#define VEGAS_NOALLOC_MAX_WORDS (1 << 18)
+int vegas_rng_words_noalloc(uint64_t seed, uint32_t iteration, uint32_t batch,
+                            int64_t first_event, int64_t n, int ndim, uint32_t* out);
+
 /* FP64 sums of the last iteration: (sum w, sum w^2, d[ndim*nbins]), with
  * d[a*nbins + i] = sum of w^2 over the events in bin i of axis a. */
 int vegas_last_sums(const vegas_ctx* ctx, double* sums);

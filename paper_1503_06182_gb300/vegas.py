@@ -27,6 +27,7 @@ VEGAS_KERNEL_FILL, VEGAS_KERNEL_REDUCE, VEGAS_KERNEL_REFINE = 0, 1, 2
 VEGAS_NGRAD = 5
 VEGAS_MAX_PARAMS = 16
 VEGAS_TILE = 1024
+VEGAS_NOALLOC_MAX_WORDS = 1 << 18
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +79,8 @@ def lib():
                                    _i32p], C.c_int),
             "vegas_rng_words": ([C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64, C.c_int,
                                  _u32p], C.c_int),
+            "vegas_rng_words_noalloc": ([C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64,
+                                         C.c_int, _u32p], C.c_int),
             "vegas_last_sums": ([_vp, _dp], C.c_int),
             "vegas_kernel_time": ([_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.c_int], C.c_int),
@@ -228,6 +231,20 @@ def vegas_rng_words(seed: int, iteration: int, batch: int, first_event: int, n: 
     out = np.zeros((n, ndim), np.uint32)
     _check(lib().vegas_rng_words(seed, iteration, batch, first_event, n, ndim, out.reshape(-1)),
            "vegas_rng_words")
+    return out
+
+
+def vegas_rng_words_noalloc(seed: int, iteration: int, batch: int, first_event: int, n: int,
+                            ndim: int) -> np.ndarray:
+    """vegas_rng_words through the library's fixed device buffer (no device
+    allocation); n * ndim is limited to VEGAS_NOALLOC_MAX_WORDS."""
+    out = np.zeros((n, ndim), np.uint32)
+    st = lib().vegas_rng_words_noalloc(seed, iteration, batch, first_event, n, ndim,
+                                       out.reshape(-1))
+    if st == VEGAS_EINVAL and ndim >= 1 and n * ndim > VEGAS_NOALLOC_MAX_WORDS:
+        raise VegasError(st, f"vegas_rng_words_noalloc: n*ndim = {n * ndim} exceeds the fixed "
+                             f"buffer of {VEGAS_NOALLOC_MAX_WORDS} words")
+    _check(st, "vegas_rng_words_noalloc")
     return out
 
 
