@@ -233,6 +233,7 @@ def run_gpu(args):
     ept = v.vegas_get_ept(g32.h)
     g32.close()
     g64.close()
+    form_rates = {} if args.no_forms else forms(v, stream, seed)
 
     clocks = sampler.summary(t_wall0 - 0.1, t_wall2 + 0.1) if sampler else None
     if sampler:
@@ -263,6 +264,7 @@ def run_gpu(args):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "flops_per_event": FLOPS_PER_EVENT_FP32},
         "fp64_path": {"value": value64, "unit": UNIT},
+        "forms": form_rates,
         "equal_error": {"sigma_fp32": sig["fp32"][1], "sigma_fp64": sig["fp64"][1],
                         "integral_fp32": sig["fp32"][0], "integral_fp64": sig["fp64"][0],
                         "efficiency_ratio_fp32_over_fp64": eff_ratio},
@@ -273,6 +275,68 @@ def run_gpu(args):
     print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def forms(v, stream, seed):
+    """The other workloads, each a warm-up stage then one timed stage on the
+    bench stream (device time between CUDA events; L2 not flushed inside a
+    stage, as in a real run): 3-jet 10 x 1e7 FP32; Drell-Yan adjoint 10 x 1e8
+    FP32 on a frozen grid; 64 batched integrations x 10 iterations (one graph);
+    the plain FP64 Gauss case 5 x 1e5."""
+    import torch
+
+    from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, EE3J, EE3J_PARAMS, GAUSS,
+                                                  GAUSS_PARAMS, batch_spec)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b), out
+
+    res = {}
+    for name, (iid, params, d, n, ncall, itmx, prec) in {
+            "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32"),
+            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64")}.items():
+        g = v.Vegas(d, n, seed, precision=prec)
+        v.vegas_set_stream(g.h, stream.cuda_stream)
+        try:
+            g.iterate(ncall, itmx, iid, params)  # warm-up stage (adapts, tunes, captures)
+            ms, (I, e, c, _, _) = timed(lambda: g.iterate(ncall, itmx, iid, params))
+        finally:
+            g.close()
+        res[name] = {"value": ncall * itmx / (ms * 1e-3), "unit": UNIT, "integral": I,
+                     "error": e, "chi2_dof": c}
+    # gradient: frozen grid adapted by a forward warm-up, then the adjoint stage
+    g = v.Vegas(NDIM, NBINS, seed, precision="fp32")
+    v.vegas_set_stream(g.h, stream.cuda_stream)
+    try:
+        g.iterate(NCALL, 5, DY, DY_PARAMS)
+        g.set(v.VEGAS_OPT_ADAPT, 0)
+        g.adjoint(10_000_000, 1, DY_PARAMS)  # tunes and sizes the workspace
+        ms, (grad, gerr, _, _, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
+    finally:
+        g.close()
+    res["dy_adjoint_d4_n100_10x1e8_fp32"] = {"value": 1e9 / (ms * 1e-3), "unit": UNIT,
+                                              "grad": list(grad), "grad_err": list(gerr)}
+    # batched: 64 integrations of uneven dimension, calls and integrand
+    spec = batch_spec(64, seed)
+    members = [(m.ndim, m.ncall, m.integrand, m.params) for m in spec]
+    B = v.VegasBatch(members, NBINS, seed, precision="fp32")
+    v.vegas_batch_set_stream(B.h, stream.cuda_stream)
+    try:
+        B.iterate(1)  # tunes events per thread
+        B.iterate(10)  # captures the 10-iteration graph
+        ms, _ = timed(lambda: B.iterate(10))
+    finally:
+        B.close()
+    tot = sum(m.ncall for m in spec) * 10
+    res["batch64_10it_fp32"] = {"value": tot / (ms * 1e-3), "unit": UNIT,
+                                "events_per_iteration": tot // 10}
+    return res
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -345,6 +409,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="CPU work of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the extra workloads reported under 'forms'")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

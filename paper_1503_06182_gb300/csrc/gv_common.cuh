@@ -39,7 +39,8 @@
 #define GV_NGRAD 5            // Drell-Yan gradient components
 #define GV_MAXCH (1 + GV_NGRAD)
 #define GV_EMPTY (-0x40000000)  // scale of a tile / iteration with no nonzero value
-#define GV_NCONST 48          // derived integrand constants per integration
+#define GV_NCONST 48          // derived integrand constants per integration (doubles)
+#define GV_NCONST_F32 24      // constants 0..23 in FP64, then their FP32 copies
 #define GV_MAXPARAMS 16
 #define GV_BINE_OFF 1100      // stored bin exponent F + GV_BINE_OFF (0: no nonzero weight)
 #define GV_BIN_QBITS 56       // bits of one w^2 below its bin's scale in a tile
@@ -65,18 +66,25 @@ struct GvState {
 };
 
 // Grid pack of one integration (device memory, rewritten by every refine):
-//   e64[d][N+1] | wd64[d][N] | jac[d][N] | e32[d][N+1] | wd32[d][N]
-// wd = e[i+1]-e[i]; jac = N*wd (the axis' Jacobian factor).
+//   e64[d][N+1] | wd64[d][N] | jac[d][N] | e32[d][N+1] | wd32[d][N] | jm32[d][N] | je[d][N]
+// wd = e[i+1]-e[i]; jac = N*wd (the axis' Jacobian factor) = jm32 2^je with
+// jm32 in [1,2] (FP32, for the FP32 form: mantissas multiplied in FP32,
+// exponents summed as integers, so the product has no FP32 range limit).
 struct GvGridLayout {
   int d, N;
   __host__ __device__ size_t off_e64() const { return 0; }
   __host__ __device__ size_t off_wd64() const { return (size_t)d * (N + 1); }
   __host__ __device__ size_t off_jac() const { return off_wd64() + (size_t)d * N; }
-  // float parts, counted in doubles from the start of the pack
+  // 32-bit parts, counted in doubles from the start of the pack
   __host__ __device__ size_t off_f32_base() const { return off_jac() + (size_t)d * N; }
+  // offsets of the 32-bit tables in 32-bit words from off_f32_base()
+  __host__ __device__ size_t w_e32() const { return 0; }
+  __host__ __device__ size_t w_wd32() const { return (size_t)d * (N + 1); }
+  __host__ __device__ size_t w_jm32() const { return w_wd32() + (size_t)d * N; }
+  __host__ __device__ size_t w_je() const { return w_jm32() + (size_t)d * N; }
   __host__ __device__ size_t doubles() const {
-    size_t nf = (size_t)d * (N + 1) + (size_t)d * N;  // floats
-    return off_f32_base() + (nf + 1) / 2;
+    const size_t nw = w_je() + (size_t)d * N;  // 32-bit words
+    return off_f32_base() + (nw + 1) / 2;
   }
 };
 

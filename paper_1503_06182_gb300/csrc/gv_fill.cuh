@@ -4,7 +4,8 @@
 // event generated and evaluated independently), with EPT events per thread:
 //   pass 1: Philox words -> bins and in-bin positions -> x on the adaptive grid
 //           ((edge, width) pairs and Jacobian factors staged in shared memory)
-//           -> g(x) -> w = J g (J in FP64 always); the bins stay in registers
+//           -> g(x) -> w = J g (J in FP64 in the FP64 form; FP32 mantissas
+//           with an integer exponent in the FP32 form); the bins stay in registers
 //           (d <= 4) or go to shared memory;
 //   tile scale: block max of |w| (order-free) -> E_t;
 //   pass 2: w and the exact square w^2 rounded once to fixed point at the tile
@@ -50,11 +51,72 @@ __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
 // One bin of one axis as staged in shared memory.
 struct __align__(16) GvBin32 {
   float e, w;     // edge and width in FP32
-  double jac;     // N * (e_{i+1} - e_i) in FP64
+  float jm;       // N * (e_{i+1} - e_i) = jm 2^je, jm in [1,2]
+  int je;
 };
 struct __align__(16) GvBin64 {
   double e, w;
 };
+// A float widened to double by integer operations (exact; the FP64 pipe of
+// this chip is scarce).  Zero, subnormal and non-finite inputs are handled.
+__device__ __forceinline__ double gv_widen(float g) {
+  const unsigned u = __float_as_uint(g);
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned ef = (u >> 23) & 0xFFu;
+  unsigned long long m = u & 0x7FFFFFu;
+  unsigned long long bits;
+  if (ef == 0xFFu) {
+    bits = sign | 0x7FF0000000000000ull | (m << 29);
+  } else if (ef != 0u) {
+    bits = sign | ((unsigned long long)(ef + 896u) << 52) | (m << 29);
+  } else if (m == 0ull) {
+    bits = sign;
+  } else {  // subnormal float m 2^-149, leading one at bit p = 23 - lz
+    const int lz = __clzll((long long)m) - 40;
+    m = (m << lz) & 0x7FFFFFull;
+    bits = sign | ((unsigned long long)(897 - lz) << 52) | (m << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double gv_widen(double g) { return g; }
+
+// The Jacobian of one event: FP64 in the FP64 form; in the FP32 form the
+// product of the FP32 mantissas and the sum of the exponents (no range limit,
+// and nothing on the FP64 pipe, of which this chip has little).
+template <typename Real>
+struct GvJac;
+template <>
+struct GvJac<double> {
+  double v;
+};
+template <>
+struct GvJac<float> {
+  float m;
+  int e;
+};
+
+// x 2^E for a double x, on the integer pipes: zero, infinity and NaN pass
+// through, a result beyond FP64 becomes infinity (counted as non-finite by
+// the caller), one below the normal range becomes zero.
+__device__ __forceinline__ double gv_ldexp_bits(double x, int E) {
+  const long long b = __double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  if (ef == 0 || ef == 0x7FF || E == 0) return x;
+  const int nf = ef + E;
+  const long long sign = b & (long long)0x8000000000000000ull;
+  if (nf >= 0x7FF) return __longlong_as_double(sign | 0x7FF0000000000000ll);
+  if (nf <= 0) return __longlong_as_double(sign);
+  return __longlong_as_double((b & ~0x7FF0000000000000ll) | ((long long)nf << 52));
+}
+
+// w = J g as a double.
+__device__ __forceinline__ double gv_weight(const GvJac<double>& J, double g) {
+  return __dmul_rn(J.v, g);
+}
+__device__ __forceinline__ double gv_weight(const GvJac<float>& J, float g) {
+  return gv_ldexp_bits(gv_widen(__fmul_rn(J.m, g)), J.e);
+}
+
 template <typename Real>
 struct GvPair;
 template <>
@@ -70,7 +132,7 @@ struct GvPair<double> {
 //   hist [4][d*N] u32     per-bin sums of w^2 in three 22-bit limbs, then the
 //                         tile's bin exponents F_tb + GV_BINE_OFF (forward only)
 //   jac  [d*N]    f64     Jacobian factor N*(e_{i+1}-e_i) (FP64 form only)
-//   ew   [d*N]    GvBin32 (e, w, jac) in the FP32 form, GvBin64 (e, w) in FP64
+//   ew   [d*N]    GvBin32 (e, w, jm, je) in the FP32 form, GvBin64 (e, w) in FP64
 //   bins [d][GV_TILE] u16 (forward kernels of the d > 4 classes only)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -98,9 +160,10 @@ __device__ __forceinline__ void gv_stage_grid(const double* grid, int d, int N, 
     const int a = k / N, i = k - a * N;
     if constexpr (sizeof(Real) == 4) {
       GvBin32 b;
-      b.e = g32[a * (N + 1) + i];
-      b.w = g32[(size_t)d * (N + 1) + k];
-      b.jac = grid[L.off_jac() + k];
+      b.e = g32[L.w_e32() + a * (N + 1) + i];
+      b.w = g32[L.w_wd32() + k];
+      b.jm = g32[L.w_jm32() + k];
+      b.je = reinterpret_cast<const int*>(g32)[L.w_je() + k];
       s_ew[k] = b;
     } else {
       s_jac[k] = grid[L.off_jac() + k];
@@ -112,16 +175,17 @@ __device__ __forceinline__ void gv_stage_grid(const double* grid, int d, int N, 
   }
 }
 
-// Map one event's words through the grid: x, bins and the FP64 Jacobian.
+// Map one event's words through the grid: x, bins and the Jacobian.
 // FP64: x = e_i + f*(e_{i+1}-e_i) with f = (lo + 1/2) 2^-32, rounded as
-// written; FP32: the same with FP32 edges and one fma.  The Jacobian product
-// starts from the first factor (J = 1 * f0 * f1 ... exactly).
+// written, J the FP64 product of the factors N (e_{i+1}-e_i); FP32: x with
+// FP32 edges and one fma, J as FP32 mantissa product and exponent sum.  The
+// product starts from the first factor (J = 1 * f0 * f1 ... exactly).
 template <typename Real, int MAXD>
-__device__ __forceinline__ double gv_map_event(const uint32_t (&r)[MAXD], int d, int N,
-                                               const double* s_jac,
-                                               const typename GvPair<Real>::T* s_ew,
-                                               Real (&x)[MAXD], int (&bin)[MAXD]) {
-  double J = 1.0;
+__device__ __forceinline__ GvJac<Real> gv_map_event(const uint32_t (&r)[MAXD], int d, int N,
+                                                    const double* s_jac,
+                                                    const typename GvPair<Real>::T* s_ew,
+                                                    Real (&x)[MAXD], int (&bin)[MAXD]) {
+  GvJac<Real> J;
 #pragma unroll
   for (int a = 0; a < MAXD; ++a) {
     if (a < d) {
@@ -129,17 +193,17 @@ __device__ __forceinline__ double gv_map_event(const uint32_t (&r)[MAXD], int d,
       const int i = (int)(v >> 32);
       const uint32_t lo = (uint32_t)v;
       const auto ew = s_ew[a * N + i];
-      double jf;
       if constexpr (sizeof(Real) == 4) {
         const float f = fmaf(__uint2float_rn(lo), 0x1p-32f, 0x1p-33f);
         x[a] = fmaf(f, ew.w, ew.e);
-        jf = ew.jac;
+        J.m = (a == 0) ? ew.jm : __fmul_rn(J.m, ew.jm);
+        J.e = (a == 0) ? ew.je : J.e + ew.je;
       } else {
         const double f = ((double)lo + 0.5) * 0x1p-32;
         x[a] = __dadd_rn(ew.e, __dmul_rn(f, ew.w));
-        jf = s_jac[a * N + i];
+        const double jf = s_jac[a * N + i];
+        J.v = (a == 0) ? jf : __dmul_rn(J.v, jf);
       }
-      J = (a == 0) ? jf : __dmul_rn(J, jf);
       bin[a] = i;
     }
   }
@@ -200,28 +264,6 @@ struct GvBinStore {
   }
 };
 
-// A float widened to double by integer operations (exact; the FP64 pipe of
-// this chip is scarce).  Zero, subnormal and non-finite inputs are handled.
-__device__ __forceinline__ double gv_widen(float g) {
-  const unsigned u = __float_as_uint(g);
-  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-  const unsigned ef = (u >> 23) & 0xFFu;
-  unsigned long long m = u & 0x7FFFFFu;
-  unsigned long long bits;
-  if (ef == 0xFFu) {
-    bits = sign | 0x7FF0000000000000ull | (m << 29);
-  } else if (ef != 0u) {
-    bits = sign | ((unsigned long long)(ef + 896u) << 52) | (m << 29);
-  } else if (m == 0ull) {
-    bits = sign;
-  } else {  // subnormal float m 2^-149, leading one at bit p = 23 - lz
-    const int lz = __clzll((long long)m) - 40;
-    m = (m << lz) & 0x7FFFFFull;
-    bits = sign | ((unsigned long long)(897 - lz) << 52) | (m << 29);
-  }
-  return __longlong_as_double((long long)bits);
-}
-__device__ __forceinline__ double gv_widen(double g) { return g; }
 
 // |x| bits of a double, and its finiteness, on the integer pipes.
 __device__ __forceinline__ unsigned long long gv_abs_bits(double x) {
@@ -271,10 +313,10 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
       Real x[MAXD];
       int bin[MAXD];
-      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
+      const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
       bs[k].put(bin, d, s_bin, local);
       const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
-      const double wv = __dmul_rn(J, gv_widen(g));
+      const double wv = gv_weight(J, g);
       const unsigned long long ab = gv_abs_bits(wv);
       if (gv_finite_bits(ab)) {
         w[k] = wv;
@@ -409,13 +451,13 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
       Real x[MAXD];
       int bin[MAXD];
-      const double J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
+      const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
       Real gr[GV_NGRAD];
       const Real g = gv_drell_yan<Real, true>(x, K, gr);
       double vals[NCH];
-      vals[0] = __dmul_rn(J, gv_widen(g));
+      vals[0] = gv_weight(J, g);
 #pragma unroll
-      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = __dmul_rn(J, gv_widen(gr[p]));
+      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = gv_weight(J, gr[p]);
       bool finite = true;
 #pragma unroll
       for (int c = 0; c < NCH; ++c) finite &= gv_finite_bits(gv_abs_bits(vals[c]));
@@ -471,31 +513,36 @@ __global__ void gv_eval_events_kernel(const GvFillArgs a, uint32_t it, const lon
   const double* wd64 = a.grid + L.off_wd64();
   const double* jac = a.grid + L.off_jac();
   const float* g32 = reinterpret_cast<const float*>(a.grid + L.off_f32_base());
-  const float* e32 = g32;
-  const float* wd32 = g32 + (size_t)d * (N + 1);
+  const float* e32 = g32 + L.w_e32();
+  const float* wd32 = g32 + L.w_wd32();
+  const float* jm32 = g32 + L.w_jm32();
+  const int* je = reinterpret_cast<const int*>(g32 + L.w_je());
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
   uint32_t r[MAXD];
   gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)events[j], d, r);
   Real x[MAXD];
-  double J = 1.0;
+  GvJac<Real> J;
 #pragma unroll
   for (int ax = 0; ax < MAXD; ++ax) {
     if (ax < d) {
       const unsigned long long v = (unsigned long long)r[ax] * (unsigned)N;
       const int i = (int)(v >> 32);
       const uint32_t lo = (uint32_t)v;
+      const int k = ax * N + i;
       if constexpr (sizeof(Real) == 4) {
         const float f = fmaf(__uint2float_rn(lo), 0x1p-32f, 0x1p-33f);
-        x[ax] = fmaf(f, wd32[ax * N + i], e32[ax * (N + 1) + i]);
+        x[ax] = fmaf(f, wd32[k], e32[ax * (N + 1) + i]);
+        J.m = (ax == 0) ? jm32[k] : __fmul_rn(J.m, jm32[k]);
+        J.e = (ax == 0) ? je[k] : J.e + je[k];
       } else {
         const double f = ((double)lo + 0.5) * 0x1p-32;
-        x[ax] = __dadd_rn(e64[ax * (N + 1) + i], __dmul_rn(f, wd64[ax * N + i]));
+        x[ax] = __dadd_rn(e64[ax * (N + 1) + i], __dmul_rn(f, wd64[k]));
+        J.v = (ax == 0) ? jac[k] : __dmul_rn(J.v, jac[k]);
       }
-      J = (ax == 0) ? jac[i] : __dmul_rn(J, jac[ax * N + i]);
       bins[j * d + ax] = i;
     }
   }
   const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
-  w[j] = __dmul_rn(J, gv_widen(g));
+  w[j] = gv_weight(J, g);
 }

@@ -82,10 +82,19 @@ struct GvMath<double> {
 // Constants as the integrand's arithmetic type, loaded once per thread.
 template <typename Real, int NC>
 struct GvConst {
+  static_assert(NC <= GV_NCONST_F32, "constants beyond the FP32 copy");
   Real v[NC];
+  // FP64 constants from k[0..NC); the FP32 form reads the FP32 copies that
+  // the constants kernel stores after them (no conversions per CTA)
   __device__ __forceinline__ void load(const double* k) {
+    if constexpr (sizeof(Real) == 4) {
+      const float* kf = reinterpret_cast<const float*>(k + GV_NCONST_F32);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) v[i] = (Real)k[i];
+      for (int i = 0; i < NC; ++i) v[i] = kf[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) v[i] = k[i];
+    }
   }
   __device__ __forceinline__ Real operator[](int i) const { return v[i]; }
 };

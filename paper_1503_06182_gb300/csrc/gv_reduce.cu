@@ -532,8 +532,11 @@ __device__ void pack_axis_tables(double* grid, const double* e_src, int d, int N
   double* e64 = grid + L.off_e64();
   double* wd64 = grid + L.off_wd64();
   double* jac = grid + L.off_jac();
-  float* e32 = reinterpret_cast<float*>(grid + L.off_f32_base());
-  float* wd32 = e32 + (size_t)d * (N + 1);
+  float* w32 = reinterpret_cast<float*>(grid + L.off_f32_base());
+  float* e32 = w32 + L.w_e32();
+  float* wd32 = w32 + L.w_wd32();
+  float* jm32 = w32 + L.w_jm32();
+  int* je = reinterpret_cast<int*>(w32 + L.w_je());
   for (int k = tid; k < d * (N + 1); k += nthr) {
     const int a = k / (N + 1), i = k % (N + 1);
     const size_t ie = (size_t)a * (N + 1) + i;
@@ -542,9 +545,20 @@ __device__ void pack_axis_tables(double* grid, const double* e_src, int d, int N
     e32[ie] = (float)e;
     if (i < N) {
       const double w = e_src[ie + 1] - e;
-      wd64[(size_t)a * N + i] = w;
-      jac[(size_t)a * N + i] = (double)N * w;
-      wd32[(size_t)a * N + i] = (float)w;
+      const double j = (double)N * w;
+      const size_t ib = (size_t)a * N + i;
+      wd64[ib] = w;
+      jac[ib] = j;
+      wd32[ib] = (float)w;
+      // j = m 2^x with m in [1,2): exponent from the bits (j > 0; a subnormal
+      // j is scaled into the normal range first)
+      const bool sub = j < 0x1p-1000;
+      const double js = sub ? j * 0x1p200 : j;
+      const long long b = __double_as_longlong(js);
+      const int x = (int)((b >> 52) & 0x7FF) - 1023;
+      const double m = __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+      jm32[ib] = (float)m;
+      je[ib] = sub ? x - 200 : x;
     }
   }
 }
@@ -786,6 +800,8 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
     K[EK_Q] = Q;
     K[EK_INVQ2] = 1.0 / (Q * Q);
   }
+  float* kf = reinterpret_cast<float*>(K + GV_NCONST_F32);
+  for (int i = 0; i < GV_NCONST_F32; ++i) kf[i] = (float)K[i];
 }
 
 // Reset the per-iteration invariants (at creation and after the autotuner's
