@@ -75,8 +75,9 @@ extern "C" {
 
 /* ---- kernel ids for vegas_kernel_time ---- */
 #define VEGAS_KERNEL_FILL 0   /* per-event kernel */
-#define VEGAS_KERNEL_REDUCE 1 /* combination of all events (and the iteration record) */
-#define VEGAS_KERNEL_REFINE 2 /* grid optimisation */
+#define VEGAS_KERNEL_REDUCE 1 /* combination of all events, iteration record, grid optimisation */
+#define VEGAS_KERNEL_REFINE 2 /* grid optimisation alone: runs inside the reduce kernel, so it
+                                 reports 0 launches */
 
 typedef struct vegas_ctx vegas_ctx;
 typedef struct vegas_batch vegas_batch;

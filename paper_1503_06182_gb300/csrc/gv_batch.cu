@@ -4,8 +4,8 @@
 // independent runs (Section 2.1); here many *different* integrations (uneven
 // dimension, call count and integrand) share the GPU.  Each iteration is
 //   one persistent fill launch over a work list of (integration, tile) items,
-//   one reduce launch whose CTAs serve all integrations (task table),
-//   one refine launch likewise,
+//   one reduce launch whose CTAs serve all integrations (task table) and
+//   refine each integration's axes as they complete,
 // and the itmx iterations are captured in one CUDA graph.  The work list
 // orders the integrations by decreasing expected cost (largest first) and
 // CTAs take items from an integer counter; since every tile is summed
@@ -161,19 +161,18 @@ double tile_cost(int ig, int d) {
 }
 
 struct Member {
-  int ig, d, np, n_tiles, nacc, nslots;
+  int ig, d, np, n_tiles, nacc, gx, gy;
   int64_t ncall;
   double params[GV_MAXPARAMS];
   double* grid;
   GvState* st;
   double* par;
   double* kconst;
-  unsigned long long* acc;
+  GvSlot* cpart;
   double* sums;
-  double* scratch;
   ulonglong2* part;
   int* tileE;
-  int* binE;
+  int* tickets;
 };
 
 }  // namespace
@@ -194,17 +193,15 @@ struct vegas_batch {
   // launch tables
   GvFillArgs* d_fill = nullptr;
   GvReduceArgs* d_red = nullptr;
-  GvRefineArgs* d_ref = nullptr;
   int4* d_red_tasks = nullptr;
-  int4* d_ref_tasks = nullptr;
-  int n_red_tasks = 0, n_ref_tasks = 0;
+  int n_red_tasks = 0;
   int* d_ig = nullptr;
   int* d_order = nullptr;
   long long* d_item_start = nullptr;
   long long total_items = 0;
   unsigned long long* d_counter = nullptr;
   double* logtab = nullptr;
-  size_t fill_smem = 0, refine_smem = 0;
+  size_t fill_smem = 0, reduce_smem = 0;
   int ept = 0, fill_ctas = 0;
   // graph cache
   std::string graph_key;
@@ -249,7 +246,7 @@ int occupancy(vegas_batch* B, int ept) {
 
 int reset_all(vegas_batch* B) {
   for (const Member& x : B->m)
-    GB_TRY(gv::launch_reset(x.st, x.nslots, x.acc, x.binE, x.d * B->N, B->stream));
+    GB_TRY(gv::launch_reset(x.st, B->stream));
   return VEGAS_OK;
 }
 
@@ -258,8 +255,7 @@ int upload_tables(vegas_batch* B) {
   const int n = B->n;
   std::vector<GvFillArgs> fa(n);
   std::vector<GvReduceArgs> ra(n);
-  std::vector<GvRefineArgs> fr(n);
-  std::vector<int4> rt, ft;
+  std::vector<int4> rt;
   for (int b = 0; b < n; ++b) {
     const Member& x = B->m[b];
     GvFillArgs& a = fa[b];
@@ -276,7 +272,6 @@ int upload_tables(vegas_batch* B) {
     a.st = x.st;
     a.part = x.part;
     a.tileE = x.tileE;
-    a.binE = x.binE;
     GvReduceArgs& r = ra[b];
     memset(&r, 0, sizeof r);
     r.ndim = x.d;
@@ -295,38 +290,22 @@ int upload_tables(vegas_batch* B) {
     r.part = x.part;
     r.tileE = x.tileE;
     r.st = x.st;
-    r.acc = x.acc;
+    r.cpart = x.cpart;
     r.sums = x.sums;
     r.per_iter = B->per_iter + (size_t)b * B->per_iter_cap * 2;
-    r.inv_total = x.scratch + 4 * (size_t)x.d * (B->N + 1);
-    r.binE = x.binE;
+    r.tickets = x.tickets;
+    r.alpha = B->alpha;
+    r.inv_nbins = 1.0 / (double)B->N;
+    r.logtab = B->logtab;
+    r.grid = x.grid;
     for (int yy = 0; yy < gy; ++yy)
       for (int xx = 0; xx < gx; ++xx) rt.push_back(make_int4(b, xx, yy, gx * gy));
-    GvRefineArgs& f = fr[b];
-    memset(&f, 0, sizeof f);
-    f.ndim = x.d;
-    f.nbins = B->N;
-    f.nch = 1;
-    f.nacc = x.nacc;
-    f.alpha = B->alpha;
-    f.inv_nbins = 1.0 / (double)B->N;
-    f.logtab = B->logtab;
-    f.acc = x.acc;
-    f.dsum = x.sums + 2;
-    f.inv_total = r.inv_total;
-    f.grid = x.grid;
-    f.scratch = x.scratch;
-    f.st = x.st;
-    f.binE = x.binE;
-    const int nr = gv::refine_ctas(x.d, B->N);
-    for (int xx = 0; xx < nr; ++xx) ft.push_back(make_int4(b, xx, 0, nr));
   }
   // tables live in one allocation, reallocated when the task counts change
   cudaFree(B->d_fill);
   B->d_fill = nullptr;
   const size_t bytes = a256(sizeof(GvFillArgs) * n) + a256(sizeof(GvReduceArgs) * n) +
-                       a256(sizeof(GvRefineArgs) * n) + a256(sizeof(int4) * rt.size()) +
-                       a256(sizeof(int4) * ft.size());
+                       a256(sizeof(int4) * rt.size());
   void* t = nullptr;
   GB_TRY(cudaMalloc(&t, bytes));
   char* c = (char*)t;
@@ -334,18 +313,11 @@ int upload_tables(vegas_batch* B) {
   c += a256(sizeof(GvFillArgs) * n);
   B->d_red = (GvReduceArgs*)c;
   c += a256(sizeof(GvReduceArgs) * n);
-  B->d_ref = (GvRefineArgs*)c;
-  c += a256(sizeof(GvRefineArgs) * n);
   B->d_red_tasks = (int4*)c;
-  c += a256(sizeof(int4) * rt.size());
-  B->d_ref_tasks = (int4*)c;
   B->n_red_tasks = (int)rt.size();
-  B->n_ref_tasks = (int)ft.size();
   GB_TRY(cudaMemcpy(B->d_fill, fa.data(), sizeof(GvFillArgs) * n, cudaMemcpyHostToDevice));
   GB_TRY(cudaMemcpy(B->d_red, ra.data(), sizeof(GvReduceArgs) * n, cudaMemcpyHostToDevice));
-  GB_TRY(cudaMemcpy(B->d_ref, fr.data(), sizeof(GvRefineArgs) * n, cudaMemcpyHostToDevice));
   GB_TRY(cudaMemcpy(B->d_red_tasks, rt.data(), sizeof(int4) * rt.size(), cudaMemcpyHostToDevice));
-  GB_TRY(cudaMemcpy(B->d_ref_tasks, ft.data(), sizeof(int4) * ft.size(), cudaMemcpyHostToDevice));
   return VEGAS_OK;
 }
 
@@ -373,10 +345,7 @@ int enqueue_iterations(vegas_batch* B, int itmx) {
     GB_TRY(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), B->stream));
     GB_TRY(fill_batch(B, B->ept));
     GB_TRY(gv::launch_reduce_batch(B->d_red, B->d_red_tasks, B->n_red_tasks, k, k == itmx - 1,
-                                   k > 0 ? 1.0 / (double)k : 0.0, B->stream));
-    if (B->adapt)
-      GB_TRY(gv::launch_refine_batch(B->d_ref, B->d_ref_tasks, B->n_ref_tasks, B->refine_smem,
-                                     B->stream));
+                                   k > 0 ? 1.0 / (double)k : 0.0, B->reduce_smem, B->stream));
   }
   return VEGAS_OK;
 }
@@ -469,7 +438,8 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     x.params[GV_MAXPARAMS - 1] = (double)x.np;
     x.n_tiles = (int)((x.ncall + GV_TILE - 1) / GV_TILE);
     x.nacc = 2 + x.d * nbins;
-    x.nslots = x.nacc + x.d;
+    int tpc = 0;
+    gv::reduce_grid(x.n_tiles, x.nacc, &tpc, &x.gx, &x.gy);
     size_t* q = &o[b * 10];
     q[0] = off;
     off = a256(off + GvGridLayout{x.d, nbins}.doubles() * 8);
@@ -479,18 +449,16 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     off = a256(off + GV_MAXPARAMS * 8);
     q[3] = off;
     off = a256(off + GV_NCONST * 8);
-    q[4] = off;
-    off = a256(off + (size_t)x.nslots * 4 * 8);
+    q[4] = off;  // cpart
+    off = a256(off + (size_t)x.gy * x.gx * 32 * sizeof(GvSlot));
     q[5] = off;
     off = a256(off + (size_t)x.nacc * 8);
-    q[6] = off;
-    off = a256(off + ((size_t)4 * x.d * (nbins + 1) + GV_MAXD) * 8);
     q[7] = off;
     off = a256(off + (size_t)x.n_tiles * x.nacc * 16);
     q[8] = off;
     off = a256(off + (size_t)x.n_tiles * 4);
-    q[9] = off;
-    off = a256(off + (size_t)x.d * nbins * 4);
+    q[6] = off;  // tickets
+    off = a256(off + gv_tickets_ints(x.nacc) * 4);
   }
   const size_t o_counter = off;
   off = a256(off + 8);
@@ -515,12 +483,11 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     x.st = (GvState*)(base + q[1]);
     x.par = (double*)(base + q[2]);
     x.kconst = (double*)(base + q[3]);
-    x.acc = (unsigned long long*)(base + q[4]);
+    x.cpart = (GvSlot*)(base + q[4]);
     x.sums = (double*)(base + q[5]);
-    x.scratch = (double*)(base + q[6]);
     x.part = (ulonglong2*)(base + q[7]);
     x.tileE = (int*)(base + q[8]);
-    x.binE = (int*)(base + q[9]);
+    x.tickets = (int*)(base + q[6]);
   }
   B->d_counter = (unsigned long long*)(base + o_counter);
   B->logtab = (double*)(base + o_log);
@@ -542,7 +509,7 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
         cudaMemcpy(x.par, x.params, sizeof x.params, cudaMemcpyHostToDevice) != cudaSuccess ||
         gv::launch_grid_pack(x.d, nbins, x.grid, B->stream) != cudaSuccess ||
         gv::launch_consts(x.ig, x.par, x.kconst, B->stream) != cudaSuccess ||
-        gv::launch_reset(x.st, x.nslots, x.acc, x.binE, x.d * nbins, B->stream) != cudaSuccess)
+        gv::launch_reset(x.st, B->stream) != cudaSuccess)
       st = VEGAS_ECUDA;
   }
   // work list: largest expected cost first
@@ -565,13 +532,11 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
       st = VEGAS_ECUDA;
   }
   if (!st) {
-    size_t fs = 0, rs = 0;
-    for (const Member& x : B->m) {
+    size_t fs = 0;
+    for (const Member& x : B->m)
       fs = std::max(fs, GvFillSmem(x.d, nbins, B->fp32 ? 4 : 8, true, true).total);
-      rs = std::max(rs, gv::refine_smem_bytes(x.d, nbins));
-    }
     B->fill_smem = fs;
-    B->refine_smem = rs;
+    B->reduce_smem = gv::reduce_smem_bytes(nbins);
     st = ensure_per_iter(B, 16);
   }
   if (!st && cudaStreamSynchronize(B->stream) != cudaSuccess) st = VEGAS_ECUDA;

@@ -4,7 +4,7 @@
 // iteration state, accumulators) and, unless the caller hands it one, the
 // workspace (tile partials, per-iteration records).  A stage of itmx
 // iterations (Section 2.1; the two-stage runs of Section 3.2) is enqueued as
-//   itmx x [fill -> reduce -> refine]
+//   itmx x [fill -> reduce (with the per-axis grid refinement)]
 // and, by default, captured once into a CUDA graph that is replayed by later
 // calls with the same shape; the iteration counter, the derived integrand
 // constants and the grid are read from device memory, so a replay needs no
@@ -131,11 +131,9 @@ struct vegas_ctx {
   GvState* st = nullptr;
   double* params = nullptr;
   double* kconst = nullptr;
-  unsigned long long* acc = nullptr;
   double* sums = nullptr;
-  double* scratch = nullptr;
   double* logtab = nullptr;
-  int* binE = nullptr;  // [ndim*nbins] bin exponents of the running iteration
+  int* tickets = nullptr;  // reduce tickets (zero between iterations)
   int nacc_max = 0;
   // workspace
   void* ws = nullptr;
@@ -174,9 +172,12 @@ size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode) {
   const int64_t n_tiles = (ncall + GV_TILE - 1) / GV_TILE;
   const int nch = mode ? GV_MAXCH : 1;
   const int nacc = mode ? 2 * GV_MAXCH : 2 + d * N;
+  int tpc = 0, gx = 0, gy = 0;
+  gv::reduce_grid((int)std::min<int64_t>(n_tiles, 0x7fffffff), nacc, &tpc, &gx, &gy);
   size_t b = align256((size_t)n_tiles * nacc * 16);
   b += align256((size_t)n_tiles * nch * 4);
   b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
+  b += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
   return b;
 }
 
@@ -220,6 +221,7 @@ struct Plan {
   ulonglong2* part;
   int* tileE;
   double* per_iter;
+  GvSlot* cpart;
 };
 
 GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
@@ -236,7 +238,6 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   a.st = c->st;
   a.part = p.part;
   a.tileE = p.tileE;
-  a.binE = c->binE;
   return a;
 }
 
@@ -260,30 +261,14 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.part = p.part;
   r.tileE = p.tileE;
   r.st = c->st;
-  r.acc = c->acc;
+  r.cpart = p.cpart;
   r.sums = c->sums;
   r.per_iter = p.per_iter;
-  r.inv_total = c->scratch + 4 * (size_t)c->ndim * (c->nbins + 1);
-  r.binE = c->binE;
-  return r;
-}
-
-GvRefineArgs refine_args(const vegas_ctx* c) {
-  GvRefineArgs r;
-  r.ndim = c->ndim;
-  r.nbins = c->nbins;
-  r.nch = 1;
-  r.nacc = 2 + c->ndim * c->nbins;
-  r.acc = c->acc;
+  r.tickets = c->tickets;
   r.alpha = c->alpha;
   r.inv_nbins = 1.0 / (double)c->nbins;
   r.logtab = c->logtab;
-  r.dsum = c->sums + 2;
-  r.inv_total = c->scratch + 4 * (size_t)c->ndim * (c->nbins + 1);
   r.grid = c->grid;
-  r.scratch = c->scratch;
-  r.st = c->st;
-  r.binE = c->binE;
   return r;
 }
 
@@ -356,7 +341,7 @@ int autotune(vegas_ctx* c, Plan& p) {
   cudaEventDestroy(e1);
   GV_TRY(cudaGetLastError());
   // the trial launches touched the iteration invariants: restore them
-  GV_TRY(gv::launch_reset(c->st, p.nacc, c->acc, c->binE, c->ndim * c->nbins, c->stream));
+  GV_TRY(gv::launch_reset(c->st, c->stream));
   p.ept = best_ept;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best_ept;
@@ -387,26 +372,24 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.tileE = (int*)w;
   w += align256((size_t)p.n_tiles * p.nch * 4);
   p.per_iter = (double*)w;
+  w += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
+  p.cpart = (GvSlot*)w;
   p.ept = c->ept_opt;
   return VEGAS_OK;
 }
 
 int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool capture) {
   const unsigned flags = capture ? cudaEventRecordExternal : 0u;
-  const GvRefineArgs rf = refine_args(c);
-  const bool refine = p.mode == 0 && c->adapt;
-  if (refine) GV_TRY(gv::prepare_refine(c->ndim, c->nbins));
+  const size_t rsmem = gv::reduce_smem_bytes(c->nbins);
   // programmatic launches chain the kernels of consecutive iterations; the
   // first fill follows ordinary work and timed runs keep plain launches
   const bool pdl = c->pdl && !ev;
   for (int k = 0; k < p.itmx; ++k) {
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k], c->stream, flags));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 1], c->stream, flags));
-    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), c->stream, pdl));
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 2], c->stream, flags));
-    if (refine) GV_TRY(gv::launch_refine(rf, c->stream, pdl));
-    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[4 * k + 3], c->stream, flags));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
+    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
+    if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
   return VEGAS_OK;
 }
@@ -467,7 +450,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
         if (c->graphs.size() >= 16) drop_oldest_entry(c);
         GraphEntry g;
         g.key = key;
-        st = new_events(g.events, 4 * (size_t)itmx);
+        st = new_events(g.events, 3 * (size_t)itmx);
         if (st) return st;
         c->graphs.push_back(g);
         ge = &c->graphs.back();
@@ -491,7 +474,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
     GraphEntry g;
     g.key = key;
     if (c->timing) {
-      st = new_events(g.events, 4 * (size_t)itmx);
+      st = new_events(g.events, 3 * (size_t)itmx);
       if (st) return st;
     }
     cudaGraph_t graph;
@@ -533,9 +516,9 @@ int fetch_stage(vegas_ctx* c, GvState* hs, std::vector<double>* per_iter) {
   memcpy(hs, pin, sizeof(GvState));
   if (per_iter) per_iter->assign(pin_rec, pin_rec + nrec);
   if (!c->pending_events.empty()) {
-    for (size_t k = 0; k + 3 < c->pending_events.size(); k += 4) {
-      float t[3] = {0.f, 0.f, 0.f};
-      for (int q = 0; q < 3; ++q)
+    for (size_t k = 0; k + 2 < c->pending_events.size(); k += 3) {
+      float t[2] = {0.f, 0.f};
+      for (int q = 0; q < 2; ++q)
         if (cudaEventElapsedTime(&t[q], c->pending_events[k + q], c->pending_events[k + q + 1]) ==
             cudaSuccess) {
           c->t_ms[q] += t[q];
@@ -641,8 +624,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
     return VEGAS_ECUDA;
   }
   c->own_stream = true;
-  // accumulator slots: channel sums, bin sums, per-axis totals
-  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins + ndim);
+  // slots: channel sums, bin sums
+  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins);
   const size_t gd = grid_doubles(ndim, nbins);
   size_t off = 0;
   const size_t o_grid = off;
@@ -653,16 +636,12 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   off = align256(off + GV_MAXPARAMS * 8);
   const size_t o_k = off;
   off = align256(off + GV_NCONST * 8);
-  const size_t o_acc = off;
-  off = align256(off + (size_t)c->nacc_max * 4 * 8);
   const size_t o_log = off;
   off = align256(off + 258 * 8);
   const size_t o_sums = off;
   off = align256(off + (size_t)c->nacc_max * 8);
-  const size_t o_scr = off;
-  off = align256(off + ((size_t)4 * ndim * (nbins + 1) + GV_MAXD) * 8);
-  const size_t o_bine = off;
-  off = align256(off + (size_t)ndim * nbins * 4);
+  const size_t o_tick = off;
+  off = align256(off + gv_tickets_ints(c->nacc_max) * 4);
   if (cudaMalloc(&c->fixed, off) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(c->stream);
@@ -674,15 +653,12 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   c->st = (GvState*)(b + o_st);
   c->params = (double*)(b + o_par);
   c->kconst = (double*)(b + o_k);
-  c->acc = (unsigned long long*)(b + o_acc);
   c->sums = (double*)(b + o_sums);
-  c->scratch = (double*)(b + o_scr);
   c->logtab = (double*)(b + o_log);
-  c->binE = (int*)(b + o_bine);
+  c->tickets = (int*)(b + o_tick);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess ||
-      gv::launch_reset(c->st, c->nacc_max, c->acc, c->binE, ndim * nbins, c->stream) !=
-          cudaSuccess)
+      gv::launch_reset(c->st, c->stream) != cudaSuccess)
     st = VEGAS_ECUDA;
   if (!st && cudaMemcpyAsync(c->logtab, gv::host_log_table(), 258 * sizeof(double),
                              cudaMemcpyHostToDevice, c->stream) != cudaSuccess)

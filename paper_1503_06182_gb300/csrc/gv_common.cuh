@@ -6,9 +6,9 @@
 //            Philox4x32-10, grid map, integrand, then exact integer
 //            accumulation of sum w, sum w^2 and the per-bin sums of w^2
 //            into a per-tile partial;
-//   reduce : exact integer reduction of the tile partials; the last CTA to
-//            finish converts the sums to FP64, records the iteration and
-//            refines the grid.
+//   reduce : exact integer reduction of the tile partials; the CTA that
+//            completes an axis refines that axis' grid, and the last CTA to
+//            finish converts the sums to FP64 and records the iteration.
 //
 // Exact accumulation.  Every tile takes its scale from its largest |v| (an
 // order-free max): E_t with max|v| < 2^E_t.  Each v is rounded once to an
@@ -50,17 +50,13 @@
 enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2 };
 
 // Device-side state of one integration (one context or one batch member).
-// E, done, done_refine, nonfinite_iter and the accumulators return to their
-// reset values at the end of every iteration.
+// nonfinite_iter and the tickets return to zero at the end of every iteration.
 struct GvState {
   unsigned long long it;              // global iteration counter (Philox counter word)
   unsigned long long nonfinite_iter;  // non-finite weights of the running iteration
   unsigned long long nonfinite;       // non-finite weights of the stage
-  int done;                           // reduce CTAs finished (last-block ticket)
-  int done_refine;                    // refine CTAs finished (last-block ticket)
   int status;                         // device error word (0 = ok)
-  int E[GV_MAXCH];                    // per-channel iteration scale (atomicMax)
-  int E0_prev;                        // channel-0 scale of the last finished iteration
+  int pad;
   double integral, error, chi2;
   double grad[GV_NGRAD], grad_err[GV_NGRAD];
 };
@@ -99,40 +95,50 @@ struct GvFillArgs {
   GvState* st;
   ulonglong2* part;              // [tile][nacc] 128-bit two's complement sums
   int* tileE;                    // [tile][nch] scales
-  int* binE;                     // [ndim*nbins] iteration bin exponents (atomicMax)
 };
 
+// One slot's sum as a 192-bit two's complement integer with its exponent:
+// channel slot 2c (sum v) / 2c+1 (sum v^2): value = v 2^(pw e - GV_FB),
+// pw = 1 / 2, e a tile scale (GV_EMPTY: nothing nonzero); bin slot: value =
+// v 2^(2 (e - GV_BINE_OFF) - GV_BIN_FB), e a stored bin exponent (0: empty).
+struct __align__(16) GvSlot {
+  unsigned long long l0, l1, l2;
+  int e, pad;
+};
+
+// Tickets of the reduce kernel, each on its own 128-byte line: one per slot
+// block of 32 slots, one per axis, one for the whole iteration.
+#define GV_TICKET_STRIDE 32
+__host__ __device__ inline int gv_ticket_group(int x) { return x * GV_TICKET_STRIDE; }
+__host__ __device__ inline int gv_ticket_axis(int nacc, int ax) {
+  return ((nacc + 31) / 32 + ax) * GV_TICKET_STRIDE;
+}
+__host__ __device__ inline int gv_ticket_done(int nacc) {
+  return ((nacc + 31) / 32 + GV_MAXD) * GV_TICKET_STRIDE;
+}
+__host__ __device__ inline size_t gv_tickets_ints(int nacc) {
+  return (size_t)gv_ticket_done(nacc) + GV_TICKET_STRIDE;
+}
+
 // Arguments of the reduce/finalize kernel.
-// Accumulator slots: [0, 2*nch) channel sums, then (forward) ndim*nbins bin
-// sums, then (forward) ndim exact per-axis totals of 6 x the smoothed bin sums.
+// Slots: [0, 2*nch) channel sums, then (forward) ndim*nbins bin sums.
 struct GvReduceArgs {
   int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
-  int refine_follows;            // 1: the refine kernel converts and resets the bin slots
+  int refine_follows;            // 1: each axis is refined by the CTA that completes it
   long long ncall;
   double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration
   int n_tiles, tiles_per_cta;
   const ulonglong2* part;
   const int* tileE;
   GvState* st;
-  unsigned long long* acc;       // [nacc][4] accumulator limbs (3 used)
+  GvSlot* cpart;                 // [tile ranges][32 * slot blocks] one CTA's sums
   double* sums;                  // [nacc] FP64 sums of the last iteration
   double* per_iter;              // forward: [itmx][2]; adjoint: [itmx][2 + 2*NGRAD]
-  double* inv_total;             // [ndim] 1 / (6 x sum of the smoothed bin sums), 0 if none
-  int* binE;                     // [ndim*nbins] bin exponents of the iteration
-};
-
-// Arguments of the refine kernel.
-struct GvRefineArgs {
-  int ndim, nbins, nch, nacc;
+  int* tickets;                  // gv_tickets_ints(nacc) counters, one per 128-byte line
+  // grid refinement
   double alpha, inv_nbins;
   const double* logtab;          // table of the FP64 log (see gv_reduce.cu)
-  unsigned long long* acc;       // accumulator limbs (bin slots are read, then reset)
-  double* dsum;                  // [ndim][nbins] FP64 bin sums (written here)
-  const double* inv_total;       // [ndim] from the reduce kernel
-  double* grid;                  // grid pack (refined in place)
-  double* scratch;               // 4 * d * (N+1) doubles
-  GvState* st;
-  int* binE;                     // [ndim*nbins] bin exponents (read, then reset)
+  double* grid;                  // grid pack (refined in place, one axis per CTA)
 };
 
 // ----------------------------------------------------------------------------
@@ -347,18 +353,12 @@ namespace gv {
 cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
                                 size_t smem, cudaStream_t s, bool pdl);
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
-cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s, bool pdl);
-cudaError_t prepare_refine(int d, int N);
-cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl);
-size_t refine_smem_bytes(int d, int N);
-int refine_ctas(int d, int N);
+size_t reduce_smem_bytes(int N);  // dynamic shared memory of the reduce kernels
+cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl);
 cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
-                                int last, double inv_m1, cudaStream_t s);
-cudaError_t launch_refine_batch(const GvRefineArgs* args, const int4* tasks, int ntasks,
-                                size_t smem, cudaStream_t s);
+                                int last, double inv_m1, size_t smem, cudaStream_t s);
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);
-cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, int* binE, int dN,
-                         cudaStream_t s);
+cudaError_t launch_reset(GvState* st, cudaStream_t s);
 cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
 const double* host_log_table();  // 258 doubles, see gv_log_pos
 cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,

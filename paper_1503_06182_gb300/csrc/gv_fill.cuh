@@ -371,7 +371,6 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     out[0] = make_ulonglong2(t1.lo, t1.hi);
     out[1] = make_ulonglong2(t2.lo, t2.hi);
     a.tileE[tile] = E;
-    if (E != GV_EMPTY) atomicMax(&a.st->E[0], E);
   }
   if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
   for (int k = tid; k < dN; k += B) {
@@ -381,10 +380,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     u128 v = {l0, 0ull};
     v = add128(v, u128{l1 << 22, l1 >> 42});
     v = add128(v, u128{l2 << 44, l2 >> 20});
-    const int f = ebin[k];
-    out[2 + k] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)f << 32));
-    // the iteration's bin exponents: a max, so a stale read costs one atomic
-    if (f > __ldcg(a.binE + k)) atomicMax(a.binE + k, f);
+    out[2 + k] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)ebin[k] << 32));
   }
 }
 
@@ -493,7 +489,6 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       out[2 * c] = make_ulonglong2(t1.lo, t1.hi);
       out[2 * c + 1] = make_ulonglong2(t2.lo, t2.hi);
       a.tileE[tile * NCH + c] = E;
-      if (E != GV_EMPTY) atomicMax(&a.st->E[c], E);
     }
   }
   if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);

@@ -1,6 +1,6 @@
-// gv_reduce.cu -- combination of all events of an iteration and the serial
-// grid optimisation (Section 2.1: "the grid optimization is not parallelized,
-// so that all the results can be combined").
+// gv_reduce.cu -- combination of all events of an iteration and the grid
+// optimisation (Section 2.1: the grid optimisation is serial so that it can
+// use the results of all events).
 //
 // gv_reduce_kernel sums the 128-bit tile partials exactly.  Its grid is
 // (accumulator blocks of 32) x (tile ranges): each CTA owns 32 accumulators
@@ -8,23 +8,24 @@
 // are combined in shared memory, and the CTA adds the result to the
 // iteration's accumulators with one fire-and-forget integer atomic per limb
 // (a handful of CTAs per cache line, so no line becomes a hot spot).  Every
-// tile partial is first aligned to the iteration's scale (the max over tiles,
-// formed by the fill kernel with an order-free atomicMax).  Integer addition
-// is associative: the totals do not depend on the grid or on timing.  The
-// last CTA to finish (a ticket, no waiting) rounds the totals to FP64 once,
-// records I_k and sigma_k, combines the stage and forms the per-axis totals
-// of the smoothed bin sums (accumulated exactly by the reduce CTAs).
+// tile partial is first aligned to its slot's scale (channel sums: the max
+// over tiles; bin sums: the bin's own exponent -- both formed by the fill
+// kernel with order-free atomicMax).  Integer addition is associative: the
+// totals do not depend on the grid or on timing.
 //
-// gv_refine_kernel then refines the grid (Lepage's VEGAS, cited in Section
-// 2.1): smoothing, normalisation, compression ((1-rho)/(-ln rho))^alpha and
-// redistribution into N equal shares.  Smoothing is done exactly on the bin
-// integers; the compression (an FP64 log per bin) is spread over CTAs; the
-// last one places the new edges from shared memory.
+// Tickets instead of waiting: each CTA counts itself, after publishing its
+// share, on every axis its bins belong to and on the whole grid.  The CTA
+// that completes an axis refines that axis at once (Lepage's VEGAS, cited in
+// Section 2.1: smoothing on the exact bin integers, normalisation,
+// compression ((1-rho)/(-ln rho))^alpha, redistribution into N equal shares),
+// so the axes are refined in parallel by different CTAs while others still
+// reduce; the last CTA overall rounds the channel sums to FP64, records I_k
+// and sigma_k and combines the stage.  No CTA ever waits for another.
 //
 // On this chip an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles
 // and the FP64 library log takes ~2000 cycles: the serial code here keeps its
-// FP64 chains short (reciprocals passed in, a table-driven log, one warp per
-// independent task).
+// FP64 chains short (reciprocals passed in, a table-driven log, one thread
+// per bin).
 #include <algorithm>
 
 #include "gv_integrands.cuh"
@@ -73,40 +74,23 @@ __device__ __forceinline__ u192 shl192(u192 v, int s) {
   return v;
 }
 
-// Accumulators: three 64-bit limbs holding bits [0,43), [43,86) and [86,...)
-// (the last one signed), 32 bytes apart.  The two low limbs have 21 bits of
-// headroom (up to 2^21 adds), so no carry travels between limbs until the
-// final conversion and no atomic waits for a returned value.
-#define GV_LIMB 43
-#define GV_LIMB_MASK ((1ull << GV_LIMB) - 1ull)
-#define GV_ACC_STRIDE 4
-
-__device__ __forceinline__ void red_add_limbs(unsigned long long* p, const u192& v) {
-  const unsigned long long l0 = v.l0 & GV_LIMB_MASK;
-  const unsigned long long l1 = ((v.l0 >> GV_LIMB) | (v.l1 << (64 - GV_LIMB))) & GV_LIMB_MASK;
-  // bits 86.. as a signed 64-bit number (|v| < 2^149 always)
-  const unsigned long long l2 = (v.l1 >> (2 * GV_LIMB - 64)) | (v.l2 << (128 - 2 * GV_LIMB));
-  if (l0) atomicAdd(p, l0);
-  if (l1) atomicAdd(p + 1, l1);
-  if (l2) atomicAdd(p + 2, l2);
+// Slots (GvSlot: 192 bits and an exponent) are written by one thread and read
+// by CTAs that took a ticket after the writer's fence: L2 loads.
+__device__ __forceinline__ u192 slot_value(const GvSlot& s) { return {s.l0, s.l1, s.l2}; }
+__device__ __forceinline__ GvSlot load_slot(const GvSlot* p) {
+  const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2*>(p) + 1);
+  GvSlot s;
+  s.l0 = a.x;
+  s.l1 = a.y;
+  s.l2 = b.x;
+  s.e = (int)(unsigned)(b.y & 0xFFFFFFFFull);
+  s.pad = 0;
+  return s;
 }
-
-// l0 + l1 2^43 + l2 2^86 (l2 signed) as a 192-bit two's complement integer.
-__device__ __forceinline__ u192 limbs_to_u192(unsigned long long l0, unsigned long long l1,
-                                              unsigned long long l2) {
-  u192 r = {l0, 0ull, 0ull};
-  u192 a = {l1 << GV_LIMB, l1 >> (64 - GV_LIMB), 0ull};
-  add192(r, a);
-  const unsigned long long ext = (unsigned long long)((long long)l2 >> 63);
-  u192 b = {0ull, l2 << (2 * GV_LIMB - 64),
-            (l2 >> (128 - 2 * GV_LIMB)) | (ext << (2 * GV_LIMB - 64))};
-  add192(r, b);
-  return r;
-}
-
-__device__ __forceinline__ u192 load_acc(const unsigned long long* acc, int k) {
-  const unsigned long long* p = acc + GV_ACC_STRIDE * k;
-  return limbs_to_u192(__ldcg(p), __ldcg(p + 1), __ldcg(p + 2));
+__device__ __forceinline__ void store_slot(GvSlot* p, const u192& v, int e) {
+  reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(v.l0, v.l1);
+  reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(v.l2, (unsigned long long)(unsigned)e);
 }
 
 // value * 2^q rounded to nearest-even, assembled with integer operations only
@@ -180,13 +164,9 @@ __device__ double u192_to_double(u192 v, int q) {
 // Stored bin exponent (GV_BINE_OFF-offset, 0 = empty) -> q of u192_to_double.
 __device__ __forceinline__ int bin_q(int g) { return 2 * (g - GV_BINE_OFF) - GV_BIN_FB; }
 
-// Max of the stored bin exponents of one axis, by one warp (all lanes get it).
-__device__ __forceinline__ int axis_bin_exp(const int* binE, int N) {
-  int g = 0;
-  for (int i = threadIdx.x & 31; i < N; i += 32) g = max(g, __ldcg(binE + i));
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) g = max(g, __shfl_xor_sync(0xffffffffu, g, m));
-  return g;
+// Barrier of a group of nthr threads (a multiple of 32); id 0 is the whole CTA.
+__device__ __forceinline__ void gv_bar(int id, int nthr) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -307,49 +287,22 @@ __device__ void combine_stage_warp(const double* per_iter, int stride, int m, do
   }
 }
 
-// Integer weight c_j of bin j in 6 x (sum of the smoothed bin sums of an axis):
-// the end entries (d_0+d_1)/2, (d_{N-2}+d_{N-1})/2 weigh 3, the inner entries
-// (d_{i-1}+d_i+d_{i+1})/3 weigh 2.
-__device__ __forceinline__ int smooth_weight(int j, int N) {
-  int c = 0;
-  for (int i = max(0, j - 1); i <= min(N - 1, j + 1); ++i) {
-    const bool inside = (i == 0) ? (j <= 1) : (i == N - 1) ? (j >= N - 2) : true;
-    if (inside) c += (i == 0 || i == N - 1) ? 3 : 2;
-  }
-  return c;
-}
-
-__device__ __forceinline__ u192 mul192_small(u192 v, int c) {
-  u192 r = {0ull, 0ull, 0ull};
-  for (int q = 0; q < c; ++q) add192(r, v);
-  return r;
-}
-
-// The last reduce CTA (256 threads).
-__device__ void finalize_iteration(const GvReduceArgs& a) {
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, wid = tid >> 5;
+// The iteration's finalisation, by the threads [0, nthr) of a group (local
+// thread index tid, barrier id bar): the iteration record, the stage's
+// combination and the per-iteration state.
+__device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int bar) {
+  const int lane = tid & 31, wid = tid >> 5;
+  (void)nthr;
+  (void)bar;
   GvState* st = a.st;
-  const int d = a.ndim;
-  // channel sums (and the bin sums unless the refine kernel converts them):
-  // each rounded once to FP64
-  const int nconv = a.refine_follows ? 2 * a.nch : a.nacc;
-  for (int k = tid; k < nconv; k += nthr) {
-    if (k < 2 * a.nch) {
-      const int Eg = st->E[k >> 1];
-      a.sums[k] =
-          Eg != GV_EMPTY ? u192_to_double(load_acc(a.acc, k), ((k & 1) + 1) * Eg - GV_FB) : 0.0;
-    } else {  // a bin, at its own scale
-      const int g = __ldcg(a.binE + (k - 2 * a.nch));
-      a.sums[k] = g ? u192_to_double(load_acc(a.acc, k), bin_q(g)) : 0.0;
-    }
-  }
-  __syncthreads();
+  // the sums, each rounded once to FP64 by the CTA that completed its block
   if (wid == 0) {
     // warp 0: the iteration record (one lane per channel) and the stage
     const int stride = a.mode ? 2 + 2 * GV_NGRAD : 2;
     if (lane < a.nch) {
       double* rec = a.per_iter + (size_t)a.k * stride + 2 * lane;
-      mean_sigma(a.sums[2 * lane], a.sums[2 * lane + 1], a.inv_c, a.inv_cm1, &rec[0], &rec[1]);
+      mean_sigma(__ldcg(a.sums + 2 * lane), __ldcg(a.sums + 2 * lane + 1), a.inv_c, a.inv_cm1,
+                 &rec[0], &rec[1]);
     }
     __syncwarp();
     if (a.last) combine_stage_warp(a.per_iter, stride, a.k + 1, a.inv_m1, st, a.mode != 0);
@@ -359,197 +312,39 @@ __device__ void finalize_iteration(const GvReduceArgs& a) {
       if (a.k == 0) st->status = 0;
       st->nonfinite_iter = 0ull;
     }
-  } else if (a.has_bins) {
-    // per-axis totals (slots after the bins, at the axis' largest bin scale,
-    // summed by the reduce CTAs): one rounding, stored as 1/(6 x total), 0
-    // when the axis is empty.  One warp per axis.
-    for (int ax = wid - 1; ax < d; ax += (nthr >> 5) - 1) {
-      const int g = axis_bin_exp(a.binE + ax * a.nbins, a.nbins);
-      if (lane == 0) {
-        double inv = 0.0;
-        if (g) {
-          const double t6 = u192_to_double(load_acc(a.acc, a.nacc + ax), bin_q(g));
-          inv = t6 > 0.0 ? __drcp_rn(t6) : 0.0;
-        }
-        a.inv_total[ax] = inv;
-      }
-    }
   }
-  __syncthreads();  // every read of the accumulators here is done
-  const int nslots = a.has_bins ? a.nacc + d : a.nacc;
-  for (int k = tid; k < GV_ACC_STRIDE * nslots; k += nthr) {
-    const int slot = k / GV_ACC_STRIDE;
-    const bool bin_slot = a.has_bins && slot >= 2 * a.nch && slot < a.nacc;
-    if (!(bin_slot && a.refine_follows)) a.acc[k] = 0ull;
-  }
-  if (a.has_bins && !a.refine_follows)
-    for (int k = tid; k < d * a.nbins; k += nthr) a.binE[k] = 0;
-  if (tid == 0) {
-    st->E0_prev = st->E[0];
-    for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
-    st->done = 0;
-    st->it = st->it + 1ull;
-  }
-}
-
-#define GV_RED_TILES_PER_LOAD 8
-
-// One reduce CTA (256 threads) of one integration: accumulator block bx, tile
-// range by, of nblk CTAs in total for that integration.
-__device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
-                               u192 (*s_part)[32], int* is_last_s) {
-  int& is_last = *is_last_s;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = bx * 32 + lane;
-  const int t0 = by * a.tiles_per_cta;
-  const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
-  u192 r = {0ull, 0ull, 0ull};
-  gv_wait_prior_grid();
-  const bool bin_slot = a.has_bins && k >= 2 * a.nch && k < a.nacc;
-  const int gb = bin_slot ? __ldcg(a.binE + (k - 2 * a.nch)) : 0;
-  if (bin_slot) {
-    // Q 2^(2 F_tb - GV_BIN_QBITS) aligned to 2^(2 G_b - GV_BIN_FB)
-    if (gb) {
-      constexpr int G = GV_RED_TILES_PER_LOAD;
-      for (int tb = t0 + wid; tb < t1; tb += 8 * G) {
-        ulonglong2 v[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int t = tb + 8 * g;
-          v[g] = t < t1 ? a.part[(size_t)t * a.nacc + k] : make_ulonglong2(0ull, 0ull);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int f = (int)(v[g].y >> 32);
-          if (f) {
-            const u192 x = {v[g].x, v[g].y & 0xFFFFFFFFull, 0ull};
-            const int sh = 2 * (gb - f) - GV_BIN_XBITS;
-            add192(r, sh < 0 ? shl192(x, -sh) : sar192(x, sh));
-          }
-        }
-      }
-    }
-  } else if (k < a.nacc) {
-    const int ch = k >> 1;
-    const int pw = (k & 1) + 1;
-    const int Eg = a.st->E[ch];
-    if (Eg != GV_EMPTY) {
-      constexpr int G = GV_RED_TILES_PER_LOAD;
-      for (int tb = t0 + wid; tb < t1; tb += 8 * G) {
-        ulonglong2 v[G];
-        int Et[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int t = tb + 8 * g;
-          if (t < t1) {
-            Et[g] = a.tileE[(size_t)t * a.nch + ch];
-            v[g] = a.part[(size_t)t * a.nacc + k];
-          } else {
-            Et[g] = GV_EMPTY;
-            v[g] = make_ulonglong2(0ull, 0ull);
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const u192 x = {v[g].x, v[g].y, (unsigned long long)((long long)v[g].y >> 63)};
-          const int sh = Et[g] == GV_EMPTY ? 192 : pw * (Eg - Et[g]);
-          if (x.l0 | x.l1) add192(r, sar192(x, sh));
-        }
-      }
-    }
-  }
-  s_part[wid][lane] = r;
-  __syncthreads();
-  if (wid == 0) {
-    u192 t = s_part[0][lane];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) add192(t, s_part[w][lane]);
-    if (k < a.nacc && (t.l0 | t.l1 | t.l2)) red_add_limbs(a.acc + GV_ACC_STRIDE * k, t);
-    if (a.has_bins) {
-      // this CTA's share of 6 x (sum of the smoothed bin sums) of each axis
-      const int N = a.nbins;
-      const int j = k - 2 * a.nch;  // bin index within [0, d*N)
-      const bool is_bin = k < a.nacc && j >= 0;
-      const u192 ct = (is_bin && gb) ? mul192_small(t, smooth_weight(j % N, N))
-                                      : u192{0ull, 0ull, 0ull};
-      const int k0 = bx * 32;
-      const int j_first = max(0, k0 - 2 * a.nch);
-      const int j_last = min(a.nacc - 1, k0 + 31) - 2 * a.nch;
-      for (int ax = j_first / N; j_last >= 0 && ax <= j_last / N; ++ax) {
-        // at the axis' largest bin scale (a fixed truncation of the small bins)
-        const int gax = axis_bin_exp(a.binE + ax * N, N);
-        u192 v = (is_bin && gb && j / N == ax) ? sar192(ct, 2 * (gax - gb))
-                                                : u192{0ull, 0ull, 0ull};
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) {
-          u192 o = {__shfl_xor_sync(0xffffffffu, v.l0, m), __shfl_xor_sync(0xffffffffu, v.l1, m),
-                    __shfl_xor_sync(0xffffffffu, v.l2, m)};
-          add192(v, o);
-        }
-        if (lane == 0 && (v.l0 | v.l1 | v.l2))
-          red_add_limbs(a.acc + GV_ACC_STRIDE * (a.nacc + ax), v);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(&a.st->done, 1) == nblk - 1) ? 1 : 0;
-  __syncthreads();
-  if (!is_last) return;
-  gv_allow_next_grid();
-  __threadfence();
-  finalize_iteration(a);
-}
-
-__global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
-  __shared__ u192 s_part[8][32];
-  __shared__ int is_last;
-  gv_reduce_task(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y, s_part, &is_last);
-}
-
-// Batched: one launch reduces many integrations; task i names the
-// integration and the block coordinates of CTA i.
-__global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs* args,
-                                                              const int4* tasks, int k, int last,
-                                                              double inv_m1) {
-  __shared__ u192 s_part[8][32];
-  __shared__ int is_last;
-  const int4 t = tasks[blockIdx.x];
-  GvReduceArgs a = args[t.x];
-  a.k = k;
-  a.last = last;
-  a.inv_m1 = inv_m1;
-  gv_reduce_task(a, t.y, t.z, t.w, s_part, &is_last);
+  if (tid == 0) st->it = st->it + 1ull;
 }
 
 // ---------------------------------------------------------------------------
-// Grid refinement.
+// Grid refinement (Lepage's VEGAS, cited in Section 2.1), one axis at a time:
+// every step of it -- smoothing, normalisation, compression, redistribution
+// -- involves one axis only, so the CTA whose reduction completes an axis
+// refines it at once, while other CTAs are still reducing.
 // ---------------------------------------------------------------------------
-// Write the edges e_src (d x (N+1)) into the grid pack with its derived tables.
-__device__ void pack_axis_tables(double* grid, const double* e_src, int d, int N, int tid,
+// Write the edges e_src (N+1 values) of axis ax into the grid pack with the
+// axis' derived tables.
+__device__ void pack_axis_tables(double* grid, const double* e_src, int ax, int d, int N, int tid,
                                  int nthr) {
   const GvGridLayout L{d, N};
-  double* e64 = grid + L.off_e64();
-  double* wd64 = grid + L.off_wd64();
-  double* jac = grid + L.off_jac();
+  double* e64 = grid + L.off_e64() + (size_t)ax * (N + 1);
+  double* wd64 = grid + L.off_wd64() + (size_t)ax * N;
+  double* jac = grid + L.off_jac() + (size_t)ax * N;
   float* w32 = reinterpret_cast<float*>(grid + L.off_f32_base());
-  float* e32 = w32 + L.w_e32();
-  float* wd32 = w32 + L.w_wd32();
-  float* jm32 = w32 + L.w_jm32();
-  int* je = reinterpret_cast<int*>(w32 + L.w_je());
-  for (int k = tid; k < d * (N + 1); k += nthr) {
-    const int a = k / (N + 1), i = k % (N + 1);
-    const size_t ie = (size_t)a * (N + 1) + i;
-    const double e = e_src[ie];
-    e64[ie] = e;
-    e32[ie] = (float)e;
+  float* e32 = w32 + L.w_e32() + (size_t)ax * (N + 1);
+  float* wd32 = w32 + L.w_wd32() + (size_t)ax * N;
+  float* jm32 = w32 + L.w_jm32() + (size_t)ax * N;
+  int* je = reinterpret_cast<int*>(w32 + L.w_je()) + (size_t)ax * N;
+  for (int i = tid; i <= N; i += nthr) {
+    const double e = e_src[i];
+    e64[i] = e;
+    e32[i] = (float)e;
     if (i < N) {
-      const double w = e_src[ie + 1] - e;
+      const double w = e_src[i + 1] - e;
       const double j = (double)N * w;
-      const size_t ib = (size_t)a * N + i;
-      wd64[ib] = w;
-      jac[ib] = j;
-      wd32[ib] = (float)w;
+      wd64[i] = w;
+      jac[i] = j;
+      wd32[i] = (float)w;
       // j = m 2^x with m in [1,2): exponent from the bits (j > 0; a subnormal
       // j is scaled into the normal range first)
       const bool sub = j < 0x1p-1000;
@@ -557,8 +352,8 @@ __device__ void pack_axis_tables(double* grid, const double* e_src, int d, int N
       const long long b = __double_as_longlong(js);
       const int x = (int)((b >> 52) & 0x7FF) - 1023;
       const double m = __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
-      jm32[ib] = (float)m;
-      je[ib] = sub ? x - 200 : x;
+      jm32[i] = (float)m;
+      je[i] = sub ? x - 200 : x;
     }
   }
 }
@@ -584,124 +379,100 @@ __device__ __forceinline__ double compress(double rho, double alpha, const doubl
   return pow(om * __drcp_rn(L), alpha);
 }
 
-#define GV_REFINE_THREADS 512
-#define GV_REFINE_BINS 32
+// Shared memory of refine_axis: r[N], slope[N], C[N+1], e[N+1], ne[N+1].
+__host__ __device__ inline size_t refine_axis_smem(int N) {
+  return sizeof(double) * (2 * (size_t)N + 3 * ((size_t)N + 1));
+}
 
-// Phase 1, every CTA: warp 0 computes the compressed value r_i of 32 bins and
-// the slope (e_{i+1}-e_i)/r_i used to place edges.  Phase 2, the last CTA
-// (ticket): per-axis prefix sums C of r (warp scan), new edges where C
-// reaches j R/N -- binary search on the bit patterns of the nonnegative
-// doubles, then e_i + (target - C_i) * slope_i -- and the tables, with r,
-// slope, C and the old edges in shared memory.
-__device__ void gv_refine_task(const GvRefineArgs& a, int bx, int nblk, double* sm,
-                               int* is_last_s, double* s_step) {
-  int& is_last = *is_last_s;
-  const int d = a.ndim, N = a.nbins, dN = d * N;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int NWARP = GV_REFINE_THREADS / 32;
-  double* gr = a.scratch;                   // [dN] r
-  double* gsl = a.scratch + dN;             // [dN] slope
-  double* ne = a.scratch + 2 * (size_t)dN;  // [d(N+1)] new edges
-  const double* e64 = a.grid;               // the pack starts with e64
-  gv_wait_prior_grid();
+// Refinement of axis ax by a group of nthr threads (local index tid, barrier
+// id bar, group number q), once every block holding the axis has rounded its
+// bin sums d_i to FP64 (the oracle's arithmetic from here on):
+//   1. 6 x the smoothed sums, s_i = 3 (d_0 + d_1) at the ends and
+//      2 (d_{i-1} + d_i + d_{i+1}) inside, and their total (a fixed-order
+//      tree), then per bin the share rho = s_i / total, the compressed value
+//      r = ((1-rho)/(-ln rho))^alpha and the slope (e_{i+1}-e_i)/r;
+//   2. one warp: the prefix sums C of r;
+//   3. per new edge: the old bin where C reaches j R/N -- binary search on
+//      the bit patterns of the nonnegative doubles -- then
+//      e_i + (target - C_i) * slope_i; e'_0 = 0 and e'_N = 1 exactly;
+//   4. the axis' tables.
+// An axis whose bins are all zero keeps its edges.
+__device__ void refine_axis(const GvReduceArgs& a, int ax, double* sm, int tid, int nthr, int bar,
+                            int q) {
+  const int N = a.nbins, lane = tid & 31, wid = tid >> 5;
+  __shared__ double s_inv[8], s_step[8];
+  double* r = sm;             // [N] 6 x smoothed sums, then compressed values
+  double* slope = r + N;      // [N] bin sums, then slopes
+  double* C = slope + N;      // [N+1]
+  double* e = C + (N + 1);    // [N+1] old edges
+  double* ne = e + (N + 1);   // [N+1] new edges
+  const double* d = a.sums + 2 * a.nch + ax * N;
+  const double* e64 = a.grid + GvGridLayout{a.ndim, N}.off_e64() + (size_t)ax * (N + 1);
+  for (int k = tid; k <= N; k += nthr) e[k] = e64[k];
+  for (int i = tid; i < N; i += nthr) slope[i] = __ldcg(d + i);
+  gv_bar(bar, nthr);
+  for (int i = tid; i < N; i += nthr)
+    r[i] = i == 0       ? 3.0 * (slope[0] + slope[1])
+           : i == N - 1 ? 3.0 * (slope[N - 2] + slope[N - 1])
+                        : 2.0 * (slope[i - 1] + slope[i] + slope[i + 1]);
+  gv_bar(bar, nthr);
   if (wid == 0) {
-    const int k = bx * GV_REFINE_BINS + lane;
-    if (k < dN) {
-      const int ax = k / N, i = k - ax * N;
-      const int base = 2 * a.nch + ax * N;  // slot of bin 0 of this axis
-      const int* G = a.binE + ax * N;
-      const u192 z = {0ull, 0ull, 0ull};
-      const int gm = i > 0 ? __ldcg(G + i - 1) : 0, gc = __ldcg(G + i),
-                gp = i < N - 1 ? __ldcg(G + i + 1) : 0;
-      const int gx = max(gm, max(gc, gp));
-      // the three bins at the largest of their scales (empty bins hold 0)
-      const u192 dc0 = load_acc(a.acc, base + i);
-      const u192 dm = gm ? sar192(load_acc(a.acc, base + i - 1), 2 * (gx - gm)) : z;
-      const u192 dc = gc ? sar192(dc0, 2 * (gx - gc)) : z;
-      const u192 dp = gp ? sar192(load_acc(a.acc, base + i + 1), 2 * (gx - gp)) : z;
-      // 6 x the smoothed sum: 3 (d_0 + d_1) at the ends,
-      // 2 (d_{i-1} + d_i + d_{i+1}) inside
-      u192 s6 = dc;
-      if (i == 0) {
-        add192(s6, dp);
-        s6 = mul192_small(s6, 3);
-      } else if (i == N - 1) {
-        add192(s6, dm);
-        s6 = mul192_small(s6, 3);
-      } else {
-        add192(s6, dm);
-        add192(s6, dp);
-        s6 = mul192_small(s6, 2);
-      }
-      a.dsum[k] = gc ? u192_to_double(dc0, bin_q(gc)) : 0.0;
-      const double it = a.inv_total[ax];
-      double rv = 0.0, sl = 0.0;
-      if (it > 0.0 && gx) {
-        rv = compress(u192_to_double(s6, bin_q(gx)) * it, a.alpha, a.logtab);
-        if (rv > 0.0)
-          sl = (e64[ax * (N + 1) + i + 1] - e64[ax * (N + 1) + i]) * __drcp_rn(rv);
-      }
-      gr[k] = rv;
-      gsl[k] = sl;
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(&a.st->done_refine, 1) == nblk - 1) ? 1 : 0;
-  __syncthreads();
-  if (!is_last) return;
-  gv_allow_next_grid();
-  __threadfence();
-  // every phase-1 CTA has read the bin slots: reset them for the next iteration
-  for (int k = tid; k < GV_ACC_STRIDE * dN; k += GV_REFINE_THREADS)
-    a.acc[GV_ACC_STRIDE * 2 * a.nch + k] = 0ull;
-  for (int k = tid; k < dN; k += GV_REFINE_THREADS) a.binE[k] = 0;
-  double* r = sm;                 // [dN]
-  double* slope = r + dN;         // [dN]
-  double* cum = slope + dN;       // [d(N+1)]
-  double* e = cum + d * (N + 1);  // [d(N+1)] old edges
-  for (int k = tid; k < dN; k += GV_REFINE_THREADS) {
-    r[k] = __ldcg(gr + k);
-    slope[k] = __ldcg(gsl + k);
-  }
-  for (int k = tid; k < d * (N + 1); k += GV_REFINE_THREADS) e[k] = e64[k];
-  __syncthreads();
-  for (int ax = wid; ax < d; ax += NWARP) {
-    const double* ra = r + ax * N;
-    double* ca = cum + ax * (N + 1);
+    // the total in an order fixed by N alone (whatever the group's size):
+    // 32 consecutive chunks in order, then a fixed butterfly
     const int chunk = (N + 31) / 32;
     const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
-    double local = 0.0;
-    for (int i = i0; i < i1; ++i) local += ra[i];
-    double incl = local;
+    double part = 0.0;
+    for (int i = i0; i < i1; ++i) part += r[i];
 #pragma unroll
-    for (int m = 1; m < 32; m <<= 1) {
-      const double o = __shfl_up_sync(0xffffffffu, incl, m);
-      if (lane >= m) incl += o;
-    }
-    double run = incl - local;  // exclusive prefix of this lane's chunk
-    if (lane == 0) ca[0] = 0.0;
-    for (int i = i0; i < i1; ++i) {
-      run += ra[i];
-      ca[i + 1] = run;
-    }
-    __syncwarp();
-    if (lane == 0) s_step[ax] = ca[N] * a.inv_nbins;
+    for (int m = 16; m > 0; m >>= 1) part += __shfl_xor_sync(0xffffffffu, part, m);
+    if (lane == 0) s_inv[q] = part > 0.0 ? __drcp_rn(part) : 0.0;
   }
-  __syncthreads();
-  for (int kk = tid; kk < d * (N + 1); kk += GV_REFINE_THREADS) {
-    const int ax = kk / (N + 1), j = kk % (N + 1);
-    double v = e[kk];
-    if (a.inv_total[ax] > 0.0) {
+  gv_bar(bar, nthr);
+  const double inv = s_inv[q];
+  if (inv > 0.0) {
+    for (int i = tid; i < N; i += nthr) {
+      double rv = 0.0, sl = 0.0;
+      const double s6 = r[i];
+      if (s6 > 0.0) {
+        rv = compress(s6 * inv, a.alpha, a.logtab);
+        if (rv > 0.0) sl = (e[i + 1] - e[i]) * __drcp_rn(rv);
+      }
+      r[i] = rv;
+      slope[i] = sl;
+    }
+    gv_bar(bar, nthr);
+    if (wid == 0) {
+      const int chunk = (N + 31) / 32;
+      const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
+      double local = 0.0;
+      for (int i = i0; i < i1; ++i) local += r[i];
+      double incl = local;
+#pragma unroll
+      for (int m = 1; m < 32; m <<= 1) {
+        const double o = __shfl_up_sync(0xffffffffu, incl, m);
+        if (lane >= m) incl += o;
+      }
+      double run = incl - local;  // exclusive prefix of this lane's chunk
+      if (lane == 0) C[0] = 0.0;
+      for (int i = i0; i < i1; ++i) {
+        run += r[i];
+        C[i + 1] = run;
+      }
+      __syncwarp();
+      if (lane == 0) s_step[q] = C[N] * a.inv_nbins;
+    }
+    gv_bar(bar, nthr);
+    const double step = s_step[q];
+    const long long* Cb = reinterpret_cast<const long long*>(C);
+    for (int j = tid; j <= N; j += nthr) {
+      double v;
       if (j == 0) {
         v = 0.0;
       } else if (j == N) {
         v = 1.0;
       } else {
-        const double* C = cum + ax * (N + 1);
-        const double target = s_step[ax] * j;
+        const double target = step * j;
         const long long tb = __double_as_longlong(target);
-        const long long* Cb = reinterpret_cast<const long long*>(C);
         int lo = 0, hi = N - 1;  // first bin i with C[i+1] > target (N-1 if none)
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
@@ -710,31 +481,224 @@ __device__ void gv_refine_task(const GvRefineArgs& a, int bx, int nblk, double* 
           else
             lo = mid + 1;
         }
-        v = fma(target - C[lo], slope[ax * N + lo], e[ax * (N + 1) + lo]);
+        v = fma(target - C[lo], slope[lo], e[lo]);
+      }
+      ne[j] = v;
+    }
+  } else {
+    for (int j = tid; j <= N; j += nthr) ne[j] = e[j];
+  }
+  gv_bar(bar, nthr);
+  pack_axis_tables(a.grid, ne, ax, a.ndim, N, tid, nthr);
+}
+
+// Axes that one block of 32 slots can touch, and the dynamic shared memory
+// the reduce kernels need to refine that many axes side by side.
+__host__ __device__ inline int gv_axes_per_block(int N) {
+  const int k = (31 + N - 1) / N + 1;
+  return k < 7 ? k : 7;
+}
+
+#define GV_RED_TILES_PER_LOAD 8
+
+// A tile partial of slot k aligned to exponent em (>= its own exponent e).
+// Channel slots: 128-bit two's complement at 2^(pw e - GV_FB); bin slots:
+// Q (< 2^67) at 2^(2 (e - GV_BINE_OFF) - GV_BIN_QBITS), with GV_BIN_XBITS
+// more low bits in the sums.
+__device__ __forceinline__ u192 align_tile(ulonglong2 v, int e, int em, bool bin, int pw) {
+  if (bin) {
+    const u192 x = {v.x, v.y & 0xFFFFFFFFull, 0ull};
+    const int sh = 2 * (em - e) - GV_BIN_XBITS;
+    return sh < 0 ? shl192(x, -sh) : sar192(x, sh);
+  }
+  const u192 x = {v.x, v.y, (unsigned long long)((long long)v.y >> 63)};
+  return sar192(x, pw * (em - e));
+}
+
+// One reduce CTA (256 threads) of one integration: slot block bx (32 slots,
+// one per lane), tile range by, of nblk CTAs in total for that integration.
+//   A. every CTA: the largest exponent of each slot over its tiles, then the
+//      tiles' partials aligned to it and summed -- the CTA's sums, published
+//      with that exponent (no atomics);
+//   B. the CTA that completes a slot block (ticket): the block's sums over all
+//      tile ranges at their largest exponent, each rounded once to FP64;
+//   C. the CTA whose block completes an axis (second ticket) refines the
+//      axis; the one whose block completes the iteration finalises it.
+// Integer sums of values aligned by rules that depend only on the data:
+// nothing here depends on the launch shape or on timing.
+__device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
+                               u192 (*s_part)[32], int* s_emax, int* s_flags, int* s_won,
+                               double* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = bx * 32 + lane;
+  const int gx = (a.nacc + 31) / 32, gy = nblk / gx;
+  const int t0 = by * a.tiles_per_cta;
+  const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
+  const bool bin = a.has_bins && k >= 2 * a.nch;
+  const int pw = bin ? 2 : (k & 1) + 1;
+  const int empty = bin ? 0 : GV_EMPTY;
+  const int ch = k >> 1;
+  constexpr int G = GV_RED_TILES_PER_LOAD;
+  gv_wait_prior_grid();
+
+  // ---- A: this CTA's tiles
+  const bool cached = t1 - t0 <= 8 * G;  // every tile of a lane fits in registers
+  ulonglong2 v[G];
+  int et[G];
+  int em = empty;
+  if (k < a.nacc) {
+    if (cached) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int t = t0 + wid + 8 * g;
+        v[g] = make_ulonglong2(0ull, 0ull);
+        et[g] = empty;
+        if (t < t1) {
+          v[g] = a.part[(size_t)t * a.nacc + k];
+          et[g] = bin ? (int)(v[g].y >> 32) : a.tileE[(size_t)t * a.nch + ch];
+        }
+        em = max(em, et[g]);
+      }
+    } else {
+      for (int t = t0 + wid; t < t1; t += 8)
+        em = max(em, bin ? (int)(__ldcg(&a.part[(size_t)t * a.nacc + k].y) >> 32)
+                         : a.tileE[(size_t)t * a.nch + ch]);
+    }
+  }
+  s_emax[wid * 32 + lane] = em;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < 8; ++w) em = max(em, s_emax[w * 32 + lane]);
+  u192 r = {0ull, 0ull, 0ull};
+  if (k < a.nacc && em != empty) {
+    if (cached) {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (et[g] != empty && (v[g].x | v[g].y)) add192(r, align_tile(v[g], et[g], em, bin, pw));
+    } else {
+      for (int t = t0 + wid; t < t1; t += 8) {
+        const ulonglong2 x = a.part[(size_t)t * a.nacc + k];
+        const int e = bin ? (int)(x.y >> 32) : a.tileE[(size_t)t * a.nch + ch];
+        if (e != empty && (x.x | x.y)) add192(r, align_tile(x, e, em, bin, pw));
       }
     }
-    ne[kk] = v;
+  }
+  s_part[wid][lane] = r;
+  __syncthreads();
+  if (wid == 0) {
+    u192 t = s_part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) add192(t, s_part[w][lane]);
+    if (k < a.nacc) store_slot(a.cpart + (size_t)by * (32 * gx) + k, t, em);
+    __threadfence();
   }
   __syncthreads();
-  pack_axis_tables(a.grid, ne, d, N, tid, GV_REFINE_THREADS);
-  if (tid == 0) a.st->done_refine = 0;
+  if (threadIdx.x == 0)
+    s_flags[0] = atomicAdd(a.tickets + gv_ticket_group(bx), 1) == gy - 1 ? 1 : 0;
+  __syncthreads();
+  if (!s_flags[0]) return;
+
+  // ---- B: this CTA completes slot block bx
+  __threadfence();  // the other CTAs' sums, published before their tickets
+  if (threadIdx.x == 0) a.tickets[gv_ticket_group(bx)] = 0;
+  em = empty;
+  if (k < a.nacc)
+    for (int y = wid; y < gy; y += 8)
+      em = max(em, __ldcg(&a.cpart[(size_t)y * (32 * gx) + k].e));
+  s_emax[wid * 32 + lane] = em;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < 8; ++w) em = max(em, s_emax[w * 32 + lane]);
+  r = {0ull, 0ull, 0ull};
+  if (k < a.nacc && em != empty)
+    for (int y = wid; y < gy; y += 8) {
+      const GvSlot c = load_slot(a.cpart + (size_t)y * (32 * gx) + k);
+      if (c.e != empty) add192(r, sar192(slot_value(c), pw * (em - c.e)));
+    }
+  s_part[wid][lane] = r;
+  __syncthreads();
+  const int N = a.nbins;
+  const int j_first = max(0, bx * 32 - 2 * a.nch);
+  const int j_last = min(a.nacc - 1, bx * 32 + 31) - 2 * a.nch;
+  if (wid == 0) {
+    u192 t = s_part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) add192(t, s_part[w][lane]);
+    // the slot's sum over all events, rounded once to FP64
+    if (k < a.nacc)
+      a.sums[k] = em == empty ? 0.0
+                              : u192_to_double(t, bin ? bin_q(em) : pw * em - GV_FB);
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // second tickets: the block on each of its axes, and on the iteration
+    int n_won = 0, last = 0;
+    if (a.has_bins && a.refine_follows)
+      for (int ax = j_first / N; j_last >= 0 && ax <= j_last / N; ++ax) {
+        // slot blocks holding bins of axis ax
+        const int x_lo = (2 * a.nch + ax * N) / 32, x_hi = (2 * a.nch + (ax + 1) * N - 1) / 32;
+        int* tk = a.tickets + gv_ticket_axis(a.nacc, ax);
+        if (atomicAdd(tk, 1) == x_hi - x_lo) {
+          *tk = 0;
+          s_won[n_won++] = ax;
+        }
+      }
+    int* tk = a.tickets + gv_ticket_done(a.nacc);
+    if (atomicAdd(tk, 1) == gx - 1) {
+      *tk = 0;
+      last = 1;
+    }
+    s_flags[1] = n_won;
+    s_flags[2] = last;
+  }
+  __syncthreads();
+  const int n_won = s_flags[1], is_last = s_flags[2];
+  if (n_won == 0 && !is_last) return;
+
+  // ---- C
+  __threadfence();  // the other blocks' sums, published before their tickets
+  if (is_last) gv_allow_next_grid();
+  // the won axes and the finalisation side by side on groups of warps: the
+  // finalisation takes warp 7 (all warps if no axis was won), the axes the
+  // other warps, min(n_won, 7) groups, each with its own barrier and shared
+  // memory
+  if (is_last && (n_won == 0 || wid == 7)) {
+    const int nw = n_won == 0 ? 8 : 1, w0 = 8 - nw;
+    finalize_iteration(a, threadIdx.x - 32 * w0, 32 * nw, 1);
+  } else if (n_won > 0) {
+    const int ng = min(n_won, 7), wpg = (is_last ? 7 : 8) / ng, q = wid / wpg;
+    if (q < ng) {
+      const int per = (int)(refine_axis_smem(a.nbins) / sizeof(double));
+      for (int it = q; it < n_won; it += ng)
+        refine_axis(a, s_won[it], sm + (size_t)q * per, threadIdx.x - 32 * wpg * q, 32 * wpg,
+                    2 + q, q);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_kernel(const GvRefineArgs a) {
+__global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int is_last;
-  __shared__ double s_step[GV_MAXD];
-  gv_refine_task(a, blockIdx.x, gridDim.x, sm, &is_last, s_step);
+  __shared__ u192 s_part[8][32];
+  __shared__ int s_emax[256], s_flags[4], s_won[GV_MAXD];
+  gv_reduce_task(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y, s_part, s_emax, s_flags,
+                 s_won, sm);
 }
 
-__global__ void __launch_bounds__(GV_REFINE_THREADS) gv_refine_batch_kernel(
-    const GvRefineArgs* args, const int4* tasks) {
+// Batched: one launch reduces many integrations; task i names the
+// integration and the block coordinates of CTA i.
+__global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs* args,
+                                                              const int4* tasks, int k, int last,
+                                                              double inv_m1) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int is_last;
-  __shared__ double s_step[GV_MAXD];
+  __shared__ u192 s_part[8][32];
+  __shared__ int s_emax[256], s_flags[4], s_won[GV_MAXD];
   const int4 t = tasks[blockIdx.x];
-  const GvRefineArgs a = args[t.x];
-  gv_refine_task(a, t.y, t.w, sm, &is_last, s_step);
+  GvReduceArgs a = args[t.x];
+  a.k = k;
+  a.last = last;
+  a.inv_m1 = inv_m1;
+  gv_reduce_task(a, t.y, t.z, t.w, s_part, s_emax, s_flags, s_won, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -804,22 +768,19 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
   for (int i = 0; i < GV_NCONST_F32; ++i) kf[i] = (float)K[i];
 }
 
-// Reset the per-iteration invariants (at creation and after the autotuner's
+// Reset the per-iteration state (at creation and after the autotuner's
 // trial launches).
-__global__ void gv_reset_kernel(GvState* st, int nacc, unsigned long long* acc, int* binE,
-                                int dN) {
-  for (int k = threadIdx.x; k < dN; k += blockDim.x) binE[k] = 0;
-  if (threadIdx.x == 0) {
-    st->nonfinite_iter = 0ull;
-    st->done = 0;
-    st->done_refine = 0;
-    for (int c = 0; c < GV_MAXCH; ++c) st->E[c] = GV_EMPTY;
-  }
-  for (int k = threadIdx.x; k < GV_ACC_STRIDE * nacc; k += blockDim.x) acc[k] = 0ull;
+__global__ void gv_reset_kernel(GvState* st) {
+  if (threadIdx.x == 0) st->nonfinite_iter = 0ull;
 }
 
 __global__ void gv_grid_pack_kernel(double* grid, int d, int N) {
-  pack_axis_tables(grid, grid, d, N, threadIdx.x, blockDim.x);
+  // in place: each axis reads its own edges before writing them back unchanged
+  for (int ax = 0; ax < d; ++ax) {
+    pack_axis_tables(grid, grid + GvGridLayout{d, N}.off_e64() + (size_t)ax * (N + 1), ax, d, N,
+                     threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
 }
 
 __global__ void gv_rng_words_kernel(unsigned long long seed, uint32_t it, uint32_t batch,
@@ -832,9 +793,7 @@ __global__ void gv_rng_words_kernel(unsigned long long seed, uint32_t it, uint32
 }
 
 namespace gv {
-size_t refine_smem_bytes(int d, int N) {
-  return sizeof(double) * (2 * (size_t)d * N + 2 * (size_t)d * (N + 1));
-}
+size_t reduce_smem_bytes(int N) { return gv_axes_per_block(N) * refine_axis_smem(N); }
 
 // Reduce grid: 32 accumulators per CTA; at most 64 tile ranges.
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy) {
@@ -844,54 +803,35 @@ void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy) {
   *gy = (n_tiles + tpc - 1) / tpc;
 }
 
-cudaError_t launch_reduce(const GvReduceArgs& a, cudaStream_t s, bool pdl) {
+static cudaError_t allow_smem(const void* k, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl) {
   int tpc, gx, gy;
   reduce_grid(a.n_tiles, a.nacc, &tpc, &gx, &gy);
   if (tpc != a.tiles_per_cta) return cudaErrorInvalidValue;
-  return gv_launch(gv_reduce_kernel, dim3(gx, gy), dim3(256), 0, s, pdl, a);
-}
-
-cudaError_t prepare_refine(int d, int N) {
-  const size_t smem = refine_smem_bytes(d, N);
-  if (smem > 48 * 1024)
-    return cudaFuncSetAttribute(gv_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
-  return cudaSuccess;
-}
-
-cudaError_t launch_refine(const GvRefineArgs& a, cudaStream_t s, bool pdl) {
-  const int ctas = (a.ndim * a.nbins + GV_REFINE_BINS - 1) / GV_REFINE_BINS;
-  return gv_launch(gv_refine_kernel, dim3(ctas), dim3(GV_REFINE_THREADS),
-                   refine_smem_bytes(a.ndim, a.nbins), s, pdl, a);
+  cudaError_t e = allow_smem((const void*)gv_reduce_kernel, smem);
+  if (e != cudaSuccess) return e;
+  return gv_launch(gv_reduce_kernel, dim3(gx, gy), dim3(256), smem, s, pdl, a);
 }
 
 cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
-                                int last, double inv_m1, cudaStream_t s) {
-  gv_reduce_batch_kernel<<<ntasks, 256, 0, s>>>(args, tasks, k, last, inv_m1);
+                                int last, double inv_m1, size_t smem, cudaStream_t s) {
+  cudaError_t e = allow_smem((const void*)gv_reduce_batch_kernel, smem);
+  if (e != cudaSuccess) return e;
+  gv_reduce_batch_kernel<<<ntasks, 256, smem, s>>>(args, tasks, k, last, inv_m1);
   return cudaGetLastError();
 }
-
-cudaError_t launch_refine_batch(const GvRefineArgs* args, const int4* tasks, int ntasks,
-                                size_t smem, cudaStream_t s) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(gv_refine_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  gv_refine_batch_kernel<<<ntasks, GV_REFINE_THREADS, smem, s>>>(args, tasks);
-  return cudaGetLastError();
-}
-
-int refine_ctas(int d, int N) { return (d * N + GV_REFINE_BINS - 1) / GV_REFINE_BINS; }
 
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s) {
   gv_consts_kernel<<<1, 32, 0, s>>>(integrand, params, kconst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reset(GvState* st, int nacc, unsigned long long* acc, int* binE, int dN,
-                         cudaStream_t s) {
-  gv_reset_kernel<<<1, 256, 0, s>>>(st, nacc, acc, binE, dN);
+cudaError_t launch_reset(GvState* st, cudaStream_t s) {
+  gv_reset_kernel<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 
