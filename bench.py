@@ -35,6 +35,27 @@ L2_FLUSH_BYTES = 256 << 20
 # counted as 1 each + 3 divisions counted as 1 each.
 FLOPS_PER_EVENT_FP32 = 16 + 83 + 8 + 3
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) of one fill launch of this workload, from the ncu
+# capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
+# the fill's sources are the ones captured (their SHA-256 below); otherwise the
+# traffic is reported as unknown (null).
+FILL_TRAFFIC_BYTES = 72_192
+FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy.cu", "gv_integrands.cuh",
+                "gv_common.cuh")
+FILL_SOURCES_SHA256 = "bcb2dd10b8ef7c5e5b355bf3b0b21ab8d98630e8a1f103198e29514fe5326698"
+
+
+def _fill_traffic():
+    import hashlib
+
+    h = hashlib.sha256()
+    try:
+        for f in FILL_SOURCES:
+            with open(os.path.join(ROOT, "paper_1503_06182_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return FILL_TRAFFIC_BYTES if h.hexdigest() == FILL_SOURCES_SHA256 else None
 
 
 def _fp32_peak_tflops():
@@ -260,7 +281,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": 176},
         "gpu_launches": 2 * K,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": _fill_traffic(),
                      "kernel": "gv_fill_kernel<drell_yan, float>",
                      "kernel_avg_ms": fill_avg, "reduce_refine_avg_ms": kavg[1],
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
