@@ -324,6 +324,50 @@ __device__ __forceinline__ unsigned long long gv_square_bin(unsigned long long P
   return rs <= 64 ? ((P >> (rs - 1)) + 1ull) >> 1 : 0ull;
 }
 
+// The same roundings as gv_fixed_dec / gv_square_fixed_dec (half up, bit for
+// bit), specialised to the shifts that occur in a tile for normal x (|x| <
+// 2^E, so the mantissa shift of x is at most GV_FB - 53 and that of x^2 at
+// least 106 - GV_FB; subnormal x take the general routine), on 64-bit
+// pieces.  round(v 2^-r) = ((v >> (r-1)) + 1) >> 1.
+__device__ __forceinline__ u128 gv_fixed_tile(const GvDecoded& d, int E) {
+  const int s = d.e2 - E + GV_FB;  // <= GV_FB - 53 unless x is subnormal
+  if (s > GV_FB - 53) return gv_fixed_dec(d, E);
+  u128 v;
+  if (s > 0) {
+    v.lo = d.m << s;
+    v.hi = d.m >> (64 - s);
+  } else if (s == 0) {
+    v.lo = d.m;
+    v.hi = 0ull;
+  } else {
+    const int r = -s;
+    v.lo = r <= 54 ? ((d.m >> (r - 1)) + 1ull) >> 1 : 0ull;
+    v.hi = 0ull;
+  }
+  return gv_negate_if(v, d.neg);
+}
+// x^2 from its exact 128-bit mantissa square (hi = floor(m^2 2^-64) taken
+// from P = floor(m^2 2^-42), see gv_square_hi; lo = m^2 mod 2^64).
+__device__ __forceinline__ u128 gv_square_tile(const GvDecoded& d, unsigned long long P, int E) {
+  const int k = 2 * E - 2 * d.e2 - GV_FB - 1;  // r - 1 >= 105 - GV_FB unless x is subnormal
+  if (k < 105 - GV_FB) return gv_square_fixed_dec(d, E);
+  const unsigned long long hi = P >> 22, lo = d.m * d.m;
+  u128 t;
+  if (k < 64) {
+    t.lo = (lo >> k) | (hi << (64 - k));
+    t.hi = hi >> k;
+  } else {
+    t.lo = k < 128 ? hi >> (k - 64) : 0ull;
+    t.hi = 0ull;
+  }
+  // (t + 1) >> 1
+  t.lo += 1ull;
+  t.hi += t.lo == 0ull ? 1ull : 0ull;
+  t.lo = (t.lo >> 1) | (t.hi << 63);
+  t.hi >>= 1;
+  return t;
+}
+
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
   return __shfl_xor_sync(0xffffffffu, v, m);
 }

@@ -114,7 +114,15 @@ __device__ __forceinline__ double gv_weight(const GvJac<double>& J, double g) {
   return __dmul_rn(J.v, g);
 }
 __device__ __forceinline__ double gv_weight(const GvJac<float>& J, float g) {
-  return gv_ldexp_bits(gv_widen(__fmul_rn(J.m, g)), J.e);
+  const float p = __fmul_rn(J.m, g);
+  const unsigned u = __float_as_uint(p);
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const int nf = ef + 896 + J.e;  // the double's exponent field
+  if (ef != 0 && ef != 0xFF && nf > 0 && nf < 0x7FF)  // normal in and out: one assembly
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) |
+                                            ((unsigned long long)nf << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  return gv_ldexp_bits(gv_widen(p), J.e);
 }
 
 template <typename Real>
@@ -342,10 +350,10 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       if (gv_abs_bits(w[k]) != 0ull) {
         const int local = k * B + tid;
         const GvDecoded dw = gv_decode(w[k]);
-        s1 = add128(s1, gv_fixed_dec(dw, E));
-        s2 = add128(s2, gv_square_fixed_dec(dw, E));
-        // bins: w^2 at its bin's scale, a 56-bit value, as three 22-bit limbs
         const unsigned long long P = gv_square_hi(dw.m);
+        s1 = add128(s1, gv_fixed_tile(dw, E));
+        s2 = add128(s2, gv_square_tile(dw, P, E));
+        // bins: w^2 at its bin's scale, a 56-bit value, as three 22-bit limbs
         const int c = 2 * dw.e2 + 98 + 2 * GV_BINE_OFF;
 #pragma unroll
         for (int ax = 0; ax < MAXD; ++ax) {
@@ -478,8 +486,8 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       for (int k = 0; k < EPT; ++k) {
         if (gv_abs_bits(v[k][c]) != 0ull) {
           const GvDecoded dv = gv_decode(v[k][c]);
-          s1 = add128(s1, gv_fixed_dec(dv, E));
-          s2 = add128(s2, gv_square_fixed_dec(dv, E));
+          s1 = add128(s1, gv_fixed_tile(dv, E));
+          s2 = add128(s2, gv_square_tile(dv, gv_square_hi(dv.m), E));
         }
       }
     }
