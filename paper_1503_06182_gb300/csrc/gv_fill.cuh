@@ -29,7 +29,7 @@ struct GvTraits<GV_GAUSS> {
 };
 template <>
 struct GvTraits<GV_DY> {
-  static constexpr int NK = 22;
+  static constexpr int NK = DK_NK;
 };
 template <>
 struct GvTraits<GV_EE3J> {
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   const int tid = threadIdx.x;
   gv_wait_prior_grid();
   gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
-  GvConst<Real, 22> K;
+  GvConst<Real, DK_NK> K;
   K.load(a.kconst);
   const uint32_t it = (uint32_t)a.st->it;
   __syncthreads();

@@ -43,6 +43,8 @@
 #define DK_DCA1 19
 #define DK_DCA2 20
 #define DK_DCB2 21
+#define DK_LOGTAULO 22  // ln tau_lo
+#define DK_NK 23        // Drell-Yan constants
 // e+e- -> q qbar g
 #define EK_YCUT 0
 #define EK_Q 1
@@ -126,22 +128,20 @@ __device__ __forceinline__ Real gv_gauss(const Real (&x)[MAXD], int d, Real inv2
 // With GRAD the reverse sweep also returns dg/d(M_Z, Gamma_Z, sw2, a, b).
 // ---------------------------------------------------------------------------
 template <typename Real, bool GRAD>
-__device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 22>& K,
+__device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, DK_NK>& K,
                                              Real* grad) {
   using Mt = GvMath<Real>;
   const Real one = (Real)1, two = (Real)2;
-  // phase space
-  const Real tau = K[DK_TAULO] * Mt::exp(x[0] * K[DK_L]);
+  // phase space: ln tau linear in x[0]; x1,2 = sqrt(tau) e^(+-y)
+  const Real ltau = Mt::fma(x[0], K[DK_L], K[DK_LOGTAULO]);
+  const Real tau = Mt::exp(ltau);
   const Real jac_tau = tau * K[DK_L];
-  const Real ymax = (Real)(-0.5) * Mt::log(tau);
+  const Real ymax = (Real)(-0.5) * ltau;
   const Real y = Mt::fma(two, x[1], -one) * ymax;
   const Real jac_y = two * ymax;
   const Real opc = two * x[2];          // 1 + cos theta
   const Real omc = two * (one - x[2]);  // 1 - cos theta
-  const Real rt = Mt::sqrt(tau);
-  const Real ey = Mt::exp(y);
-  const Real emy = Mt::div(one, ey);
-  const Real x1 = rt * ey, x2 = rt * emy;
+  const Real x1 = Mt::exp(y - ymax), x2 = Mt::exp(-y - ymax);
   const Real omx1 = one - x1, omx2 = one - x2;
   if (!(omx1 > (Real)0) || !(omx2 > (Real)0)) {
     // parton densities vanish at x = 1
@@ -151,23 +151,26 @@ __device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 
     }
     return (Real)0;
   }
-  // momenta as light-cone components; k = sqrt(shat)/2.  The mu- transverse
-  // momentum k sin(theta) (cos phi, sin phi) enters none of the invariants of
-  // the LO matrix element, so phi is a flat direction and is not evaluated.
-  const Real k = (Real)0.5 * rt * K[DK_SQRTS];
-  const Real p1p = K[DK_SQRTS] * x1;   // parton 1: (p+, 0, 0, 0)
-  const Real p2m = K[DK_SQRTS] * x2;   // parton 2: (0, p-, 0, 0)
-  const Real p3p = k * opc * ey;       // mu-: (p+, p-, k sin(theta) cos(phi), ...)
-  const Real p3m = k * omc * emy;
+  // momenta as light-cone components (p+, p-): partons x1,2 sqrt(s)/2 (1, 0,
+  // 0, +-1); the mu- at angle theta in the dilepton frame, boosted by y:
+  // p+ = (sqrt(shat)/2)(1 + cos theta) e^y = (sqrt(s)/2) x1 (1 + cos theta),
+  // p- = (sqrt(s)/2) x2 (1 - cos theta).  Its transverse momentum enters none
+  // of the invariants of the LO matrix element, so phi is a flat direction.
+  const Real hs = (Real)0.5 * K[DK_SQRTS];
+  const Real p1p = K[DK_SQRTS] * x1;   // parton 1: (p+, 0)
+  const Real p2m = K[DK_SQRTS] * x2;   // parton 2: (0, p-)
+  const Real p3p = hs * x1 * opc;      // mu-: (p+, p-)
+  const Real p3m = hs * x2 * omc;
   const Real shat = p1p * p2m;          // 2 p1.p2
   const Real that = -p1p * p3m;         // -2 p1.p3
   const Real uhat = -p2m * p3p;         // -2 p2.p3
   const Real inv_shat = Mt::div(one, shat);
   const Real c = (that - uhat) * inv_shat;
   const Real opc2 = Mt::fma(c, c, one);
-  // parton luminosities: f_q f_qbar(x2) and f_qbar(x1) f_q(x2)
-  const Real lx = Mt::log(x1) + Mt::log(x2);
-  const Real l1x = Mt::log(omx1) + Mt::log(omx2);
+  // parton luminosities f_q(x1) f_qbar(x2) and f_qbar(x1) f_q(x2):
+  // ln(x1 x2) = ln tau, ln((1-x1)(1-x2)) in one log
+  const Real lx = ltau;
+  const Real l1x = Mt::log(omx1 * omx2);
   const Real common = K[DK_NORM] * Mt::exp(Mt::fma(K[DK_A], lx, K[DK_B] * l1x));
   const Real q1 = (omx1 * omx1) * (omx1 * omx1);
   const Real q2 = (omx2 * omx2) * (omx2 * omx2);

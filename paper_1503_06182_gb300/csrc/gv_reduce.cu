@@ -721,6 +721,7 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
     K[DK_S] = s;
     K[DK_TAULO] = tau_lo;
     K[DK_L] = log(tau_hi / tau_lo);
+    K[DK_LOGTAULO] = log(tau_lo);
     K[DK_MZ2] = MZ * MZ;
     K[DK_GM2] = (GZ * MZ) * (GZ * MZ);
     const double kappa = 1.0 / (4.0 * sw2 * (1.0 - sw2));
