@@ -107,7 +107,7 @@ struct __align__(16) GvSlot {
 };
 
 // Tickets of the reduce kernel, each on its own 128-byte line: one per slot
-// block of 32 slots, one per axis, one for the whole iteration.
+// block of 32 slots, one per axis (and one spare line).
 #define GV_TICKET_STRIDE 32
 __host__ __device__ inline int gv_ticket_group(int x) { return x * GV_TICKET_STRIDE; }
 __host__ __device__ inline int gv_ticket_axis(int nacc, int ax) {

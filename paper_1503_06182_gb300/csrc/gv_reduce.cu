@@ -13,14 +13,16 @@
 // kernel with order-free atomicMax).  Integer addition is associative: the
 // totals do not depend on the grid or on timing.
 //
-// Tickets instead of waiting: each CTA counts itself, after publishing its
-// share, on every axis its bins belong to and on the whole grid.  The CTA
-// that completes an axis refines that axis at once (Lepage's VEGAS, cited in
-// Section 2.1: smoothing on the exact bin integers, normalisation,
-// compression ((1-rho)/(-ln rho))^alpha, redistribution into N equal shares),
-// so the axes are refined in parallel by different CTAs while others still
-// reduce; the last CTA overall rounds the channel sums to FP64, records I_k
-// and sigma_k and combines the stage.  No CTA ever waits for another.
+// Tickets instead of waiting: each CTA publishes its sums and counts itself
+// on its block of 32 slots; the CTA that completes a block combines the
+// block's sums, rounds them once to FP64 and counts the block on each axis
+// its bins belong to.  The CTA whose count completes an axis refines that
+// axis at once (Lepage's VEGAS, cited in Section 2.1: smoothing,
+// normalisation, compression ((1-rho)/(-ln rho))^alpha, redistribution into
+// N equal shares), so the axes are refined in parallel by different CTAs
+// while others still reduce; the CTA that completes block 0 (the channel
+// sums) records I_k and sigma_k and combines the stage.  No CTA ever waits
+// for another.
 //
 // On this chip an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles
 // and the FP64 library log takes ~2000 cycles: the serial code here keeps its
@@ -196,7 +198,7 @@ __device__ __forceinline__ double gv_log1p_series(double r) {
   return p * r;
 }
 
-__device__ double gv_log_pos(double x, const double* __restrict__ tab) {
+__device__ __forceinline__ double gv_log_pos(double x, const double* __restrict__ tab) {
   // near 1 the reduction would cancel: r = x - 1 is exact there (Sterbenz)
   if (fabs(x - 1.0) <= 0x1p-7) return gv_log1p_series(x - 1.0);
   long long b = __double_as_longlong(x);
@@ -324,7 +326,7 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
 // ---------------------------------------------------------------------------
 // Write the edges e_src (N+1 values) of axis ax into the grid pack with the
 // axis' derived tables.
-__device__ void pack_axis_tables(double* grid, const double* e_src, int ax, int d, int N, int tid,
+__device__ __forceinline__ void pack_axis_tables(double* grid, const double* e_src, int ax, int d, int N, int tid,
                                  int nthr) {
   const GvGridLayout L{d, N};
   double* e64 = grid + L.off_e64() + (size_t)ax * (N + 1);
@@ -397,7 +399,7 @@ __host__ __device__ inline size_t refine_axis_smem(int N) {
 //      e_i + (target - C_i) * slope_i; e'_0 = 0 and e'_N = 1 exactly;
 //   4. the axis' tables.
 // An axis whose bins are all zero keeps its edges.
-__device__ void refine_axis(const GvReduceArgs& a, int ax, double* sm, int tid, int nthr, int bar,
+__device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, double* sm, int tid, int nthr, int bar,
                             int q) {
   const int N = a.nbins, lane = tid & 31, wid = tid >> 5;
   __shared__ double s_inv[8], s_step[8];
@@ -523,10 +525,11 @@ __device__ __forceinline__ u192 align_tile(ulonglong2 v, int e, int em, bool bin
 //   B. the CTA that completes a slot block (ticket): the block's sums over all
 //      tile ranges at their largest exponent, each rounded once to FP64;
 //   C. the CTA whose block completes an axis (second ticket) refines the
-//      axis; the one whose block completes the iteration finalises it.
+//      axis; the CTA that completes block 0 (the channel sums) finalises the
+//      iteration.
 // Integer sums of values aligned by rules that depend only on the data:
 // nothing here depends on the launch shape or on timing.
-__device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
+__device__ __forceinline__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
                                u192 (*s_part)[32], int* s_emax, int* s_flags, int* s_won,
                                double* sm) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -600,9 +603,20 @@ __device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
 
   // ---- B: this CTA completes slot block bx
   __threadfence();  // the other CTAs' sums, published before their tickets
+  gv_allow_next_grid();  // what is left is short: the next fill's CTAs may come in
   if (threadIdx.x == 0) a.tickets[gv_ticket_group(bx)] = 0;
+  constexpr int YC = 2;  // tile ranges per warp held in registers (gy <= 16)
+  GvSlot cs[YC];
+  const bool held = gy <= 8 * YC;
   em = empty;
-  if (k < a.nacc)
+#pragma unroll
+  for (int q = 0; q < YC; ++q) {
+    const int y = wid + 8 * q;
+    cs[q].e = empty;
+    if (held && k < a.nacc && y < gy) cs[q] = load_slot(a.cpart + (size_t)y * (32 * gx) + k);
+    em = max(em, cs[q].e);
+  }
+  if (!held && k < a.nacc)
     for (int y = wid; y < gy; y += 8)
       em = max(em, __ldcg(&a.cpart[(size_t)y * (32 * gx) + k].e));
   s_emax[wid * 32 + lane] = em;
@@ -610,11 +624,18 @@ __device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
 #pragma unroll
   for (int w = 0; w < 8; ++w) em = max(em, s_emax[w * 32 + lane]);
   r = {0ull, 0ull, 0ull};
-  if (k < a.nacc && em != empty)
-    for (int y = wid; y < gy; y += 8) {
-      const GvSlot c = load_slot(a.cpart + (size_t)y * (32 * gx) + k);
-      if (c.e != empty) add192(r, sar192(slot_value(c), pw * (em - c.e)));
+  if (k < a.nacc && em != empty) {
+    if (held) {
+#pragma unroll
+      for (int q = 0; q < YC; ++q)
+        if (cs[q].e != empty) add192(r, sar192(slot_value(cs[q]), pw * (em - cs[q].e)));
+    } else {
+      for (int y = wid; y < gy; y += 8) {
+        const GvSlot c = load_slot(a.cpart + (size_t)y * (32 * gx) + k);
+        if (c.e != empty) add192(r, sar192(slot_value(c), pw * (em - c.e)));
+      }
     }
+  }
   s_part[wid][lane] = r;
   __syncthreads();
   const int N = a.nbins;
@@ -629,45 +650,40 @@ __device__ void gv_reduce_task(const GvReduceArgs& a, int bx, int by, int nblk,
       a.sums[k] = em == empty ? 0.0
                               : u192_to_double(t, bin ? bin_q(em) : pw * em - GV_FB);
     __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // second tickets: the block on each of its axes, and on the iteration
-    int n_won = 0, last = 0;
-    if (a.has_bins && a.refine_follows)
-      for (int ax = j_first / N; j_last >= 0 && ax <= j_last / N; ++ax) {
-        // slot blocks holding bins of axis ax
-        const int x_lo = (2 * a.nch + ax * N) / 32, x_hi = (2 * a.nch + (ax + 1) * N - 1) / 32;
-        int* tk = a.tickets + gv_ticket_axis(a.nacc, ax);
-        if (atomicAdd(tk, 1) == x_hi - x_lo) {
-          *tk = 0;
-          s_won[n_won++] = ax;
-        }
+    // second tickets, one lane per axis the block touches: the block whose
+    // count completes an axis refines it
+    const int ax0 = j_first / N;
+    const int nax = (a.has_bins && a.refine_follows && j_last >= 0) ? j_last / N - ax0 + 1 : 0;
+    bool won = false;
+    if (lane < nax) {
+      const int ax = ax0 + lane;
+      const int x_lo = (2 * a.nch + ax * N) / 32, x_hi = (2 * a.nch + (ax + 1) * N - 1) / 32;
+      int* tk = a.tickets + gv_ticket_axis(a.nacc, ax);
+      if (atomicAdd(tk, 1) == x_hi - x_lo) {
+        *tk = 0;
+        won = true;
       }
-    int* tk = a.tickets + gv_ticket_done(a.nacc);
-    if (atomicAdd(tk, 1) == gx - 1) {
-      *tk = 0;
-      last = 1;
     }
-    s_flags[1] = n_won;
-    s_flags[2] = last;
+    const unsigned mask = __ballot_sync(0xffffffffu, won);
+    if (won) s_won[__popc(mask & ((1u << lane) - 1u))] = ax0 + lane;
+    if (lane == 0) s_flags[1] = __popc(mask);
   }
   __syncthreads();
-  const int n_won = s_flags[1], is_last = s_flags[2];
-  if (n_won == 0 && !is_last) return;
+  // block 0 holds the channel sums: it finalises the iteration
+  const int n_won = s_flags[1], fin = bx == 0;
+  if (n_won == 0 && !fin) return;
 
   // ---- C
-  __threadfence();  // the other blocks' sums, published before their tickets
-  if (is_last) gv_allow_next_grid();
+  if (n_won) __threadfence();  // the other blocks' sums, published before their tickets
   // the won axes and the finalisation side by side on groups of warps: the
   // finalisation takes warp 7 (all warps if no axis was won), the axes the
   // other warps, min(n_won, 7) groups, each with its own barrier and shared
   // memory
-  if (is_last && (n_won == 0 || wid == 7)) {
+  if (fin && (n_won == 0 || wid == 7)) {
     const int nw = n_won == 0 ? 8 : 1, w0 = 8 - nw;
     finalize_iteration(a, threadIdx.x - 32 * w0, 32 * nw, 1);
   } else if (n_won > 0) {
-    const int ng = min(n_won, 7), wpg = (is_last ? 7 : 8) / ng, q = wid / wpg;
+    const int ng = min(n_won, 7), wpg = (fin ? 7 : 8) / ng, q = wid / wpg;
     if (q < ng) {
       const int per = (int)(refine_axis_smem(a.nbins) / sizeof(double));
       for (int it = q; it < n_won; it += ng)
