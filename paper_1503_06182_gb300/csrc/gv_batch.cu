@@ -22,103 +22,7 @@
 #include <vector>
 
 #include "../../include/vegas.h"
-#include "gv_fill.cuh"
-
-// ---------------------------------------------------------------------------
-// Persistent fill over the work list.
-// ---------------------------------------------------------------------------
-template <typename Real, int EPT>
-__global__ void __launch_bounds__(GV_TILE / EPT)
-    gv_fill_batch_kernel(const GvFillArgs* __restrict__ args, const int* __restrict__ ig_of,
-                         const int* __restrict__ order, const long long* __restrict__ item_start,
-                         int n, long long total, unsigned long long* counter) {
-  constexpr int B = GV_TILE / EPT;
-  constexpr int NW = B / 32;
-  constexpr int MAXD = GV_MAXD;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red_u64[NW];
-  __shared__ u128 red_128[NW];
-  __shared__ long long s_item;
-  __shared__ int s_pos;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long item = (long long)atomicAdd(counter, 1ull);
-      int pos = 0;
-      if (item < total) {  // last position whose first item is <= item
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (item_start[mid] <= item)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        pos = lo;
-      }
-      s_item = item;
-      s_pos = pos;
-    }
-    __syncthreads();
-    const long long item = s_item;
-    if (item >= total) break;
-    const int pos = s_pos;
-    const int b = order[pos];
-    const long long tile = item - item_start[pos];
-    const GvFillArgs a = args[b];
-    const GvFillSmem lay(a.ndim, a.nbins, (int)sizeof(Real), true, true);
-    unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
-    for (int k = threadIdx.x; k < 4 * a.ndim * a.nbins; k += B) hist[k] = 0u;
-    if (b != cur) {
-      gv_stage_grid<Real>(a.grid, a.ndim, a.nbins, reinterpret_cast<double*>(smem + lay.jac),
-                          reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew),
-                          threadIdx.x, B);
-      cur = b;
-    }
-    const uint32_t it = (uint32_t)a.st->it;
-    __syncthreads();
-    switch (ig_of[b]) {
-      case GV_GAUSS:
-        gv_fill_tile<GV_GAUSS, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
-        break;
-      case GV_DY:
-        gv_fill_tile<GV_DY, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
-        break;
-      default:
-        gv_fill_tile<GV_EE3J, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
-        break;
-    }
-    __syncthreads();
-  }
-}
-
-template <typename Real, int EPT>
-static cudaError_t gv_fill_batch_launch(int ctas, size_t smem, cudaStream_t s,
-                                        const GvFillArgs* args, const int* ig_of,
-                                        const int* order, const long long* item_start, int n,
-                                        long long total, unsigned long long* counter) {
-  auto k = gv_fill_batch_kernel<Real, EPT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k<<<ctas, GV_TILE / EPT, smem, s>>>(args, ig_of, order, item_start, n, total, counter);
-  return cudaGetLastError();
-}
-
-template <typename Real, int EPT>
-static int gv_fill_batch_occupancy(size_t smem) {
-  auto k = gv_fill_batch_kernel<Real, EPT>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, GV_TILE / EPT, smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return blocks;
-}
+#include "gv_fill_batch.cuh"
 
 namespace {
 
@@ -215,33 +119,17 @@ namespace {
 
 cudaError_t fill_batch(vegas_batch* B, int ept) {
   const int n = B->n;
-  switch (ept * 2 + B->fp32) {
-    case 8 * 2 + 1:
-      return gv_fill_batch_launch<float, 8>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
-                                            B->d_ig, B->d_order, B->d_item_start, n,
-                                            B->total_items, B->d_counter);
-    case 4 * 2 + 1:
-      return gv_fill_batch_launch<float, 4>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
-                                            B->d_ig, B->d_order, B->d_item_start, n,
-                                            B->total_items, B->d_counter);
-    case 8 * 2 + 0:
-      return gv_fill_batch_launch<double, 8>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
-                                             B->d_ig, B->d_order, B->d_item_start, n,
-                                             B->total_items, B->d_counter);
-    case 4 * 2 + 0:
-      return gv_fill_batch_launch<double, 4>(B->fill_ctas, B->fill_smem, B->stream, B->d_fill,
-                                             B->d_ig, B->d_order, B->d_item_start, n,
-                                             B->total_items, B->d_counter);
-  }
-  return cudaErrorInvalidValue;
+  auto f = ept == 8 ? (B->fp32 ? gv::fill_batch_f8 : gv::fill_batch_d8)
+                    : (B->fp32 ? gv::fill_batch_f4 : gv::fill_batch_d4);
+  if (ept != 4 && ept != 8) return cudaErrorInvalidValue;
+  return f(B->fill_ctas, B->fill_smem, B->stream, B->d_fill, B->d_ig, B->d_order,
+           B->d_item_start, n, B->total_items, B->d_counter);
 }
 
 int occupancy(vegas_batch* B, int ept) {
   if (ept == 8)
-    return B->fp32 ? gv_fill_batch_occupancy<float, 8>(B->fill_smem)
-                   : gv_fill_batch_occupancy<double, 8>(B->fill_smem);
-  return B->fp32 ? gv_fill_batch_occupancy<float, 4>(B->fill_smem)
-                 : gv_fill_batch_occupancy<double, 4>(B->fill_smem);
+    return B->fp32 ? gv::fill_batch_occ_f8(B->fill_smem) : gv::fill_batch_occ_d8(B->fill_smem);
+  return B->fp32 ? gv::fill_batch_occ_f4(B->fill_smem) : gv::fill_batch_occ_d4(B->fill_smem);
 }
 
 int reset_all(vegas_batch* B) {

@@ -1,0 +1,127 @@
+// gv_fill_batch.cuh -- the persistent fill kernel of the batched form and its
+// launch helpers (instantiated per precision and events per thread in
+// gv_batch_{f,d}{4,8}.cu, so that they compile in parallel).
+#pragma once
+#include "gv_fill.cuh"
+
+// ---------------------------------------------------------------------------
+// Persistent fill over the work list.
+// ---------------------------------------------------------------------------
+template <typename Real, int EPT>
+__global__ void __launch_bounds__(GV_TILE / EPT)
+    gv_fill_batch_kernel(const GvFillArgs* __restrict__ args, const int* __restrict__ ig_of,
+                         const int* __restrict__ order, const long long* __restrict__ item_start,
+                         int n, long long total, unsigned long long* counter) {
+  constexpr int B = GV_TILE / EPT;
+  constexpr int NW = B / 32;
+  constexpr int MAXD = GV_MAXD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long red_u64[NW];
+  __shared__ u128 red_128[NW];
+  __shared__ long long s_item;
+  __shared__ int s_pos;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long item = (long long)atomicAdd(counter, 1ull);
+      int pos = 0;
+      if (item < total) {  // last position whose first item is <= item
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (item_start[mid] <= item)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        pos = lo;
+      }
+      s_item = item;
+      s_pos = pos;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item >= total) break;
+    const int pos = s_pos;
+    const int b = order[pos];
+    const long long tile = item - item_start[pos];
+    const GvFillArgs a = args[b];
+    const GvFillSmem lay(a.ndim, a.nbins, (int)sizeof(Real), true, true);
+    unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
+    for (int k = threadIdx.x; k < 4 * a.ndim * a.nbins; k += B) hist[k] = 0u;
+    if (b != cur) {
+      gv_stage_grid<Real>(a.grid, a.ndim, a.nbins, reinterpret_cast<double*>(smem + lay.jac),
+                          reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew),
+                          threadIdx.x, B);
+      cur = b;
+    }
+    const uint32_t it = (uint32_t)a.st->it;
+    __syncthreads();
+    switch (ig_of[b]) {
+      case GV_GAUSS:
+        gv_fill_tile<GV_GAUSS, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+      case GV_DY:
+        gv_fill_tile<GV_DY, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+      default:
+        gv_fill_tile<GV_EE3J, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+        break;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename Real, int EPT>
+inline cudaError_t gv_fill_batch_launch(int ctas, size_t smem, cudaStream_t s,
+                                        const GvFillArgs* args, const int* ig_of,
+                                        const int* order, const long long* item_start, int n,
+                                        long long total, unsigned long long* counter) {
+  auto k = gv_fill_batch_kernel<Real, EPT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<ctas, GV_TILE / EPT, smem, s>>>(args, ig_of, order, item_start, n, total, counter);
+  return cudaGetLastError();
+}
+
+template <typename Real, int EPT>
+inline int gv_fill_batch_occupancy(size_t smem) {
+  auto k = gv_fill_batch_kernel<Real, EPT>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, GV_TILE / EPT, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return blocks;
+}
+
+
+// One instantiation's entry points (defined by GV_DEFINE_FILL_BATCH).
+#define GV_DECLARE_FILL_BATCH(SUF)                                                            \
+  namespace gv {                                                                              \
+  cudaError_t fill_batch_##SUF(int ctas, size_t smem, cudaStream_t s, const GvFillArgs* args, \
+                               const int* ig_of, const int* order,                            \
+                               const long long* item_start, int n, long long total,           \
+                               unsigned long long* counter);                                  \
+  int fill_batch_occ_##SUF(size_t smem);                                                      \
+  }
+#define GV_DEFINE_FILL_BATCH(SUF, REAL, EPT)                                                  \
+  namespace gv {                                                                              \
+  cudaError_t fill_batch_##SUF(int ctas, size_t smem, cudaStream_t s, const GvFillArgs* args, \
+                               const int* ig_of, const int* order,                            \
+                               const long long* item_start, int n, long long total,           \
+                               unsigned long long* counter) {                                 \
+    return gv_fill_batch_launch<REAL, EPT>(ctas, smem, s, args, ig_of, order, item_start, n,  \
+                                           total, counter);                                   \
+  }                                                                                           \
+  int fill_batch_occ_##SUF(size_t smem) { return gv_fill_batch_occupancy<REAL, EPT>(smem); }   \
+  }
+GV_DECLARE_FILL_BATCH(f4)
+GV_DECLARE_FILL_BATCH(f8)
+GV_DECLARE_FILL_BATCH(d4)
+GV_DECLARE_FILL_BATCH(d8)

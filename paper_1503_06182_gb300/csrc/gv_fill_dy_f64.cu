@@ -1,0 +1,3 @@
+// Fill kernels of the LO Drell-Yan integrand, FP64 form.
+#include "gv_fill_inst.cuh"
+GV_DEFINE_FILL_LAUNCHER(launch_fill_dy, GV_DY, double, f64)

@@ -50,16 +50,38 @@ static cudaError_t gv_launch_eval_t(const GvFillArgs& a, uint32_t it, const long
   return cudaGetLastError();
 }
 
-#define GV_DEFINE_FILL_LAUNCHER(NAME, IG)                                                     \
+// The launchers of one integrand and one precision (one translation unit
+// each, so that they compile in parallel), and the precision dispatch.
+#define GV_DEFINE_FILL_LAUNCHER(NAME, IG, REAL, SUF)                                          \
   namespace gv {                                                                              \
+  cudaError_t NAME##_##SUF(int ept, const GvFillArgs& a, int n_tiles, size_t smem,            \
+                           cudaStream_t s, bool pdl) {                                        \
+    return gv_launch_fill_maxd<IG, REAL>(ept, a, n_tiles, smem, s, pdl);                      \
+  }                                                                                           \
+  cudaError_t NAME##_eval_##SUF(const GvFillArgs& a, uint32_t it, const long long* ev,        \
+                                long long n, double* w, int* bins, cudaStream_t s) {          \
+    return gv_launch_eval_t<IG, REAL>(a, it, ev, n, w, bins, s);                              \
+  }                                                                                           \
+  }
+
+#define GV_DEFINE_FILL_DISPATCH(NAME)                                                         \
+  namespace gv {                                                                              \
+  cudaError_t NAME##_f32(int ept, const GvFillArgs& a, int n_tiles, size_t smem,              \
+                         cudaStream_t s, bool pdl);                                           \
+  cudaError_t NAME##_f64(int ept, const GvFillArgs& a, int n_tiles, size_t smem,              \
+                         cudaStream_t s, bool pdl);                                           \
+  cudaError_t NAME##_eval_f32(const GvFillArgs& a, uint32_t it, const long long* ev,          \
+                              long long n, double* w, int* bins, cudaStream_t s);             \
+  cudaError_t NAME##_eval_f64(const GvFillArgs& a, uint32_t it, const long long* ev,          \
+                              long long n, double* w, int* bins, cudaStream_t s);             \
   cudaError_t NAME(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,          \
                    cudaStream_t s, bool pdl) {                                                \
-    return fp32 ? gv_launch_fill_maxd<IG, float>(ept, a, n_tiles, smem, s, pdl)               \
-                : gv_launch_fill_maxd<IG, double>(ept, a, n_tiles, smem, s, pdl);             \
+    return fp32 ? NAME##_f32(ept, a, n_tiles, smem, s, pdl)                                   \
+                : NAME##_f64(ept, a, n_tiles, smem, s, pdl);                                  \
   }                                                                                           \
   cudaError_t NAME##_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,    \
                           long long n, double* w, int* bins, cudaStream_t s) {                \
-    return fp32 ? gv_launch_eval_t<IG, float>(a, it, ev, n, w, bins, s)                       \
-                : gv_launch_eval_t<IG, double>(a, it, ev, n, w, bins, s);                     \
+    return fp32 ? NAME##_eval_f32(a, it, ev, n, w, bins, s)                                   \
+                : NAME##_eval_f64(a, it, ev, n, w, bins, s);                                  \
   }                                                                                           \
   }
