@@ -423,6 +423,49 @@ def run_reference(args):
     }))
 
 
+def oracle_scaling(threads=None, runs=5, warmup=(4, 10_000), production=(10, 100_000), ndim=NDIM,
+                   nbins=NBINS):
+    """The paper's thread-scaling table (Section 3.2, Tables 1-8) for the
+    oracle on this host's cores: a two-stage run (warm-up stage discarded,
+    then the production stage, as in the paper's 4 x 1,000 + 10 x 10,000
+    events, here scaled up since this integrand is far cheaper than MCFM's),
+    timed `runs` times per thread count: min / avg / max, acceleration
+    T_1 / T_n and efficiency acceleration / n.  Also checks the paper's
+    invariant: the same result for every thread count."""
+    import oracle
+    from paper_1503_06182_gb300.workloads import DY, DY_PARAMS, SEED
+
+    oracle.build()
+    maxt = oracle.get_threads()
+    if threads is None:
+        threads = sorted({1, 2, 4, 8, maxt} | ({16} if maxt >= 16 else set()))
+        threads = [t for t in threads if t <= maxt]
+    rows, ref = [], None
+    for t in threads:
+        oracle.set_threads(t)
+        times = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            w = oracle.iterate(ndim, nbins, SEED, warmup[1], warmup[0], DY, DY_PARAMS)
+            r = oracle.iterate(ndim, nbins, SEED, production[1], production[0], DY, DY_PARAMS,
+                               edges=w.edges, iteration=w.iteration)
+            times.append(time.perf_counter() - t0)
+        res = (r.integral, r.error)
+        if ref is None:
+            ref = res
+        rows.append({"threads": t, "min_s": min(times), "avg_s": sum(times) / len(times),
+                     "max_s": max(times), "integral": r.integral, "error": r.error,
+                     "identical_to_1_thread": res == ref})
+    oracle.set_threads(maxt)
+    t1 = rows[0]["avg_s"]
+    for row in rows:
+        row["acceleration"] = t1 / row["avg_s"]
+        row["efficiency"] = row["acceleration"] / row["threads"]
+    return {"workload": f"drell_yan d={ndim} N={nbins}: {warmup[0]} x {warmup[1]} warm-up + "
+                        f"{production[0]} x {production[1]} production, FP64 oracle",
+            "runs": runs, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,7 +479,12 @@ def main():
                     help="events per thread of the fill kernel (0: autotuned)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the extra workloads reported under 'forms'")
+    ap.add_argument("--oracle-scaling", action="store_true",
+                    help="print the oracle's thread-scaling table (CPU only) and exit")
     args = ap.parse_args()
+    if args.oracle_scaling:
+        print(json.dumps({"oracle_scaling": oracle_scaling()}))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -49,3 +49,16 @@ def test_max_over_ranks_single_process():
     import bench
 
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_oracle_scaling_table_shape_and_invariant():
+    """The thread-scaling table (the paper's Tables 1-8 layout) on a tiny run:
+    every thread count gives the identical result (the paper's invariant)."""
+    import bench
+
+    t = bench.oracle_scaling(threads=[1, 2], runs=2, warmup=(2, 2000), production=(2, 4000))
+    assert [r["threads"] for r in t["rows"]] == [1, 2]
+    for r in t["rows"]:
+        assert r["identical_to_1_thread"]
+        assert r["min_s"] <= r["avg_s"] <= r["max_s"]
+        assert r["acceleration"] > 0 and r["efficiency"] > 0
