@@ -39,10 +39,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 72_192
+FILL_TRAFFIC_BYTES = 71_936
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "bcb2dd10b8ef7c5e5b355bf3b0b21ab8d98630e8a1f103198e29514fe5326698"
+FILL_SOURCES_SHA256 = "3bb982ea4440c2c179eec57d0baec8413098904d36a2a1e45402551fd336ae80"
 
 
 def _fill_traffic():
