@@ -3,7 +3,8 @@
 // The paper contrasts one run whose events all feed one grid with many
 // independent runs (Section 2.1); here many *different* integrations (uneven
 // dimension, call count and integrand) share the GPU.  Each iteration is
-//   one persistent fill launch over a work list of (integration, tile) items,
+//   one persistent fill launch per dimension class (at most 4, 8, 16 axes)
+//   over a work list of (integration, tile) items,
 //   one reduce launch whose CTAs serve all integrations (task table) and
 //   refine each integration's axes as they complete,
 // and the itmx iterations are captured in one CUDA graph.  The work list
@@ -100,13 +101,19 @@ struct vegas_batch {
   int4* d_red_tasks = nullptr;
   int n_red_tasks = 0;
   int* d_ig = nullptr;
-  int* d_order = nullptr;
-  long long* d_item_start = nullptr;
-  long long total_items = 0;
-  unsigned long long* d_counter = nullptr;
+  // one work list per dimension class (members of at most 4, 8, 16 axes)
+  struct FillClass {
+    int maxd = 0, n = 0, ctas = 0;
+    long long total = 0;
+    size_t smem = 0;
+    int* d_order = nullptr;
+    long long* d_start = nullptr;
+    unsigned long long* d_counter = nullptr;
+  };
+  std::vector<FillClass> cls;
   double* logtab = nullptr;
-  size_t fill_smem = 0, reduce_smem = 0;
-  int ept = 0, fill_ctas = 0;
+  size_t reduce_smem = 0;
+  int ept = 0;
   // graph cache
   std::string graph_key;
   cudaGraphExec_t graph = nullptr;
@@ -117,19 +124,34 @@ struct vegas_batch {
 
 namespace {
 
-cudaError_t fill_batch(vegas_batch* B, int ept) {
-  const int n = B->n;
-  auto f = ept == 8 ? (B->fp32 ? gv::fill_batch_f8 : gv::fill_batch_d8)
-                    : (B->fp32 ? gv::fill_batch_f4 : gv::fill_batch_d4);
-  if (ept != 4 && ept != 8) return cudaErrorInvalidValue;
-  return f(B->fill_ctas, B->fill_smem, B->stream, B->d_fill, B->d_ig, B->d_order,
-           B->d_item_start, n, B->total_items, B->d_counter);
+// Dimension class of a member (the same classes as the single-context fill).
+int dim_class(int ig, int d) { return (d <= 4 && ig != VEGAS_EE3J) ? 4 : d <= 8 ? 8 : 16; }
+
+// The class' fill launch (its counter reset first) and its occupancy.
+cudaError_t fill_class(vegas_batch* B, const vegas_batch::FillClass& c, int ept, int ctas) {
+  cudaError_t e = cudaMemsetAsync(c.d_counter, 0, sizeof(unsigned long long), B->stream);
+  if (e != cudaSuccess) return e;
+  auto f = c.maxd == 4 ? (B->fp32 ? gv::fill_batch_f4 : gv::fill_batch_d4)
+           : c.maxd == 8 ? (B->fp32 ? gv::fill_batch_f8 : gv::fill_batch_d8)
+                         : (B->fp32 ? gv::fill_batch_f16 : gv::fill_batch_d16);
+  return f(ept, ctas, c.smem, B->stream, B->d_fill, B->d_ig, c.d_order, c.d_start, c.n, c.total,
+           c.d_counter);
 }
 
-int occupancy(vegas_batch* B, int ept) {
-  if (ept == 8)
-    return B->fp32 ? gv::fill_batch_occ_f8(B->fill_smem) : gv::fill_batch_occ_d8(B->fill_smem);
-  return B->fp32 ? gv::fill_batch_occ_f4(B->fill_smem) : gv::fill_batch_occ_d4(B->fill_smem);
+int class_occupancy(vegas_batch* B, const vegas_batch::FillClass& c, int ept) {
+  auto f = c.maxd == 4 ? (B->fp32 ? gv::fill_batch_occ_f4 : gv::fill_batch_occ_d4)
+           : c.maxd == 8 ? (B->fp32 ? gv::fill_batch_occ_f8 : gv::fill_batch_occ_d8)
+                         : (B->fp32 ? gv::fill_batch_occ_f16 : gv::fill_batch_occ_d16);
+  return std::max(1, f(ept, c.smem));
+}
+
+cudaError_t fill_batch(vegas_batch* B, int ept) {
+  if (ept != 4 && ept != 8) return cudaErrorInvalidValue;
+  for (const auto& c : B->cls) {
+    const cudaError_t e = fill_class(B, c, ept, class_occupancy(B, c, ept) * B->sm_count);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int reset_all(vegas_batch* B) {
@@ -230,8 +252,7 @@ int ensure_per_iter(vegas_batch* B, int itmx) {
 
 int enqueue_iterations(vegas_batch* B, int itmx) {
   for (int k = 0; k < itmx; ++k) {
-    GB_TRY(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), B->stream));
-    GB_TRY(fill_batch(B, B->ept));
+    for (const auto& c : B->cls) GB_TRY(fill_class(B, c, B->ept, c.ctas));
     GB_TRY(gv::launch_reduce_batch(B->d_red, B->d_red_tasks, B->n_red_tasks, k, k == itmx - 1,
                                    k > 0 ? 1.0 / (double)k : 0.0, B->reduce_smem, B->stream));
   }
@@ -249,10 +270,8 @@ int autotune_batch(vegas_batch* B) {
     float best = 1e30f;
     int best_ept = 4;
     for (int ept : {4, 8}) {
-      B->fill_ctas = std::max(1, occupancy(B, ept)) * B->sm_count;
       float t = 1e30f;
       for (int rep = 0; rep < 2; ++rep) {
-        GB_TRY(cudaMemsetAsync(B->d_counter, 0, 8, B->stream));
         GB_TRY(cudaEventRecord(e0, B->stream));
         GB_TRY(fill_batch(B, ept));
         GB_TRY(cudaEventRecord(e1, B->stream));
@@ -272,7 +291,7 @@ int autotune_batch(vegas_batch* B) {
     int st = reset_all(B);
     if (st) return st;
   }
-  B->fill_ctas = std::max(1, occupancy(B, B->ept)) * B->sm_count;
+  for (auto& c : B->cls) c.ctas = class_occupancy(B, c, B->ept) * B->sm_count;
   return VEGAS_OK;
 }
 
@@ -348,8 +367,6 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     q[6] = off;  // tickets
     off = a256(off + gv_tickets_ints(x.nacc) * 4);
   }
-  const size_t o_counter = off;
-  off = a256(off + 8);
   const size_t o_log = off;
   off = a256(off + 258 * 8);
   const size_t o_ig = off;
@@ -357,7 +374,9 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
   const size_t o_order = off;
   off = a256(off + (size_t)n * 4);
   const size_t o_start = off;
-  off = a256(off + (size_t)(n + 1) * 8);
+  off = a256(off + (size_t)(n + 3) * 8);
+  const size_t o_ccount = off;  // three class counters, one per 128-byte line
+  off = a256(off + 3 * 128);
   if (cudaMalloc(&B->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     vegas_batch_free(B);
@@ -377,11 +396,8 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     x.tileE = (int*)(base + q[8]);
     x.tickets = (int*)(base + q[6]);
   }
-  B->d_counter = (unsigned long long*)(base + o_counter);
   B->logtab = (double*)(base + o_log);
   B->d_ig = (int*)(base + o_ig);
-  B->d_order = (int*)(base + o_order);
-  B->d_item_start = (long long*)(base + o_start);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(B->dmem, 0, off, B->stream) != cudaSuccess) st = VEGAS_ECUDA;
   if (!st && cudaMemcpy(B->logtab, gv::host_log_table(), 258 * sizeof(double),
@@ -400,30 +416,49 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
         gv::launch_reset(x.st, B->stream) != cudaSuccess)
       st = VEGAS_ECUDA;
   }
-  // work list: largest expected cost first
+  // work lists, one per dimension class: largest expected cost first
   if (!st) {
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
-      return B->m[p].n_tiles * tile_cost(B->m[p].ig, B->m[p].d) >
-             B->m[q].n_tiles * tile_cost(B->m[q].ig, B->m[q].d);
-    });
-    std::vector<long long> start(n + 1, 0);
+    std::vector<int> order;
+    std::vector<long long> start;
     std::vector<int> ig(n);
-    for (int p = 0; p < n; ++p) start[p + 1] = start[p] + B->m[order[p]].n_tiles;
     for (int b = 0; b < n; ++b) ig[b] = B->m[b].ig;
-    B->total_items = start[n];
-    if (cudaMemcpy(B->d_order, order.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(B->d_item_start, start.data(), (n + 1) * 8, cudaMemcpyHostToDevice) !=
+    int pos = 0, slot = 0;
+    for (int maxd : {4, 8, 16}) {
+      std::vector<int> mem;
+      for (int b = 0; b < n; ++b)
+        if (dim_class(B->m[b].ig, B->m[b].d) == maxd) mem.push_back(b);
+      if (mem.empty()) continue;
+      std::stable_sort(mem.begin(), mem.end(), [&](int p, int q) {
+        return B->m[p].n_tiles * tile_cost(B->m[p].ig, B->m[p].d) >
+               B->m[q].n_tiles * tile_cost(B->m[q].ig, B->m[q].d);
+      });
+      vegas_batch::FillClass c;
+      c.maxd = maxd;
+      c.n = (int)mem.size();
+      c.d_order = (int*)(base + o_order) + pos;
+      c.d_start = (long long*)(base + o_start) + pos + slot;
+      c.d_counter = (unsigned long long*)(base + o_ccount + 128 * slot);
+      long long acc = 0;
+      start.push_back(0);
+      for (int b : mem) {
+        order.push_back(b);
+        acc += B->m[b].n_tiles;
+        start.push_back(acc);
+        c.smem = std::max(c.smem, GvFillSmem(B->m[b].d, nbins, B->fp32 ? 4 : 8, true, maxd > 4).total);
+      }
+      c.total = acc;
+      B->cls.push_back(c);
+      pos += c.n;
+      ++slot;
+    }
+    if (cudaMemcpy(base + o_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(base + o_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(B->d_ig, ig.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       st = VEGAS_ECUDA;
   }
   if (!st) {
-    size_t fs = 0;
-    for (const Member& x : B->m)
-      fs = std::max(fs, GvFillSmem(x.d, nbins, B->fp32 ? 4 : 8, true, true).total);
-    B->fill_smem = fs;
     B->reduce_smem = gv::reduce_smem_bytes(nbins);
     st = ensure_per_iter(B, 16);
   }

@@ -1,3 +1,3 @@
-// Batched fill kernel: double, 8 events per thread.
+// Batched fill kernels: double, at most 8 axes (4 and 8 events per thread).
 #include "gv_fill_batch.cuh"
 GV_DEFINE_FILL_BATCH(d8, double, 8)

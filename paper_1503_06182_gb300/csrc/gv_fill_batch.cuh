@@ -1,20 +1,20 @@
 // gv_fill_batch.cuh -- the persistent fill kernel of the batched form and its
-// launch helpers (instantiated per precision and events per thread in
-// gv_batch_{f,d}{4,8}.cu, so that they compile in parallel).
+// launch helpers, instantiated per precision and dimension class in
+// gv_batch_{f,d}{4,8,16}.cu (so that they compile in parallel).  Each class
+// (at most 4, 8 or 16 axes) runs its own work list with code unrolled for it.
 #pragma once
 #include "gv_fill.cuh"
 
 // ---------------------------------------------------------------------------
 // Persistent fill over the work list.
 // ---------------------------------------------------------------------------
-template <typename Real, int EPT>
+template <typename Real, int EPT, int MAXD>
 __global__ void __launch_bounds__(GV_TILE / EPT)
     gv_fill_batch_kernel(const GvFillArgs* __restrict__ args, const int* __restrict__ ig_of,
                          const int* __restrict__ order, const long long* __restrict__ item_start,
                          int n, long long total, unsigned long long* counter) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
-  constexpr int MAXD = GV_MAXD;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     const int b = order[pos];
     const long long tile = item - item_start[pos];
     const GvFillArgs a = args[b];
-    const GvFillSmem lay(a.ndim, a.nbins, (int)sizeof(Real), true, true);
+    const GvFillSmem lay(a.ndim, a.nbins, (int)sizeof(Real), true, MAXD > 4);
     unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
     for (int k = threadIdx.x; k < 4 * a.ndim * a.nbins; k += B) hist[k] = 0u;
     if (b != cur) {
@@ -64,20 +64,20 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
       case GV_DY:
         gv_fill_tile<GV_DY, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
         break;
-      default:
-        gv_fill_tile<GV_EE3J, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
+      default:  // the 3-jet integrand has at least 5 axes
+        if constexpr (MAXD > 4) gv_fill_tile<GV_EE3J, Real, EPT, MAXD>(a, tile, smem, red_u64, red_128, it);
         break;
     }
     __syncthreads();
   }
 }
 
-template <typename Real, int EPT>
+template <typename Real, int EPT, int MAXD>
 inline cudaError_t gv_fill_batch_launch(int ctas, size_t smem, cudaStream_t s,
                                         const GvFillArgs* args, const int* ig_of,
                                         const int* order, const long long* item_start, int n,
                                         long long total, unsigned long long* counter) {
-  auto k = gv_fill_batch_kernel<Real, EPT>;
+  auto k = gv_fill_batch_kernel<Real, EPT, MAXD>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -86,9 +86,9 @@ inline cudaError_t gv_fill_batch_launch(int ctas, size_t smem, cudaStream_t s,
   return cudaGetLastError();
 }
 
-template <typename Real, int EPT>
+template <typename Real, int EPT, int MAXD>
 inline int gv_fill_batch_occupancy(size_t smem) {
-  auto k = gv_fill_batch_kernel<Real, EPT>;
+  auto k = gv_fill_batch_kernel<Real, EPT, MAXD>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int blocks = 0;
@@ -101,27 +101,33 @@ inline int gv_fill_batch_occupancy(size_t smem) {
 }
 
 
-// One instantiation's entry points (defined by GV_DEFINE_FILL_BATCH).
+// One precision and dimension class' entry points (GV_DEFINE_FILL_BATCH),
+// events per thread 4 or 8.
+#define GV_FILL_BATCH_SIG(NAME)                                                               \
+  cudaError_t NAME(int ept, int ctas, size_t smem, cudaStream_t s, const GvFillArgs* args,    \
+                   const int* ig_of, const int* order, const long long* item_start, int n,    \
+                   long long total, unsigned long long* counter)
 #define GV_DECLARE_FILL_BATCH(SUF)                                                            \
   namespace gv {                                                                              \
-  cudaError_t fill_batch_##SUF(int ctas, size_t smem, cudaStream_t s, const GvFillArgs* args, \
-                               const int* ig_of, const int* order,                            \
-                               const long long* item_start, int n, long long total,           \
-                               unsigned long long* counter);                                  \
-  int fill_batch_occ_##SUF(size_t smem);                                                      \
+  GV_FILL_BATCH_SIG(fill_batch_##SUF);                                                        \
+  int fill_batch_occ_##SUF(int ept, size_t smem);                                             \
   }
-#define GV_DEFINE_FILL_BATCH(SUF, REAL, EPT)                                                  \
+#define GV_DEFINE_FILL_BATCH(SUF, REAL, MAXD)                                                 \
   namespace gv {                                                                              \
-  cudaError_t fill_batch_##SUF(int ctas, size_t smem, cudaStream_t s, const GvFillArgs* args, \
-                               const int* ig_of, const int* order,                            \
-                               const long long* item_start, int n, long long total,           \
-                               unsigned long long* counter) {                                 \
-    return gv_fill_batch_launch<REAL, EPT>(ctas, smem, s, args, ig_of, order, item_start, n,  \
-                                           total, counter);                                   \
+  GV_FILL_BATCH_SIG(fill_batch_##SUF) {                                                       \
+    return ept == 8 ? gv_fill_batch_launch<REAL, 8, MAXD>(ctas, smem, s, args, ig_of, order,  \
+                                                          item_start, n, total, counter)      \
+                    : gv_fill_batch_launch<REAL, 4, MAXD>(ctas, smem, s, args, ig_of, order,  \
+                                                          item_start, n, total, counter);     \
   }                                                                                           \
-  int fill_batch_occ_##SUF(size_t smem) { return gv_fill_batch_occupancy<REAL, EPT>(smem); }   \
+  int fill_batch_occ_##SUF(int ept, size_t smem) {                                            \
+    return ept == 8 ? gv_fill_batch_occupancy<REAL, 8, MAXD>(smem)                            \
+                    : gv_fill_batch_occupancy<REAL, 4, MAXD>(smem);                           \
+  }                                                                                           \
   }
 GV_DECLARE_FILL_BATCH(f4)
 GV_DECLARE_FILL_BATCH(f8)
+GV_DECLARE_FILL_BATCH(f16)
 GV_DECLARE_FILL_BATCH(d4)
 GV_DECLARE_FILL_BATCH(d8)
+GV_DECLARE_FILL_BATCH(d16)
