@@ -26,7 +26,7 @@ _SRC = os.environ.get("ORACLE_SRC_OVERRIDE") or _SRC
 _lock = threading.Lock()
 _lib = None
 
-GAUSS, DY, EE3J = 0, 1, 2
+GAUSS, DY, EE3J, DYNLO = 0, 1, 2, 3
 NGRAD = 5
 CHUNK = 4096
 

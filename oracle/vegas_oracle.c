@@ -47,7 +47,7 @@
 #define ORACLE_MAX_DIM 16
 #define ORACLE_NGRAD 5
 
-enum { OR_GAUSS = 0, OR_DY = 1, OR_EE3J = 2 };
+enum { OR_GAUSS = 0, OR_DY = 1, OR_EE3J = 2, OR_DYNLO = 3 };
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2 };
 
 static const double OR_PI = 3.14159265358979323846;
@@ -399,12 +399,39 @@ static double ee3j_point(const double* x, const double* prm, int nparams,
   return (xm1 * xm1 + xm2 * xm2) / (y23 * y13);
 }
 
+/* NLO-shaped stand-in for the paper's 13-dimensional NLO integral (Section
+ * 3.2): the LO Drell-Yan weight of the first four variables times, for every
+ * further axis k, the factor h(x_k) = exp(beta cos(2 pi x_k)) / I0(beta).
+ * Each factor integrates to 1 over [0,1] (I0, the modified Bessel function of
+ * order 0, is the integral of exp(beta cos(2 pi u)) by definition), so the
+ * integral is the Drell-Yan cross section for any ndim and beta; the extra
+ * axes only add work per event.  Parameters: the ten Drell-Yan ones, beta. */
+static double bessel_i0(double b) {
+  /* I0(b) = sum_k ((b/2)^k / k!)^2 */
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 200; ++k) {
+    term *= (0.25 * b * b) / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+static double dynlo_point(int ndim, const double* x, const double* prm, double* mom) {
+  double g = dy_point(x, prm, mom, NULL);
+  const double beta = prm[10];
+  const double i0 = bessel_i0(beta);
+  for (int k = 4; k < ndim; ++k) g *= exp(beta * cos(2.0 * OR_PI * x[k])) / i0;
+  return g;
+}
+
 static int check_integrand(int id, int ndim, int nparams) {
   switch (id) {
     case OR_GAUSS: return (ndim >= 1 && nparams == 1) ? OR_OK : OR_EINVAL;
     case OR_DY: return (ndim >= 4 && nparams == 10) ? OR_OK : OR_EINVAL;
     case OR_EE3J:
       return (ndim >= 5 && (nparams == 1 || nparams == 2)) ? OR_OK : OR_EINVAL;
+    case OR_DYNLO: return (ndim >= 4 && nparams == 11) ? OR_OK : OR_EINVAL;
     default: return OR_EINVAL;
   }
 }
@@ -416,6 +443,7 @@ static double integrand_point(int id, int ndim, const double* x,
     case OR_GAUSS: return gauss_point(ndim, x, prm[0]);
     case OR_DY: return dy_point(x, prm, mom, grad);
     case OR_EE3J: return ee3j_point(x, prm, nparams, mom);
+    case OR_DYNLO: return dynlo_point(ndim, x, prm, mom);
   }
   return 0.0;
 }

@@ -214,6 +214,50 @@ def test_dy_total_cross_section(oracle_mod):
     assert r.error < 1e-3 * exact
 
 
+# ------------------------------------------------- NLO-shaped stand-in (id 3)
+DYNLO_BETA = 0.5
+
+
+def test_dynlo_extra_factor_integrates_to_one(oracle_mod):
+    """Along one extra axis the weight is the Drell-Yan weight times
+    exp(beta cos 2 pi u) / I0(beta); quadrature of that factor (no Bessel
+    function involved) gives 1."""
+    from scipy.integrate import quad
+
+    x = np.array([0.3, 0.6, 0.2, 0.7, 0.0])
+    g_dy = oracle_mod.integrand(oracle_mod.DY, x, DY_PARAMS)
+    for beta in (0.3, 1.0, 2.5):
+        p = tuple(DY_PARAMS) + (beta,)
+
+        def f(u):
+            xx = x.copy()
+            xx[4] = u
+            return oracle_mod.integrand(oracle_mod.DYNLO, xx, p) / g_dy
+
+        val, err = quad(f, 0.0, 1.0, epsabs=1e-14, epsrel=1e-13, limit=200)
+        assert abs(val - 1.0) < 1e-12, (beta, val)
+
+
+def test_dynlo_beta_zero_is_drell_yan(oracle_mod):
+    """beta = 0 makes every extra factor exactly 1: the events' weights are the
+    Drell-Yan ones bit for bit (13 axes, the same Philox streams and bins)."""
+    edges = oracle_mod.uniform_edges(13, 50)
+    p = tuple(DY_PARAMS) + (0.0,)
+    for ev in (0, 17, 123_456):
+        w0, b0, _ = oracle_mod.event(oracle_mod.DY, 13, 50, edges, DY_PARAMS, 1234, 2, 0, ev)
+        w1, b1, _ = oracle_mod.event(oracle_mod.DYNLO, 13, 50, edges, p, 1234, 2, 0, ev)
+        assert w0 == w1 and np.array_equal(b0, b1)
+
+
+def test_dynlo_total_is_drell_yan_cross_section(oracle_mod):
+    """13 axes, beta = 0.5: the integral is the Drell-Yan cross section."""
+    exact = refs.dy_sigma_quadrature(DY_PARAMS)
+    p = tuple(DY_PARAMS) + (DYNLO_BETA,)
+    r = _two_stage(oracle_mod, 13, 50, oracle_mod.DYNLO, p, 200_000, 4, 5, 1234)
+    assert abs(r.integral - exact) < 4.5 * r.error
+    assert r.error < 3e-3 * exact
+
+
 # --------------------------------------------------------- thread invariance
 def test_results_independent_of_thread_count(oracle_mod):
     """Section 2.2's validation invariant, bit-exact: 1, 2, 3 and 8 threads."""
