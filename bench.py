@@ -39,10 +39,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 71_936
+FILL_TRAFFIC_BYTES = 72_192
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "3bb982ea4440c2c179eec57d0baec8413098904d36a2a1e45402551fd336ae80"
+FILL_SOURCES_SHA256 = "17108804428fdfa05074be1d68754cad1472bec79ee1da5974cf59b729838723"
 
 
 def _fill_traffic():
@@ -308,8 +308,8 @@ def forms(v, stream, seed):
     the plain FP64 Gauss case 5 x 1e5."""
     import torch
 
-    from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, EE3J, EE3J_PARAMS, GAUSS,
-                                                  GAUSS_PARAMS, batch_spec)
+    from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, DYNLO, DYNLO_PARAMS, EE3J,
+                                                  EE3J_PARAMS, GAUSS, GAUSS_PARAMS, batch_spec)
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -323,7 +323,9 @@ def forms(v, stream, seed):
     res = {}
     for name, (iid, params, d, n, ncall, itmx, prec) in {
             "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32"),
-            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64")}.items():
+            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64"),
+            "dy_nlo_shaped_d13_n50_10x1e6_fp32": (DYNLO, DYNLO_PARAMS, 13, 50, 1_000_000, 10,
+                                                  "fp32")}.items():
         g = v.Vegas(d, n, seed, precision=prec)
         v.vegas_set_stream(g.h, stream.cuda_stream)
         try:

@@ -51,6 +51,11 @@ extern "C" {
                          f_q = N x^a (1-x)^b, f_qbar = 0.2 N x^a (1-x)^(b+4); ndim >= 4 */
 #define VEGAS_EE3J 2  /* params[1 or 2]: y_cut [, sqrt_s = 91.1876].
                          e+e- -> q qbar g, (x1^2+x2^2)/((1-x1)(1-x2)) with y_ij > y_cut; ndim >= 5 */
+#define VEGAS_DY_NLO 3 /* params[11]: the ten of VEGAS_DY, then beta.  An NLO-shaped stand-in
+                          for the paper's 13-dimensional NLO integral (Section 3.2): the
+                          Drell-Yan weight of x_0..x_3 times exp(beta cos(2 pi x_k)) / I0(beta)
+                          for every further axis k (each factor integrates to 1, so the
+                          integral is the Drell-Yan cross section); ndim >= 4; not batched */
 
 /* ---- limits ---- */
 #define VEGAS_MAX_DIM 16
@@ -64,7 +69,8 @@ extern "C" {
 #define VEGAS_OPT_ALPHA 0     /* grid damping exponent alpha >= 0 (default 1.5) */
 #define VEGAS_OPT_PRECISION 1 /* 0 = FP64 integrand (default), 1 = FP32 integrand, FP64 sums */
 #define VEGAS_OPT_ADAPT 2     /* 1 = refine the grid after every iteration (default), 0 = frozen */
-#define VEGAS_OPT_EPT 3       /* events per thread of the fill kernel: 0 = autotuned, or 1, 2, 4, 8 */
+#define VEGAS_OPT_EPT 3       /* events per thread of the fill kernel: 0 = autotuned, or 1, 2, 4, 8
+                                 (8 only for ndim <= 8: VEGAS_EINVAL above) */
 #define VEGAS_OPT_NONFINITE 4 /* 0 = return VEGAS_ENONFINITE if any weight is not finite (default),
                                  1 = set such weights to 0 and count them silently */
 #define VEGAS_OPT_GRAPH 5     /* 1 = replay the iterations as one CUDA graph (default), 0 = plain launches */

@@ -32,11 +32,15 @@ cudaError_t launch_fill_dy(int fp32, int ept, const GvFillArgs& a, int n_tiles, 
                            cudaStream_t s, bool pdl);
 cudaError_t launch_fill_ee3j(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
                              cudaStream_t s, bool pdl);
+cudaError_t launch_fill_dynlo(int fp32, int ept, const GvFillArgs& a, int n_tiles, size_t smem,
+                             cudaStream_t s, bool pdl);
 cudaError_t launch_fill_gauss_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
                                    long long n, double* w, int* bins, cudaStream_t s);
 cudaError_t launch_fill_dy_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
                                 long long n, double* w, int* bins, cudaStream_t s);
 cudaError_t launch_fill_ee3j_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
+                                  long long n, double* w, int* bins, cudaStream_t s);
+cudaError_t launch_fill_dynlo_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
                                   long long n, double* w, int* bins, cudaStream_t s);
 }  // namespace gv
 
@@ -62,6 +66,7 @@ cudaError_t launch_fill_any(int ig, int fp32, int ept, const GvFillArgs& a, int 
     case GV_GAUSS: return gv::launch_fill_gauss(fp32, ept, a, n_tiles, smem, s, pdl);
     case GV_DY: return gv::launch_fill_dy(fp32, ept, a, n_tiles, smem, s, pdl);
     case GV_EE3J: return gv::launch_fill_ee3j(fp32, ept, a, n_tiles, smem, s, pdl);
+    case GV_DYNLO: return gv::launch_fill_dynlo(fp32, ept, a, n_tiles, smem, s, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -84,6 +89,10 @@ int check_params(int ig, int ndim, const double* p, int np) {
     case VEGAS_EE3J:
       if ((np != 1 && np != 2) || ndim < 5 || !(p[0] > 0.0 && p[0] < 1.0)) return VEGAS_EINVAL;
       if (np == 2 && !(p[1] > 0.0)) return VEGAS_EINVAL;
+      return VEGAS_OK;
+    case VEGAS_DY_NLO:
+      if (np != 11 || check_params(VEGAS_DY, ndim, p, 10) || !(std::fabs(p[10]) <= 50.0))
+        return VEGAS_EINVAL;
       return VEGAS_OK;
   }
   return VEGAS_EINVAL;
@@ -922,7 +931,8 @@ int vegas_eval_events(vegas_ctx* c, int id, const double* params, int np, uint32
     switch (id) {
       case GV_GAUSS: e = gv::launch_fill_gauss_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
       case GV_DY: e = gv::launch_fill_dy_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
-      default: e = gv::launch_fill_ee3j_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
+      case GV_EE3J: e = gv::launch_fill_ee3j_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
+      default: e = gv::launch_fill_dynlo_eval(c->fp32, a, iteration, dev, n, dw, db, c->stream); break;
     }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(w, dw, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);

@@ -40,14 +40,14 @@
 #define GV_MAXCH (1 + GV_NGRAD)
 #define GV_EMPTY (-0x40000000)  // scale of a tile / iteration with no nonzero value
 #define GV_NCONST 48          // derived integrand constants per integration (doubles)
-#define GV_NCONST_F32 24      // constants 0..23 in FP64, then their FP32 copies
+#define GV_NCONST_F32 32      // constants 0..31 in FP64, then their FP32 copies
 #define GV_MAXPARAMS 16
 #define GV_BINE_OFF 1100      // stored bin exponent F + GV_BINE_OFF (0: no nonzero weight)
 #define GV_BIN_QBITS 56       // bits of one w^2 below its bin's scale in a tile
 #define GV_BIN_XBITS 32       // extra low bits of the iteration's bin sums
 #define GV_BIN_FB (GV_BIN_QBITS + GV_BIN_XBITS)  // bin sums in units of 2^(2F - GV_BIN_FB)
 
-enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2 };
+enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2, GV_DYNLO = 3 };
 
 // Device-side state of one integration (one context or one batch member).
 // nonfinite_iter and the tickets return to zero at the end of every iteration.

@@ -35,6 +35,10 @@ template <>
 struct GvTraits<GV_EE3J> {
   static constexpr int NK = 3;
 };
+template <>
+struct GvTraits<GV_DYNLO> {
+  static constexpr int NK = NK_NK;
+};
 
 template <int IG, typename Real, int MAXD>
 __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
@@ -43,6 +47,8 @@ __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
     return gv_gauss<Real, MAXD>(x, d, K[GK_INV2S2]);
   } else if constexpr (IG == GV_DY) {
     return gv_drell_yan<Real, false>(x, K, nullptr);
+  } else if constexpr (IG == GV_DYNLO) {
+    return gv_dy_nlo<Real, MAXD>(x, d, K);
   } else {
     return gv_ee3j<Real>(x, K);
   }

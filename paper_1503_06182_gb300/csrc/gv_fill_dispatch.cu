@@ -4,3 +4,4 @@
 GV_DEFINE_FILL_DISPATCH(launch_fill_gauss)
 GV_DEFINE_FILL_DISPATCH(launch_fill_dy)
 GV_DEFINE_FILL_DISPATCH(launch_fill_ee3j)
+GV_DEFINE_FILL_DISPATCH(launch_fill_dynlo)

@@ -45,6 +45,9 @@
 #define DK_DCB2 21
 #define DK_LOGTAULO 22  // ln tau_lo
 #define DK_NK 23        // Drell-Yan constants
+#define NK_BETA 23      // NLO-shaped stand-in: beta
+#define NK_INVI0 24     //   1 / I0(beta)
+#define NK_NK 25        //   its constants (the Drell-Yan ones first)
 // e+e- -> q qbar g
 #define EK_YCUT 0
 #define EK_Q 1
@@ -127,9 +130,10 @@ __device__ __forceinline__ Real gv_gauss(const Real (&x)[MAXD], int d, Real inv2
 // antiquark-from-hadron-1 term taking c -> -c.
 // With GRAD the reverse sweep also returns dg/d(M_Z, Gamma_Z, sw2, a, b).
 // ---------------------------------------------------------------------------
-template <typename Real, bool GRAD>
-__device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, DK_NK>& K,
+template <typename Real, bool GRAD, int NC>
+__device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, NC>& K,
                                              Real* grad) {
+  static_assert(NC >= DK_NK, "Drell-Yan constants");
   using Mt = GvMath<Real>;
   const Real one = (Real)1, two = (Real)2;
   // phase space: ln tau linear in x[0]; x1,2 = sqrt(tau) e^(+-y)
@@ -214,6 +218,28 @@ __device__ __forceinline__ Real gv_drell_yan(const Real* x, const GvConst<Real, 
     grad[4] = gb_b;
   }
   return P * S;
+}
+
+// ---------------------------------------------------------------------------
+// NLO-shaped stand-in: the Drell-Yan weight of x_0..x_3 times, for every
+// further axis, exp(beta cos(2 pi x_k)) / I0(beta) (each factor integrates to
+// 1 over [0,1]).  More axes, more work per event, the same integral.
+// ---------------------------------------------------------------------------
+template <typename Real, int MAXD>
+__device__ __forceinline__ Real gv_dy_nlo(const Real (&x)[MAXD], int d,
+                                          const GvConst<Real, NK_NK>& K) {
+  using Mt = GvMath<Real>;
+  Real g = gv_drell_yan<Real, false>(x, K, nullptr);
+  Real f = (Real)1;
+#pragma unroll
+  for (int a = 4; a < MAXD; ++a) {
+    if (a < d) {
+      Real sn, cs;
+      Mt::sincospi((Real)2 * x[a], &sn, &cs);
+      f = f * (Mt::exp(K[NK_BETA] * cs) * K[NK_INVI0]);
+    }
+  }
+  return g * f;
 }
 
 // ---------------------------------------------------------------------------

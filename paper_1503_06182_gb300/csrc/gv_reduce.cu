@@ -727,7 +727,7 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
   for (int i = 0; i < GV_NCONST; ++i) K[i] = 0.0;
   if (ig == GV_GAUSS) {
     K[GK_INV2S2] = 1.0 / (2.0 * p[0] * p[0]);
-  } else if (ig == GV_DY) {
+  } else if (ig == GV_DY || ig == GV_DYNLO) {
     const double sqrt_s = p[0], MZ = p[1], GZ = p[2], sw2 = p[3], alpha = p[4];
     const double mlo = p[5], mhi = p[6];
     const double s = sqrt_s * sqrt_s;
@@ -775,6 +775,17 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
     K[DK_DCA1] = dA1;
     K[DK_DCA2] = dA2;
     K[DK_DCB2] = dB2;
+    if (ig == GV_DYNLO) {
+      // beta and 1 / I0(beta), I0(beta) = sum_k ((beta/2)^k / k!)^2
+      const double beta = p[10];
+      double term = 1.0, i0 = 1.0;
+      for (int k = 1; k < 200 && term >= 1e-18 * i0; ++k) {
+        term *= (0.25 * beta * beta) / ((double)k * (double)k);
+        i0 += term;
+      }
+      K[NK_BETA] = beta;
+      K[NK_INVI0] = 1.0 / i0;
+    }
   } else if (ig == GV_EE3J) {
     const double Q = np > 1 ? p[1] : 91.1876;
     K[EK_YCUT] = p[0];

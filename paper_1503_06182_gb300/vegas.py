@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgvegas.so")
 VEGAS_OK = 0
 VEGAS_EINVAL, VEGAS_ENOMEM, VEGAS_ECUDA, VEGAS_EGRID = -1, -2, -3, -4
 VEGAS_ENONFINITE, VEGAS_EDEVICE, VEGAS_ESTATE = -5, -6, -7
-VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J = 0, 1, 2
+VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J, VEGAS_DY_NLO = 0, 1, 2, 3
 VEGAS_OPT_ALPHA, VEGAS_OPT_PRECISION, VEGAS_OPT_ADAPT, VEGAS_OPT_EPT = 0, 1, 2, 3
 VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH, VEGAS_OPT_TIMING, VEGAS_OPT_BATCH_ID = 4, 5, 6, 7
 VEGAS_OPT_PDL = 8

@@ -17,8 +17,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-GAUSS, DY, EE3J = 0, 1, 2
-INTEGRAND_NAMES = {GAUSS: "gauss", DY: "drell_yan", EE3J: "ee_qqg"}
+GAUSS, DY, EE3J, DYNLO = 0, 1, 2, 3
+INTEGRAND_NAMES = {GAUSS: "gauss", DY: "drell_yan", EE3J: "ee_qqg", DYNLO: "drell_yan_nlo_shaped"}
 
 # LO pp -> gamma*/Z -> mu+ mu- at sqrt(s) = 14 TeV:
 # (sqrt_s, M_Z, Gamma_Z, sin^2 theta_W, alpha, m_lo, m_hi, a, b, N)
@@ -26,6 +26,9 @@ DY_PARAMS = (14000.0, 91.1876, 2.4952, 0.2312, 1.0 / 128.0, 60.0, 120.0, -0.5, 3
 # indices of (M_Z, Gamma_Z, sin^2 theta_W, a, b) inside DY_PARAMS
 DY_GRAD_INDEX = (1, 2, 3, 7, 8)
 GAUSS_PARAMS = (0.1,)
+# NLO-shaped stand-in: the Drell-Yan parameters, then beta of the extra axes'
+# factors exp(beta cos 2 pi x) / I0(beta)
+DYNLO_PARAMS = DY_PARAMS + (0.5,)
 EE3J_PARAMS = (0.01, 91.1876)
 
 SEED = 1234
