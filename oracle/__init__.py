@@ -76,6 +76,17 @@ def _load():
                                        C.POINTER(C.c_double), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_int64)]
+        lib.oracle_iterate_hist.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                            C.POINTER(C.c_uint64), C.c_int64, C.c_int, C.c_int,
+                                            _dp, C.c_int, C.c_double, C.c_int, _dp, C.c_int,
+                                            C.c_double, C.c_double, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.POINTER(C.c_int64)]
+        lib.oracle_observable.argtypes = [C.c_int, C.c_int, _dp, _dp, C.c_int,
+                                          C.POINTER(C.c_double)]
+        lib.oracle_hist_bin.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double]
+        lib.oracle_hist_combine.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
         lib.oracle_adjoint.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32,
                                        C.POINTER(C.c_uint64), C.c_int64, C.c_int, C.c_int, _dp,
                                        C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double),
@@ -191,11 +202,42 @@ class Result(dict):
     __getattr__ = dict.__getitem__
 
 
+def observable(iid: int, x, params) -> float:
+    """The histogram observable of an event at x: Gauss x_0, Drell-Yan m_ll
+    (GeV), 3-jet thrust."""
+    x = np.ascontiguousarray(x, np.float64)
+    params = np.ascontiguousarray(params, np.float64)
+    v = C.c_double()
+    _check(_load().oracle_observable(iid, len(x), x, params, len(params), C.byref(v)),
+           "observable")
+    return v.value
+
+
+def hist_bin(v: float, nh: int, lo: float, hi: float) -> int:
+    """Bin of v among nh bins over [lo, hi): 0 underflow, nh + 1 overflow."""
+    return int(_load().oracle_hist_bin(float(v), int(nh), float(lo), float(hi)))
+
+
+def hist_combine(sk, H, V):
+    """Combined histogram (value, error) of per-iteration bin estimates H and
+    variances V (m x hb) with the integral's weights."""
+    sk = np.ascontiguousarray(sk, np.float64)
+    H = np.ascontiguousarray(H, np.float64)
+    V = np.ascontiguousarray(V, np.float64)
+    m, hb = H.shape
+    val, err = np.zeros(hb), np.zeros(hb)
+    _load().oracle_hist_combine(m, hb, sk, H.ravel(), V.ravel(), val, err)
+    return val, err
+
+
 def iterate(ndim, nbins, seed, ncall, itmx, iid, params, *, edges=None, iteration=0, batch=0,
-            alpha=1.5, adapt=True, want_sums=False) -> Result:
+            alpha=1.5, adapt=True, want_sums=False, hist=None) -> Result:
     """itmx VEGAS iterations (one stage).  Returns integral, error, chi2dof,
     per_iter (itmx x 2), edges after the stage, the next iteration counter,
-    and (optionally) the last iteration's sums."""
+    and (optionally) the last iteration's sums.  hist = (nh, lo, hi) adds the
+    combined histogram of the observable (hist_value, hist_error: nh + 2
+    entries with underflow first and overflow last) and the last iteration's
+    per-bin sums (hist_last: sum w then sum w^2)."""
     if edges is None:
         edges = uniform_edges(ndim, nbins)
     edges = np.ascontiguousarray(np.array(edges, np.float64, copy=True))
@@ -205,15 +247,23 @@ def iterate(ndim, nbins, seed, ncall, itmx, iid, params, *, edges=None, iteratio
     per = np.zeros((itmx, 2), np.float64)
     sums = np.zeros(2 + ndim * nbins, np.float64)
     bad = C.c_int64()
-    st = _load().oracle_iterate(ndim, nbins, seed, batch, C.byref(it), ncall, itmx, iid, params,
-                                len(params), alpha, int(adapt), edges.reshape(-1), C.byref(I),
-                                C.byref(e), C.byref(c), per.ctypes.data,
-                                sums.ctypes.data if want_sums else None, C.byref(bad))
+    nh, lo, hi = (0, 0.0, 0.0) if hist is None else (int(hist[0]), float(hist[1]), float(hist[2]))
+    hb = nh + 2 if nh > 0 else 0
+    hval, herr, hlast = np.zeros(max(hb, 1)), np.zeros(max(hb, 1)), np.zeros(max(2 * hb, 1))
+    st = _load().oracle_iterate_hist(ndim, nbins, seed, batch, C.byref(it), ncall, itmx, iid,
+                                     params, len(params), alpha, int(adapt), edges.reshape(-1),
+                                     nh, lo, hi, C.byref(I), C.byref(e), C.byref(c),
+                                     per.ctypes.data, sums.ctypes.data if want_sums else None,
+                                     hval.ctypes.data, herr.ctypes.data, hlast.ctypes.data,
+                                     C.byref(bad))
     _check(st, "iterate")
     r = Result(integral=I.value, error=e.value, chi2dof=c.value, per_iter=per, edges=edges,
                iteration=it.value, nonfinite=bad.value)
     if want_sums:
         r["sums"] = sums
+    if hb:
+        r["hist_value"], r["hist_error"] = hval, herr
+        r["hist_last"] = hlast.reshape(2, hb)
     return r
 
 

@@ -33,6 +33,13 @@
  *   r = ((1-rho)/(-ln rho))^alpha, redistribution of N equal shares of
  *   sum(r) with linear interpolation inside the old bins.
  *
+ * Histograms during integration (the paper's differential distributions, the
+ * di-jet mass plots of Section 3.2): each event's weight is also summed into
+ * the bin of one observable of the event.  Per iteration and bin,
+ * H_kb = sum_{e in b} w / C and V_kb = (sum_{e in b} w^2 / C - H_kb^2)/(C-1);
+ * a call's iterations are combined with the integral's weights 1/sigma_k^2,
+ * so the bins add up to the combined integral.
+ *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (oracle/__init__.py).
  */
 #include <math.h>
@@ -448,6 +455,57 @@ static double integrand_point(int id, int ndim, const double* x,
   return 0.0;
 }
 
+/* The histogram observable of an event at x (Section 3.2's differential
+ * distributions):
+ *   Gauss: x_0;
+ *   Drell-Yan (LO and the NLO-shaped stand-in): the dilepton invariant mass
+ *     m_ll in GeV; at LO the pair carries the whole partonic energy, so
+ *     m_ll^2 = shat = tau s with tau as in dy_point;
+ *   e+e- -> q qbar g: the thrust, which for three massless partons is the
+ *     largest energy fraction max(x1, x2, x3) with x3 = 2 - x1 - x2. */
+static double observable(int id, const double* x, const double* prm) {
+  switch (id) {
+    case OR_GAUSS: return x[0];
+    case OR_DY:
+    case OR_DYNLO: {
+      const double sqrt_s = prm[0], mlo = prm[5], mhi = prm[6];
+      const double s = sqrt_s * sqrt_s;
+      const double tau_lo = mlo * mlo / s, tau_hi = mhi * mhi / s;
+      const double tau = tau_lo * exp(x[0] * log(tau_hi / tau_lo));
+      return sqrt(tau * s);
+    }
+    case OR_EE3J: {
+      const double x1 = x[0], x2 = x[1], x3 = 2.0 - x1 - x2;
+      double t = x1 > x2 ? x1 : x2;
+      return t > x3 ? t : x3;
+    }
+  }
+  return 0.0;
+}
+
+int oracle_observable(int id, int ndim, const double* x, const double* prm,
+                      int nparams, double* obs) {
+  int st = check_integrand(id, ndim, nparams);
+  if (st) return st;
+  *obs = observable(id, x, prm);
+  return OR_OK;
+}
+
+/* Bin of an observable value among nh equal bins over [lo, hi), with
+ * underflow 0 and overflow nh + 1 (a value that is not a number counts as
+ * underflow); invw = nh / (hi - lo).  The position is (v - lo) * invw in
+ * FP64, truncated. */
+static int hist_bin(double v, double lo, double invw, int nh) {
+  if (!(v >= lo)) return 0;
+  double t = (v - lo) * invw;
+  if (!(t < (double)nh)) return nh + 1;
+  return 1 + (int)t;
+}
+
+int oracle_hist_bin(double v, int nh, double lo, double hi) {
+  return hist_bin(v, lo, (double)nh / (hi - lo), nh);
+}
+
 /* g at a point of the unit cube (exported for the tests). */
 int oracle_integrand(int id, int ndim, const double* x, const double* prm,
                      int nparams, double* g, double* mom, double* grad) {
@@ -621,10 +679,12 @@ int oracle_refine(int ndim, int nbins, double alpha, const double* d,
 static int iteration_sums(int id, int ndim, int nbins, const double* edges,
                           const double* prm, int nparams, uint64_t seed,
                           uint32_t it, uint32_t batch, int64_t ncall,
-                          int nch, int want_bins, double* sums,
-                          int64_t* nonfinite) {
+                          int nch, int want_bins, int nh, double h_lo,
+                          double h_invw, double* sums, int64_t* nonfinite) {
   const int nbin_acc = want_bins ? ndim * nbins : 0;
-  const int nacc = 2 * nch + nbin_acc;
+  const int hb = nh > 0 ? nh + 2 : 0; /* histogram bins incl. under/overflow */
+  const int h0 = 2 * nch + nbin_acc;  /* sum w of bin b at h0 + b, sum w^2 at h0 + hb + b */
+  const int nacc = h0 + 2 * hb;
   const int64_t nchunks = (ncall + ORACLE_CHUNK - 1) / ORACLE_CHUNK;
   csum_t* total = (csum_t*)calloc((size_t)nacc, sizeof(csum_t));
   if (!total) return OR_ENOMEM;
@@ -648,8 +708,9 @@ static int iteration_sums(int id, int ndim, int nbins, const double* edges,
           int32_t bins[ORACLE_MAX_DIM];
           double grad[ORACLE_NGRAD];
           double v[1 + ORACLE_NGRAD];
+          double x[ORACLE_MAX_DIM];
           v[0] = event_weight(id, ndim, nbins, edges, prm, nparams, seed, it,
-                              batch, (uint64_t)ev, bins, NULL,
+                              batch, (uint64_t)ev, bins, x,
                               nch > 1 ? grad : NULL);
           for (int c = 1; c < nch; ++c) v[c] = grad[c - 1];
           int finite = 1;
@@ -666,6 +727,11 @@ static int iteration_sums(int id, int ndim, int nbins, const double* edges,
             double w2 = v[0] * v[0];
             for (int a = 0; a < ndim; ++a)
               csum_add(&part[2 * nch + a * nbins + bins[a]], w2);
+          }
+          if (hb) {
+            int b = hist_bin(observable(id, x, prm), h_lo, h_invw, nh);
+            csum_add(&part[h0 + b], v[0]);
+            csum_add(&part[h0 + hb + b], v[0] * v[0]);
           }
         }
       }
@@ -697,30 +763,81 @@ static void mean_sigma(double s1, double s2, int64_t ncall, double* mean,
   *sigma = var > 0.0 ? sqrt(var) : 0.0;
 }
 
+/* Combination of the histograms of the m iterations of one call, bin by bin,
+ * with the weights of the integral (oracle_combine): 1/sigma_k^2, so that
+ * the bins of the combined histogram add up to the combined integral; if any
+ * sigma_k is 0, the zero-variance iterations alone, with equal weights.
+ * H, V: m x hb (row = iteration) bin estimates and their variances;
+ * value, error: hb each.
+ *   value_b = sum_k u_k H_kb / sum_k u_k,
+ *   error_b = sqrt(sum_k u_k^2 V_kb) / sum_k u_k. */
+void oracle_hist_combine(int m, int hb, const double* sk, const double* H,
+                         const double* V, double* value, double* error) {
+  int nzero = 0;
+  for (int k = 0; k < m; ++k)
+    if (!(sk[k] > 0.0)) ++nzero;
+  double W = 0.0;
+  for (int k = 0; k < m; ++k) {
+    if (nzero > 0)
+      W += sk[k] > 0.0 ? 0.0 : 1.0;
+    else
+      W += 1.0 / (sk[k] * sk[k]);
+  }
+  for (int b = 0; b < hb; ++b) {
+    double sv = 0.0, se = 0.0;
+    for (int k = 0; k < m; ++k) {
+      double u;
+      if (nzero > 0)
+        u = sk[k] > 0.0 ? 0.0 : 1.0;
+      else
+        u = 1.0 / (sk[k] * sk[k]);
+      sv += u * H[(size_t)k * hb + b];
+      se += u * u * V[(size_t)k * hb + b];
+    }
+    value[b] = sv / W;
+    error[b] = sqrt(se) / W;
+  }
+}
+
 /* itmx iterations of one call ("stage").  *iteration is the global
  * iteration counter (the Philox counter word), advanced by itmx.  edges
  * (ndim x (nbins+1)) is refined after every iteration when adapt != 0.
  * per_iter (nullable): itmx x (I_k, sigma_k).  last_sums (nullable): the sums
  * of the last iteration, (sum w, sum w^2, d[ndim*nbins]).
+ * Histogram (nh > 0 bins over [lo, hi), plus underflow and overflow, so
+ * hb = nh + 2 entries): hist_value, hist_error (hb each, nullable) the
+ * combined histogram; hist_last (nullable, 2 hb) the last iteration's
+ * sum w then sum w^2 per bin.
  * Returns the number of non-finite events seen through *nonfinite. */
-int oracle_iterate(int ndim, int nbins, uint64_t seed, uint32_t batch,
-                   uint64_t* iteration, int64_t ncall, int itmx, int id,
-                   const double* prm, int nparams, double alpha, int adapt,
-                   double* edges, double* integral, double* error,
-                   double* chi2dof, double* per_iter, double* last_sums,
-                   int64_t* nonfinite) {
+int oracle_iterate_hist(int ndim, int nbins, uint64_t seed, uint32_t batch,
+                        uint64_t* iteration, int64_t ncall, int itmx, int id,
+                        const double* prm, int nparams, double alpha, int adapt,
+                        double* edges, int nh, double lo, double hi,
+                        double* integral, double* error, double* chi2dof,
+                        double* per_iter, double* last_sums, double* hist_value,
+                        double* hist_error, double* hist_last,
+                        int64_t* nonfinite) {
   if (ndim < 1 || ndim > ORACLE_MAX_DIM || nbins < 2 || ncall < 2 || itmx < 1)
     return OR_EINVAL;
+  if (nh < 0 || (nh > 0 && !(hi > lo))) return OR_EINVAL;
   int st = check_integrand(id, ndim, nparams);
   if (st) return st;
-  const int nacc = 2 + ndim * nbins;
+  const int hb = nh > 0 ? nh + 2 : 0;
+  const int nd = 2 + ndim * nbins;
+  const int nacc = nd + 2 * hb;
+  const double invw = nh > 0 ? (double)nh / (hi - lo) : 0.0;
+  const double C = (double)ncall;
   double* sums = (double*)malloc(sizeof(double) * nacc);
   double* Ik = (double*)malloc(sizeof(double) * itmx);
   double* sk = (double*)malloc(sizeof(double) * itmx);
-  if (!sums || !Ik || !sk) {
+  double* H = (double*)malloc(sizeof(double) * ((size_t)itmx * hb + 1));
+  double* V = (double*)malloc(sizeof(double) * ((size_t)itmx * hb + 1));
+  if (!sums || !Ik || !sk || !H || !V) {
     free(sums);
     free(Ik);
     free(sk);
+    free(H);
+    free(V);
     return OR_ENOMEM;
   }
   int64_t bad_all = 0;
@@ -728,7 +845,7 @@ int oracle_iterate(int ndim, int nbins, uint64_t seed, uint32_t batch,
     uint32_t it = (uint32_t)(*iteration);
     int64_t bad = 0;
     st = iteration_sums(id, ndim, nbins, edges, prm, nparams, seed, it, batch,
-                        ncall, 1, 1, sums, &bad);
+                        ncall, 1, 1, nh, lo, invw, sums, &bad);
     if (st) break;
     bad_all += bad;
     *iteration += 1;
@@ -737,15 +854,43 @@ int oracle_iterate(int ndim, int nbins, uint64_t seed, uint32_t batch,
       per_iter[2 * k] = Ik[k];
       per_iter[2 * k + 1] = sk[k];
     }
-    if (last_sums && k == itmx - 1) memcpy(last_sums, sums, sizeof(double) * nacc);
+    for (int b = 0; b < hb; ++b) {
+      /* the bin's share of the iteration estimate and its variance */
+      double h = sums[nd + b] / C;
+      double v = (sums[nd + hb + b] / C - h * h) / (C - 1.0);
+      H[(size_t)k * hb + b] = h;
+      V[(size_t)k * hb + b] = v > 0.0 ? v : 0.0;
+    }
+    if (k == itmx - 1) {
+      if (last_sums) memcpy(last_sums, sums, sizeof(double) * nd);
+      if (hist_last && hb) memcpy(hist_last, sums + nd, sizeof(double) * 2 * hb);
+    }
     if (adapt) oracle_refine(ndim, nbins, alpha, sums + 2, edges);
   }
-  if (!st) oracle_combine(itmx, Ik, sk, integral, error, chi2dof);
+  if (!st) {
+    oracle_combine(itmx, Ik, sk, integral, error, chi2dof);
+    if (hb && hist_value && hist_error)
+      oracle_hist_combine(itmx, hb, sk, H, V, hist_value, hist_error);
+  }
   if (nonfinite) *nonfinite = bad_all;
   free(sums);
   free(Ik);
   free(sk);
+  free(H);
+  free(V);
   return st;
+}
+
+int oracle_iterate(int ndim, int nbins, uint64_t seed, uint32_t batch,
+                   uint64_t* iteration, int64_t ncall, int itmx, int id,
+                   const double* prm, int nparams, double alpha, int adapt,
+                   double* edges, double* integral, double* error,
+                   double* chi2dof, double* per_iter, double* last_sums,
+                   int64_t* nonfinite) {
+  return oracle_iterate_hist(ndim, nbins, seed, batch, iteration, ncall, itmx,
+                             id, prm, nparams, alpha, adapt, edges, 0, 0.0, 0.0,
+                             integral, error, chi2dof, per_iter, last_sums, NULL,
+                             NULL, NULL, nonfinite);
 }
 
 /* Gradient of the Drell-Yan cross section with respect to
@@ -782,7 +927,7 @@ int oracle_adjoint(int ndim, int nbins, uint64_t seed, uint32_t batch,
   for (int k = 0; k < itmx && !st; ++k) {
     uint32_t it = (uint32_t)(*iteration);
     st = iteration_sums(id, ndim, nbins, edges, prm, nparams, seed, it, batch,
-                        ncall, nch, 0, sums, NULL);
+                        ncall, nch, 0, 0, 0.0, 0.0, sums, NULL);
     if (st) break;
     *iteration += 1;
     mean_sigma(sums[0], sums[1], ncall, &Ik[k], &sk[k]);

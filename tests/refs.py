@@ -71,10 +71,16 @@ def dy_sigma_hat(fq, shat, MZ, GZ, sw2, alpha):
     return math.pi * alpha ** 2 / (3 * shat * NC) * sum(abs(v) ** 2 for v in F.values())
 
 
-def dy_sigma_quadrature(params, epsrel=1e-10) -> float:
+def dy_sigma_quadrature(params, epsrel=1e-10, m_range=None) -> float:
     """sigma(pp -> mu+ mu-) in pb by adaptive quadrature over (m_mumu, y):
-    sum_q int dtau dy [f_q(x1) f_qbar(x2) + f_qbar(x1) f_q(x2)] sigmahat_q(tau s)."""
+    sum_q int dtau dy [f_q(x1) f_qbar(x2) + f_qbar(x1) f_q(x2)] sigmahat_q(tau s).
+    m_range = (m_a, m_b) restricts the dilepton mass to that interval (inside
+    the generated range): the cross section in one bin of m_mumu."""
     sqrt_s, MZ, GZ, sw2, alpha, mlo, mhi, a, b, N = params
+    if m_range is not None:
+        mlo, mhi = max(mlo, m_range[0]), min(mhi, m_range[1])
+        if not mhi > mlo:
+            return 0.0
     s = sqrt_s ** 2
     fq = lambda x: N * x ** a * (1 - x) ** b
     fqb = lambda x: 0.2 * N * x ** a * (1 - x) ** (b + 4)
@@ -93,8 +99,40 @@ def dy_sigma_quadrature(params, epsrel=1e-10) -> float:
         L, _ = integrate.quad(lumi, -Y, Y, epsabs=0, epsrel=epsrel * 0.1, limit=200)
         return L * sig * 2 * m / s  # dtau = 2 m dm / s
 
-    val, _ = integrate.quad(inner, mlo, mhi, points=[MZ], epsabs=0, epsrel=epsrel, limit=400)
+    pts = [MZ] if mlo < MZ < mhi else None
+    val, _ = integrate.quad(inner, mlo, mhi, points=pts, epsabs=0, epsrel=epsrel, limit=400)
     return val * GEV2_TO_PB
+
+
+def gauss_bin(a: float, b: float, ndim: int, sigma: float = 0.1) -> float:
+    """Integral of the product Gaussian over x_0 in [a, b] (inside [0, 1]) and
+    the other axes over [0, 1], via erf."""
+    r = sigma * math.sqrt(2.0)
+    a, b = max(a, 0.0), min(b, 1.0)
+    if not b > a:
+        return 0.0
+    first = sigma * math.sqrt(math.pi / 2) * (math.erf((b - 0.5) / r) - math.erf((a - 0.5) / r))
+    return first * gauss_exact(ndim - 1, sigma)
+
+
+def ee3j_thrust_density(T: float) -> float:
+    """d sigma / dT of (x1^2+x2^2)/((1-x1)(1-x2)) over the massless 3-parton
+    phase space (unit normalisation), T = max(x1, x2, x3) in (2/3, 1): the
+    classic leading-order thrust distribution (De Rujula, Ellis, Floratos,
+    Gaillard 1978)."""
+    return (2.0 * (3 * T * T - 3 * T + 2) / (T * (1 - T)) * math.log((2 * T - 1) / (1 - T))
+            - 3.0 * (3 * T - 2) * (2 - T) / (1 - T))
+
+
+def ee3j_thrust_bin(a: float, b: float, y: float) -> float:
+    """Integral of the thrust distribution over [a, b] intersected with the
+    region the cut y_ij > y leaves, 2/3 < T < 1 - y (for three massless
+    partons y_ij = 1 - x_k, so the cut is exactly T < 1 - y)."""
+    a, b = max(a, 2.0 / 3.0), min(b, 1.0 - y)
+    if not b > a:
+        return 0.0
+    val, _ = integrate.quad(ee3j_thrust_density, a, b, epsabs=0, epsrel=1e-12, limit=200)
+    return val
 
 
 def pulls(values, errors, exact):
