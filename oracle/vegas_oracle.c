@@ -154,14 +154,17 @@ double oracle_grid_map(const double* edges_axis, int nbins, uint32_t r,
  * physical variables and its cuts.
  * ---------------------------------------------------------------------- */
 
-/* Gaussian product: g = prod_a exp(-(x_a - 1/2)^2 / (2 sigma^2)). */
-static double gauss_point(int ndim, const double* x, double sigma) {
+/* Gaussian product: g = prod_a exp(-(x_a - 1/2)^2 / (2 sigma^2)) - shift.
+ * The optional constant shift (default 0) makes weights negative where the
+ * product is below it, as subtraction terms do at NLO. */
+static double gauss_point(int ndim, const double* x, double sigma,
+                          double shift) {
   double g = 1.0;
   for (int a = 0; a < ndim; ++a) {
     double dx = x[a] - 0.5;
     g *= exp(-dx * dx / (2.0 * sigma * sigma));
   }
-  return g;
+  return g - shift;
 }
 
 /* Drell-Yan helpers.  Fermion couplings in the convention V = T3 - 2 Q sw2,
@@ -434,7 +437,8 @@ static double dynlo_point(int ndim, const double* x, const double* prm, double* 
 
 static int check_integrand(int id, int ndim, int nparams) {
   switch (id) {
-    case OR_GAUSS: return (ndim >= 1 && nparams == 1) ? OR_OK : OR_EINVAL;
+    case OR_GAUSS:
+      return (ndim >= 1 && (nparams == 1 || nparams == 2)) ? OR_OK : OR_EINVAL;
     case OR_DY: return (ndim >= 4 && nparams == 10) ? OR_OK : OR_EINVAL;
     case OR_EE3J:
       return (ndim >= 5 && (nparams == 1 || nparams == 2)) ? OR_OK : OR_EINVAL;
@@ -447,7 +451,7 @@ static double integrand_point(int id, int ndim, const double* x,
                               const double* prm, int nparams, double* mom,
                               double* grad) {
   switch (id) {
-    case OR_GAUSS: return gauss_point(ndim, x, prm[0]);
+    case OR_GAUSS: return gauss_point(ndim, x, prm[0], nparams > 1 ? prm[1] : 0.0);
     case OR_DY: return dy_point(x, prm, mom, grad);
     case OR_EE3J: return ee3j_point(x, prm, nparams, mom);
     case OR_DYNLO: return dynlo_point(ndim, x, prm, mom);

@@ -26,6 +26,9 @@ DY_PARAMS = (14000.0, 91.1876, 2.4952, 0.2312, 1.0 / 128.0, 60.0, 120.0, -0.5, 3
 # indices of (M_Z, Gamma_Z, sin^2 theta_W, a, b) inside DY_PARAMS
 DY_GRAD_INDEX = (1, 2, 3, 7, 8)
 GAUSS_PARAMS = (0.1,)
+# the Gaussian minus a constant 0.1: negative weights over most of the cube
+# (as subtraction terms give at NLO), a negative integral in d = 2
+GAUSS_SHIFTED_PARAMS = (0.1, 0.1)
 # NLO-shaped stand-in: the Drell-Yan parameters, then beta of the extra axes'
 # factors exp(beta cos 2 pi x) / I0(beta)
 DYNLO_PARAMS = DY_PARAMS + (0.5,)

@@ -14,7 +14,8 @@ import numpy as np
 import pytest
 
 import refs
-from paper_1503_06182_gb300.workloads import DY_PARAMS, DYNLO_PARAMS, EE3J_PARAMS, GAUSS_PARAMS
+from paper_1503_06182_gb300.workloads import (DY_PARAMS, DYNLO_PARAMS, EE3J_PARAMS, GAUSS_PARAMS,
+                                              GAUSS_SHIFTED_PARAMS)
 
 
 def _two_stage(o, ndim, nbins, iid, params, ncall, warm, prod, seed, hist):
@@ -125,6 +126,7 @@ def test_hist_combine_hand_values(oracle_mod):
     (1, DY_PARAMS, 4, (30, 70.0, 110.0)),
     (2, EE3J_PARAMS, 5, (10, 2 / 3, 1.0)),
     (3, DYNLO_PARAMS, 7, (12, 60.0, 120.0)),
+    (0, GAUSS_SHIFTED_PARAMS, 2, (16, 0.1, 0.9)),
 ])
 def test_hist_adds_up_to_the_integral(oracle_mod, iid, params, ndim, hist):
     """Bins including underflow and overflow add up to the combined integral
@@ -227,3 +229,20 @@ def test_ee3j_thrust_against_closed_form(oracle_mod):
     exact = [0.0] + [refs.ee3j_thrust_bin(lo + j * w, lo + (j + 1) * w, y)
                      for j in range(nh)] + [0.0]
     _pulls_ok(r.hist_value, r.hist_error, exact)
+
+
+def test_shifted_gauss_signed_weights(oracle_mod):
+    """The Gaussian minus a constant: mostly negative weights.  The integral
+    is the closed form minus the constant; each x_0 bin is its erf integral
+    minus the constant times the bin width; negative bins come out negative."""
+    sigma, shift = GAUSS_SHIFTED_PARAMS
+    nh, lo, hi = 10, 0.0, 1.0
+    r = _two_stage(oracle_mod, 2, 50, oracle_mod.GAUSS, GAUSS_SHIFTED_PARAMS, 200_000, 3, 5,
+                   1234, (nh, lo, hi))
+    exact = refs.gauss_exact(2, sigma) - shift
+    assert exact < 0 and abs(r.integral - exact) < 4.5 * r.error
+    w = (hi - lo) / nh
+    bins = [0.0] + [refs.gauss_bin(lo + j * w, lo + (j + 1) * w, 2, sigma) - shift * w
+                    for j in range(nh)] + [0.0]
+    _pulls_ok(r.hist_value, r.hist_error, bins)
+    assert r.hist_value[1] < 0 < r.hist_value[5]
