@@ -305,7 +305,8 @@ def forms(v, stream, seed):
     bench stream (device time between CUDA events; L2 not flushed inside a
     stage, as in a real run): 3-jet 10 x 1e7 FP32; Drell-Yan adjoint 10 x 1e8
     FP32 on a frozen grid; 64 batched integrations x 10 iterations (one graph);
-    the plain FP64 Gauss case 5 x 1e5."""
+    the plain FP64 Gauss case 5 x 1e5; the NLO-shaped 13-axis case 10 x 1e6
+    FP32; Drell-Yan 10 x 1e6 FP32 filling a 60-bin m_ll histogram."""
     import torch
 
     from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, DYNLO, DYNLO_PARAMS, EE3J,
@@ -321,13 +322,17 @@ def forms(v, stream, seed):
         return a.elapsed_time(b), out
 
     res = {}
-    for name, (iid, params, d, n, ncall, itmx, prec) in {
-            "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32"),
-            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64"),
+    for name, (iid, params, d, n, ncall, itmx, prec, hist) in {
+            "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32", None),
+            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64", None),
             "dy_nlo_shaped_d13_n50_10x1e6_fp32": (DYNLO, DYNLO_PARAMS, 13, 50, 1_000_000, 10,
-                                                  "fp32")}.items():
+                                                  "fp32", None),
+            "dy_mll_hist60_d4_n100_10x1e6_fp32": (DY, DY_PARAMS, 4, 100, 1_000_000, 10, "fp32",
+                                                  (60, 60.0, 120.0))}.items():
         g = v.Vegas(d, n, seed, precision=prec)
         v.vegas_set_stream(g.h, stream.cuda_stream)
+        if hist:
+            g.hist_set(*hist)
         try:
             g.iterate(ncall, itmx, iid, params)  # warm-up stage (adapts, tunes, captures)
             ms, (I, e, c, _, _) = timed(lambda: g.iterate(ncall, itmx, iid, params))

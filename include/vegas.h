@@ -45,7 +45,8 @@ extern "C" {
 #define VEGAS_ESTATE (-7)     /* checkpoint buffer does not match this context */
 
 /* ---- integrands (synthetic stand-ins for the paper's H+2 jets, Section 3.2) ---- */
-#define VEGAS_GAUSS 0 /* params[1]: sigma.  g = prod_a exp(-(x_a-1/2)^2/(2 sigma^2)); ndim >= 1 */
+#define VEGAS_GAUSS 0 /* params[1] or [2]: sigma [, shift].  g = prod_a exp(-(x_a-1/2)^2/(2 sigma^2))
+                         - shift (shift 0 if not given; weights can then be negative); ndim >= 1 */
 #define VEGAS_DY 1    /* params[10]: sqrt_s, M_Z, Gamma_Z, sin2_thetaW, alpha, m_lo, m_hi, a, b, N.
                          LO pp -> gamma*,Z -> mu+ mu- in pb with toy densities
                          f_q = N x^a (1-x)^b, f_qbar = 0.2 N x^a (1-x)^(b+4); ndim >= 4 */
@@ -205,6 +206,37 @@ int vegas_rng_words_noalloc(uint64_t seed, uint32_t iteration, uint32_t batch,
 /* FP64 sums of the last iteration: (sum w, sum w^2, d[ndim*nbins]), with
  * d[a*nbins + i] = sum of w^2 over the events in bin i of axis a. */
 int vegas_last_sums(const vegas_ctx* ctx, double* sums);
+
+/* Histogram of an observable, filled while integrating (the differential
+ * distributions of Section 3.2, there the di-jet mass; here one observable
+ * per integrand):
+ *   VEGAS_GAUSS: x_0;  VEGAS_DY and VEGAS_DY_NLO: the dilepton mass
+ *   m_ll = sqrt(tau s) in GeV;  VEGAS_EE3J: the thrust max(x1, x2, x3).
+ * vegas_hist_set(ctx, nbins, lo, hi): nbins equal bins over [lo, hi)
+ * (1 <= nbins <= VEGAS_HIST_MAX_BINS, finite lo < hi), plus an underflow bin
+ * (below lo, or not a number) and an overflow bin (hi and above): the bin of
+ * a value v >= lo is 1 + trunc((v - lo) * (nbins / (hi - lo))), computed in
+ * the integrand's precision (FP32 in the FP32 form).  nbins = 0 switches the
+ * histogram off.  Every later vegas_iterate / vegas_launch stage fills it:
+ * per iteration k and bin b, H_kb = sum_{events in b} w / C and
+ * V_kb = (sum_{b} w^2 / C - H_kb^2)/(C-1), from sums that are exact integer
+ * sums rounded once to FP64 (so bit-identical for every launch shape); the
+ * stage's iterations are combined with the weights of the integral,
+ * u_k = 1/sigma_k^2 (or, if any sigma_k is 0, 1 for those iterations and 0
+ * for the others):
+ *   value_b = sum_k u_k H_kb / sum_k u_k,
+ *   error_b = sqrt(sum_k u_k^2 V_kb) / sum_k u_k,
+ * so the nbins + 2 values add up to the stage's integral.  With a histogram
+ * the fill runs at 4 events per thread (VEGAS_OPT_EPT is not used).  The
+ * histogram is not part of a checkpoint, and vegas_adjoint does not fill it.
+ * vegas_hist_get(ctx, value, error, last_sums): after such a stage (blocks
+ * until it is done), copies value and error (nbins + 2 each, underflow first,
+ * overflow last) and last_sums (2 x (nbins + 2): the last iteration's sum w
+ * per bin, then its sum w^2); any pointer may be NULL.  EINVAL if no
+ * histogram is set, or the last stage did not fill it. */
+#define VEGAS_HIST_MAX_BINS 1000
+int vegas_hist_set(vegas_ctx* ctx, int nbins, double lo, double hi);
+int vegas_hist_get(vegas_ctx* ctx, double* value, double* error, double* last_sums);
 
 /* Accumulated device time of the VEGAS_KERNEL_* kernels since the last
  * reset (VEGAS_OPT_TIMING = 1 only); reset != 0 clears that kernel's totals

@@ -78,7 +78,7 @@ int check_params(int ig, int ndim, const double* p, int np) {
     if (!std::isfinite(p[i])) return VEGAS_EINVAL;
   switch (ig) {
     case VEGAS_GAUSS:
-      if (np != 1 || ndim < 1 || !(p[0] > 0.0)) return VEGAS_EINVAL;
+      if ((np != 1 && np != 2) || ndim < 1 || !(p[0] > 0.0)) return VEGAS_EINVAL;
       return VEGAS_OK;
     case VEGAS_DY:
       if (np != 10 || ndim < 4) return VEGAS_EINVAL;
@@ -144,6 +144,13 @@ struct vegas_ctx {
   double* logtab = nullptr;
   int* tickets = nullptr;  // reduce tickets (zero between iterations)
   int nacc_max = 0;
+  // histogram of the observable (hist_nh = 0: none); hist_valid: the last
+  // stage filled it
+  int hist_nh = 0;
+  double hist_lo = 0.0, hist_hi = 0.0;
+  double* hist_acc = nullptr;  // [4][GV_HIST_MAX + 2]
+  double* hist_out = nullptr;  // [2][GV_HIST_MAX + 2]
+  bool hist_valid = false;
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -177,10 +184,10 @@ void clear_graphs(vegas_ctx* c) {
 
 size_t grid_doubles(int d, int N) { return GvGridLayout{d, N}.doubles(); }
 
-size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode) {
+size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhist) {
   const int64_t n_tiles = (ncall + GV_TILE - 1) / GV_TILE;
   const int nch = mode ? GV_MAXCH : 1;
-  const int nacc = mode ? 2 * GV_MAXCH : 2 + d * N;
+  const int nacc = mode ? 2 * GV_MAXCH : 2 + d * N + 2 * nhist;
   int tpc = 0, gx = 0, gy = 0;
   gv::reduce_grid((int)std::min<int64_t>(n_tiles, 0x7fffffff), nacc, &tpc, &gx, &gy);
   size_t b = align256((size_t)n_tiles * nacc * 16);
@@ -225,6 +232,7 @@ int ensure_pinned(vegas_ctx* c, size_t need) {
 
 struct Plan {
   int ig, fp32, mode, itmx, n_tiles, nacc, nch, ept, reduce_ctas, tiles_per_cta;
+  int nhist;  // histogram bins with underflow and overflow (0: none)
   int64_t ncall;
   size_t smem;
   ulonglong2* part;
@@ -247,7 +255,29 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   a.st = c->st;
   a.part = p.part;
   a.tileE = p.tileE;
+  a.nhist = p.nhist;
+  if (p.nhist) {
+    const double invw = (double)c->hist_nh / (c->hist_hi - c->hist_lo);
+    a.h_lo = c->hist_lo;
+    a.h_invw = invw;
+    a.h_lo_f = (float)c->hist_lo;
+    a.h_invw_f = (float)invw;
+  }
   return a;
+}
+
+GvHistArgs hist_args(const vegas_ctx* c, const Plan& p, int k) {
+  GvHistArgs h;
+  h.sums = c->sums + 2 + (size_t)c->ndim * c->nbins;
+  h.per_iter = p.per_iter;
+  h.nhist = p.nhist;
+  h.k = k;
+  h.last = k == p.itmx - 1;
+  h.inv_c = 1.0 / (double)p.ncall;
+  h.inv_cm1 = 1.0 / (double)(p.ncall - 1);
+  h.acc = c->hist_acc;
+  h.out = c->hist_out;
+  return h;
 }
 
 GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
@@ -257,6 +287,7 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.nch = p.nch;
   r.nacc = p.nacc;
   r.has_bins = p.mode == 0;
+  r.nhist = p.nhist;
   r.k = k;
   r.last = k == p.itmx - 1;
   r.refine_follows = (p.mode == 0 && c->adapt) ? 1 : 0;
@@ -299,6 +330,7 @@ int ensure_consts(vegas_ctx* c, int ig, const double* params, int np) {
 cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pdl = false) {
   const GvFillArgs a = fill_args(c, p);
   if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
+  if (p.nhist) return gv::launch_fill_hist(p.ig, p.fp32, a, p.n_tiles, p.smem, c->stream, pdl);
   return launch_fill_any(p.ig, p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
 }
 
@@ -367,12 +399,13 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   if (nt > 0x7fffffff) return VEGAS_EINVAL;
   p.n_tiles = (int)nt;
   p.nch = mode ? GV_MAXCH : 1;
-  p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins;
-  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4).total;
+  p.nhist = (mode == 0 && c->hist_nh > 0) ? c->hist_nh + 2 : 0;
+  p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins + 2 * p.nhist;
+  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist).total;
   int gx = 0, gy = 0;
   gv::reduce_grid(p.n_tiles, p.nacc, &p.tiles_per_cta, &gx, &gy);
   p.reduce_ctas = gx * gy;
-  const size_t need = workspace_bytes(c->ndim, c->nbins, ncall, itmx, mode);
+  const size_t need = workspace_bytes(c->ndim, c->nbins, ncall, itmx, mode, p.nhist);
   int st = ensure_workspace(c, need);
   if (st) return st;
   char* w = (char*)c->ws;
@@ -398,6 +431,7 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
     GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
+    if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
   return VEGAS_OK;
@@ -440,10 +474,13 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   if (st) return st;
   st = ensure_consts(c, ig, params, np);
   if (st) return st;
-  if (p.ept == 0) {
+  if (p.nhist) {
+    p.ept = 4;  // the histogram fill has one shape
+  } else if (p.ept == 0) {
     st = autotune(c, p);
     if (st) return st;
   }
+  c->hist_valid = p.nhist > 0;
   c->last_itmx = itmx;
   c->last_mode = mode;
   c->last_ept = p.ept;
@@ -472,10 +509,11 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
     c->pending = true;
     return VEGAS_OK;
   }
-  char kb[320];
-  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d%d:%llu:%u:%p:%p", ig, p.fp32, mode,
-           (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing, c->pdl,
-           (unsigned long long)c->seed, c->batch, c->ws, (void*)c->stream);
+  char kb[400];
+  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d%d:%llu:%u:%p:%p:h%d:%a:%a", ig, p.fp32,
+           mode, (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing, c->pdl,
+           (unsigned long long)c->seed, c->batch, c->ws, (void*)c->stream, p.nhist, c->hist_lo,
+           c->hist_hi);
   const std::string key(kb);
   GraphEntry* ge = find_entry(c, key);
   if (!ge) {
@@ -633,8 +671,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
     return VEGAS_ECUDA;
   }
   c->own_stream = true;
-  // slots: channel sums, bin sums
-  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins);
+  // slots: channel sums, bin sums, the largest histogram's sums
+  c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins + 2 * (GV_HIST_MAX + 2));
   const size_t gd = grid_doubles(ndim, nbins);
   size_t off = 0;
   const size_t o_grid = off;
@@ -651,6 +689,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   off = align256(off + (size_t)c->nacc_max * 8);
   const size_t o_tick = off;
   off = align256(off + gv_tickets_ints(c->nacc_max) * 4);
+  const size_t o_hist = off;
+  off = align256(off + (size_t)6 * (GV_HIST_MAX + 2) * 8);
   if (cudaMalloc(&c->fixed, off) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(c->stream);
@@ -665,6 +705,8 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   c->sums = (double*)(b + o_sums);
   c->logtab = (double*)(b + o_log);
   c->tickets = (int*)(b + o_tick);
+  c->hist_acc = (double*)(b + o_hist);
+  c->hist_out = c->hist_acc + 4 * (GV_HIST_MAX + 2);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess ||
       gv::launch_reset(c->st, c->stream) != cudaSuccess)
@@ -754,8 +796,39 @@ int vegas_set_stream(vegas_ctx* c, void* stream) {
 
 int vegas_workspace_size(const vegas_ctx* c, int64_t ncall, int itmx, size_t* bytes) {
   if (!c || !bytes || ncall < 2 || itmx < 1) return VEGAS_EINVAL;
-  *bytes = std::max(workspace_bytes(c->ndim, c->nbins, ncall, itmx, 0),
-                    workspace_bytes(c->ndim, c->nbins, ncall, itmx, 1));
+  const int nhist = c->hist_nh > 0 ? c->hist_nh + 2 : 0;
+  *bytes = std::max(workspace_bytes(c->ndim, c->nbins, ncall, itmx, 0, nhist),
+                    workspace_bytes(c->ndim, c->nbins, ncall, itmx, 1, 0));
+  return VEGAS_OK;
+}
+
+int vegas_hist_set(vegas_ctx* c, int nbins, double lo, double hi) {
+  if (!c || nbins < 0 || nbins > VEGAS_HIST_MAX_BINS) return VEGAS_EINVAL;
+  if (nbins > 0 && !(std::isfinite(lo) && std::isfinite(hi) && hi > lo &&
+                     std::isfinite((double)nbins / (hi - lo))))
+    return VEGAS_EINVAL;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  clear_graphs(c);
+  c->hist_nh = nbins;
+  c->hist_lo = nbins > 0 ? lo : 0.0;
+  c->hist_hi = nbins > 0 ? hi : 0.0;
+  c->hist_valid = false;
+  return VEGAS_OK;
+}
+
+int vegas_hist_get(vegas_ctx* c, double* value, double* error, double* last_sums) {
+  if (!c || c->hist_nh <= 0 || !c->hist_valid) return VEGAS_EINVAL;
+  const size_t hb = (size_t)c->hist_nh + 2;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  if (value) GV_TRY(cudaMemcpy(value, c->hist_out, hb * sizeof(double), cudaMemcpyDeviceToHost));
+  if (error)
+    GV_TRY(cudaMemcpy(error, c->hist_out + hb, hb * sizeof(double), cudaMemcpyDeviceToHost));
+  if (last_sums) {
+    // device order: sum w^2 per bin, then sum w; returned as sum w, then sum w^2
+    const double* d = c->sums + 2 + (size_t)c->ndim * c->nbins;
+    GV_TRY(cudaMemcpy(last_sums, d + hb, hb * sizeof(double), cudaMemcpyDeviceToHost));
+    GV_TRY(cudaMemcpy(last_sums + hb, d, hb * sizeof(double), cudaMemcpyDeviceToHost));
+  }
   return VEGAS_OK;
 }
 

@@ -46,6 +46,7 @@
 #define GV_BIN_QBITS 56       // bits of one w^2 below its bin's scale in a tile
 #define GV_BIN_XBITS 32       // extra low bits of the iteration's bin sums
 #define GV_BIN_FB (GV_BIN_QBITS + GV_BIN_XBITS)  // bin sums in units of 2^(2F - GV_BIN_FB)
+#define GV_HIST_MAX 1000      // histogram bins of the observable (plus underflow and overflow)
 
 enum { GV_GAUSS = 0, GV_DY = 1, GV_EE3J = 2, GV_DYNLO = 3 };
 
@@ -95,6 +96,12 @@ struct GvFillArgs {
   GvState* st;
   ulonglong2* part;              // [tile][nacc] 128-bit two's complement sums
   int* tileE;                    // [tile][nch] scales
+  // histogram of the integrand's observable (forward fill only): nhist bins,
+  // 0 = underflow, nhist - 1 = overflow (nhist = 0: no histogram); the bin of
+  // a value v >= lo is 1 + trunc((v - lo) invw), in the integrand's precision
+  int nhist = 0;
+  double h_lo = 0.0, h_invw = 0.0;
+  float h_lo_f = 0.0f, h_invw_f = 0.0f;
 };
 
 // One slot's sum as a 192-bit two's complement integer with its exponent:
@@ -122,8 +129,11 @@ __host__ __device__ inline size_t gv_tickets_ints(int nacc) {
 
 // Arguments of the reduce/finalize kernel.
 // Slots: [0, 2*nch) channel sums, then (forward) ndim*nbins bin sums.
+// Slots: [2 nch channel sums | ndim * nbins bin sums of w^2 | nhist
+// histogram sums of w^2 | nhist histogram sums of w (signed)].
 struct GvReduceArgs {
   int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
+  int nhist = 0;                 // histogram bins (0: none)
   int refine_follows;            // 1: each axis is refined by the CTA that completes it
   long long ncall;
   double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration
@@ -393,12 +403,27 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 // ----------------------------------------------------------------------------
 // Host-side launchers (defined in the kernel translation units).
 // ----------------------------------------------------------------------------
+// Histogram of the observable after an iteration's reduce: the iteration's
+// bin estimates from the once-rounded sums, accumulated over the call's
+// iterations; the combined histogram at the last one.
+struct GvHistArgs {
+  const double* sums;      // [2][nhist]: sum w^2, then sum w, per bin
+  const double* per_iter;  // [itmx][2] (I_k, sigma_k)
+  int nhist, k, last;
+  double inv_c, inv_cm1;
+  double* acc;             // [4][nhist] running sums of the call (see gv_hist_kernel)
+  double* out;             // [2][nhist] value, error (written at the last iteration)
+};
+
 namespace gv {
 cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
                                 size_t smem, cudaStream_t s, bool pdl);
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
 size_t reduce_smem_bytes(int N);  // dynamic shared memory of the reduce kernels
 cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl);
+cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s);
+cudaError_t launch_fill_hist(int ig, int fp32, const GvFillArgs& a, int n_tiles, size_t smem,
+                             cudaStream_t s, bool pdl);
 cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
                                 int last, double inv_m1, size_t smem, cudaStream_t s);
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);

@@ -14,6 +14,11 @@
 //           as four 22-bit limbs in 32-bit shared-memory atomics (32-bit
 //           shared atomics run several times faster than 64-bit ones here,
 //           and 10 bits of headroom cover the 1024 events of a tile).
+// With a histogram of the observable (HIST), every event with w != 0 also
+// adds w and w^2 to its observable's bin, in the same limb scheme: a per-bin
+// exponent from pass 1, then w^2 as three unsigned 22-bit limbs and w as two
+// unsigned limbs and a signed top limb (two's complement, so negative weights
+// add like positive ones).
 // Integer sums are order-free, so the tile's result is the same for every
 // block size / events-per-thread choice.  Apart from the Jacobian product and
 // w = J g, the bookkeeping runs on the integer pipes: the FP64 pipe of this
@@ -25,7 +30,7 @@ template <int IG>
 struct GvTraits;
 template <>
 struct GvTraits<GV_GAUSS> {
-  static constexpr int NK = 1;
+  static constexpr int NK = 2;
 };
 template <>
 struct GvTraits<GV_DY> {
@@ -44,7 +49,7 @@ template <int IG, typename Real, int MAXD>
 __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
                                         const GvConst<Real, GvTraits<IG>::NK>& K) {
   if constexpr (IG == GV_GAUSS) {
-    return gv_gauss<Real, MAXD>(x, d, K[GK_INV2S2]);
+    return gv_gauss<Real, MAXD>(x, d, K[GK_INV2S2], K[GK_SHIFT]);
   } else if constexpr (IG == GV_DY) {
     return gv_drell_yan<Real, false>(x, K, nullptr);
   } else if constexpr (IG == GV_DYNLO) {
@@ -52,6 +57,50 @@ __device__ __forceinline__ Real gv_eval(const Real (&x)[MAXD], int d,
   } else {
     return gv_ee3j<Real>(x, K);
   }
+}
+
+// The histogram observable of an event (the differential distributions of
+// Section 3.2): Gauss x_0; Drell-Yan (both forms) the dilepton mass
+// m_ll = sqrt(tau s) in GeV, with tau as the integrand forms it; 3-jet the
+// thrust max(x1, x2, x3), x3 = 2 - x1 - x2.
+template <int IG, typename Real, int MAXD>
+__device__ __forceinline__ Real gv_observable(const Real (&x)[MAXD],
+                                              const GvConst<Real, GvTraits<IG>::NK>& K) {
+  using Mt = GvMath<Real>;
+  if constexpr (IG == GV_GAUSS) {
+    return x[0];
+  } else if constexpr (IG == GV_DY || IG == GV_DYNLO) {
+    const Real tau = Mt::exp(Mt::fma(x[0], K[DK_L], K[DK_LOGTAULO]));
+    return Mt::sqrt(tau * K[DK_S]);
+  } else {
+    const Real x1 = x[0], x2 = x[1], x3 = (Real)2 - x1 - x2;
+    const Real t = x1 > x2 ? x1 : x2;
+    return t > x3 ? t : x3;
+  }
+}
+
+// Histogram bin of v among nh bins over [lo, lo + nh / invw): 0 below (and
+// for a value that is not a number), nh + 1 above.
+template <typename Real>
+__device__ __forceinline__ int gv_hist_bin(Real v, Real lo, Real invw, int nh) {
+  if (!(v >= lo)) return 0;
+  const Real t = (v - lo) * invw;
+  if (!(t < (Real)nh)) return nh + 1;
+  return 1 + (int)t;
+}
+
+// |w| rounded to a multiple of 2^(Fs - GV_BIN_QBITS), Fs the bin's scale
+// (|w| < 2^Fs), with w's sign: |result| < 2^56.
+__device__ __forceinline__ long long gv_hist_fixed(const GvDecoded& dw, int Fs) {
+  const int r = Fs - GV_BIN_QBITS - dw.e2;  // right shift of the mantissa (>= -55)
+  unsigned long long q;
+  if (r <= 0)
+    q = dw.m << (-r);
+  else if (r < 64)
+    q = ((dw.m >> (r - 1)) + 1ull) >> 1;
+  else
+    q = 0ull;
+  return dw.neg ? -(long long)q : (long long)q;
 }
 
 // One bin of one axis as staged in shared memory.
@@ -148,17 +197,21 @@ struct GvPair<double> {
 //   jac  [d*N]    f64     Jacobian factor N*(e_{i+1}-e_i) (FP64 form only)
 //   ew   [d*N]    GvBin32 (e, w, jm, je) in the FP32 form, GvBin64 (e, w) in FP64
 //   bins [d][GV_TILE] u16 (forward kernels of the d > 4 classes only)
+//   hh   [7][nhist] u32   histogram: w^2 limbs [3], w limbs [3] (the third
+//                         signed), the tile's bin exponents (with a histogram)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 struct GvFillSmem {
-  size_t hist, jac, ew, bins, total;
-  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem) {
+  size_t hist, jac, ew, bins, hh, total;
+  __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem,
+                                 int nhist = 0) {
     const size_t dN = (size_t)d * N;
     hist = 0;
     jac = gv_align16(hist + (forward ? dN * 16 : 0));
     ew = gv_align16(jac + (real_bytes == 8 ? dN * 8 : 0));
     bins = gv_align16(ew + dN * 16);
-    total = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
+    hh = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
+    total = gv_align16(hh + (forward ? (size_t)nhist * 7 * 4 : 0));
   }
 };
 
@@ -294,7 +347,7 @@ __device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
 // the persistent batched kernel, so that a tile's partial is the same
 // whichever kernel computes it.
 // ---------------------------------------------------------------------------
-template <int IG, typename Real, int EPT, int MAXD>
+template <int IG, typename Real, int EPT, int MAXD, bool HIST = false>
 __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile,
                                              unsigned char* smem, unsigned long long* red_u64,
                                              u128* red_128, uint32_t it) {
@@ -302,7 +355,19 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   constexpr int NW = B / 32;
   using Pair = typename GvPair<Real>::T;
   const int d = a.ndim, N = a.nbins, dN = d * N;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4);
+  const int hb = HIST ? a.nhist : 0;
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, hb);
+  unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);  // [6][hb] limbs
+  int* hebin = reinterpret_cast<int*>(hh + 6 * hb);             // [hb] exponents
+  Real h_lo, h_invw;
+  if constexpr (sizeof(Real) == 4) {
+    h_lo = a.h_lo_f;
+    h_invw = a.h_invw_f;
+  } else {
+    h_lo = a.h_lo;
+    h_invw = a.h_invw;
+  }
+  int hbin[EPT];
   unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);  // [3][dN] limbs
   int* ebin = reinterpret_cast<int*>(hist + 3 * dN);               // [dN] exponents
   const double* s_jac = reinterpret_cast<const double*>(smem + lay.jac);
@@ -322,6 +387,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     const int local = k * B + tid;
     const long long ev = tile0 + local;
     w[k] = 0.0;
+    hbin[k] = 0;
     if (ev < a.ncall) {
       uint32_t r[MAXD];
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
@@ -330,6 +396,8 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
       bs[k].put(bin, d, s_bin, local);
       const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
+      if constexpr (HIST) hbin[k] = gv_hist_bin<Real>(gv_observable<IG, Real, MAXD>(x, K), h_lo,
+                                                      h_invw, hb - 2);
       const double wv = gv_weight(J, g);
       const unsigned long long ab = gv_abs_bits(wv);
       if (gv_finite_bits(ab)) {
@@ -340,6 +408,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
 #pragma unroll
           for (int ax = 0; ax < MAXD; ++ax)
             if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
+          if constexpr (HIST) atomicMax(hebin + hbin[k], F);
         }
       } else {
         ++nbad;  // counted, contributes nothing
@@ -374,6 +443,25 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
             if (l2) atomicAdd(hist + 2 * dN + bi, l2);
           }
         }
+        if constexpr (HIST) {
+          // the observable's bin: w^2 as the axis bins, then w (signed)
+          const int hk = hbin[k];
+          const int Fh = hebin[hk];
+          const unsigned long long q = gv_square_bin(P, 2 * Fh - c);
+          const unsigned l0 = (unsigned)(q & 0x3FFFFFull);
+          const unsigned l1 = (unsigned)((q >> 22) & 0x3FFFFFull);
+          const unsigned l2 = (unsigned)(q >> 44);
+          if (l0) atomicAdd(hh + hk, l0);
+          if (l1) atomicAdd(hh + hb + hk, l1);
+          if (l2) atomicAdd(hh + 2 * hb + hk, l2);
+          const long long v = gv_hist_fixed(dw, Fh - GV_BINE_OFF);
+          const unsigned m0 = (unsigned)((unsigned long long)v & 0x3FFFFFull);
+          const unsigned m1 = (unsigned)(((unsigned long long)v >> 22) & 0x3FFFFFull);
+          const unsigned m2 = (unsigned)(int)(v >> 44);  // signed, |v >> 44| <= 2^12
+          if (m0) atomicAdd(hh + 3 * hb + hk, m0);
+          if (m1) atomicAdd(hh + 4 * hb + hk, m1);
+          if (m2) atomicAdd(hh + 5 * hb + hk, m2);
+        }
       }
     }
   }
@@ -396,9 +484,28 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     v = add128(v, u128{l2 << 44, l2 >> 20});
     out[2 + k] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)ebin[k] << 32));
   }
+  if constexpr (HIST) {
+    for (int k = tid; k < hb; k += B) {
+      const unsigned long long eh = (unsigned long long)(unsigned)hebin[k] << 32;
+      // w^2: as the axis bins
+      const unsigned long long l0 = hh[k], l1 = hh[hb + k], l2 = hh[2 * hb + k];
+      u128 v = {l0, 0ull};
+      v = add128(v, u128{l1 << 22, l1 >> 42});
+      v = add128(v, u128{l2 << 44, l2 >> 20});
+      out[2 + dN + k] = make_ulonglong2(v.lo, v.hi | eh);
+      // w: M = m0 + m1 2^22 + m2 2^44 with m2 signed (|M| < 2^67) as a 96-bit
+      // two's complement value in units of 2^(F_tb - GV_BIN_QBITS)
+      const unsigned long long m0 = hh[3 * hb + k], m1 = hh[4 * hb + k];
+      const long long m2 = (long long)(int)hh[5 * hb + k];
+      u128 t = {m0, 0ull};
+      t = add128(t, u128{m1 << 22, m1 >> 42});
+      t = add128(t, u128{(unsigned long long)m2 << 44, (unsigned long long)(m2 >> 20)});
+      out[2 + dN + hb + k] = make_ulonglong2(t.lo, (t.hi & 0xFFFFFFFFull) | eh);
+    }
+  }
 }
 
-template <int IG, typename Real, int EPT, int MAXD>
+template <int IG, typename Real, int EPT, int MAXD, bool HIST = false>
 __global__ void __launch_bounds__(GV_TILE / EPT)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
@@ -407,15 +514,19 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4);
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
   for (int k = threadIdx.x; k < 4 * d * N; k += B) hist[k] = 0u;
+  if constexpr (HIST) {
+    unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);
+    for (int k = threadIdx.x; k < 7 * a.nhist; k += B) hh[k] = 0u;
+  }
   gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
   gv_stage_grid<Real>(a.grid, d, N, reinterpret_cast<double*>(smem + lay.jac),
                       reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew), threadIdx.x, B);
   const uint32_t it = (uint32_t)a.st->it;
   __syncthreads();
-  gv_fill_tile<IG, Real, EPT, MAXD>(a, blockIdx.x, smem, red_u64, red_128, it);
+  gv_fill_tile<IG, Real, EPT, MAXD, HIST>(a, blockIdx.x, smem, red_u64, red_128, it);
 }
 
 // ---------------------------------------------------------------------------

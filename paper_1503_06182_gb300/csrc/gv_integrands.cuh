@@ -20,6 +20,7 @@
 // Derived constants (filled by the setup kernel from the user parameters).
 // Gaussian
 #define GK_INV2S2 0
+#define GK_SHIFT 1      // constant subtracted from the product (0 by default)
 // Drell-Yan
 #define DK_SQRTS 0
 #define DK_S 1
@@ -105,10 +106,11 @@ struct GvConst {
 };
 
 // ---------------------------------------------------------------------------
-// Gaussian product: g = exp(-sum_a (x_a - 1/2)^2 / (2 sigma^2)).
+// Gaussian product minus a constant: g = exp(-sum_a (x_a - 1/2)^2 / (2 sigma^2))
+// - shift (shift = 0 unless given: negative weights, as NLO subtractions give).
 // ---------------------------------------------------------------------------
 template <typename Real, int MAXD>
-__device__ __forceinline__ Real gv_gauss(const Real (&x)[MAXD], int d, Real inv2s2) {
+__device__ __forceinline__ Real gv_gauss(const Real (&x)[MAXD], int d, Real inv2s2, Real shift) {
   Real acc = (Real)0;
 #pragma unroll
   for (int a = 0; a < MAXD; ++a) {
@@ -117,7 +119,7 @@ __device__ __forceinline__ Real gv_gauss(const Real (&x)[MAXD], int d, Real inv2
       acc = GvMath<Real>::fma(dx, dx, acc);
     }
   }
-  return GvMath<Real>::exp(-acc * inv2s2);
+  return GvMath<Real>::exp(-acc * inv2s2) - shift;
 }
 
 // ---------------------------------------------------------------------------

@@ -163,8 +163,6 @@ __device__ double u192_to_double(u192 v, int q) {
   return neg ? -r : r;
 }
 
-// Stored bin exponent (GV_BINE_OFF-offset, 0 = empty) -> q of u192_to_double.
-__device__ __forceinline__ int bin_q(int g) { return 2 * (g - GV_BINE_OFF) - GV_BIN_FB; }
 
 // Barrier of a group of nthr threads (a multiple of 32); id 0 is the whole CTA.
 __device__ __forceinline__ void gv_bar(int id, int nthr) {
@@ -504,13 +502,20 @@ __host__ __device__ inline int gv_axes_per_block(int N) {
 #define GV_RED_TILES_PER_LOAD 8
 
 // A tile partial of slot k aligned to exponent em (>= its own exponent e).
-// Channel slots: 128-bit two's complement at 2^(pw e - GV_FB); bin slots:
-// Q (< 2^67) at 2^(2 (e - GV_BINE_OFF) - GV_BIN_QBITS), with GV_BIN_XBITS
-// more low bits in the sums.
-__device__ __forceinline__ u192 align_tile(ulonglong2 v, int e, int em, bool bin, int pw) {
+// Channel slots: 128-bit two's complement at 2^(pw e - GV_FB); bin slots
+// (axis bins and histogram bins): a 96-bit value, unsigned Q (< 2^67) for
+// sums of w^2 (pw = 2) or two's complement for the histogram's sums of w
+// (pw = 1, sgn), at 2^(pw (e - GV_BINE_OFF) - GV_BIN_QBITS), with
+// GV_BIN_XBITS more low bits in the sums.
+__device__ __forceinline__ u192 align_tile(ulonglong2 v, int e, int em, bool bin, int pw,
+                                           bool sgn = false) {
   if (bin) {
-    const u192 x = {v.x, v.y & 0xFFFFFFFFull, 0ull};
-    const int sh = 2 * (em - e) - GV_BIN_XBITS;
+    const unsigned long long ext = sgn ? (unsigned long long)((long long)(int)(unsigned)v.y >> 63)
+                                       : 0ull;
+    const u192 x = {v.x, sgn ? (unsigned long long)(long long)(int)(unsigned)v.y
+                             : (v.y & 0xFFFFFFFFull),
+                    ext};
+    const int sh = pw * (em - e) - GV_BIN_XBITS;
     return sh < 0 ? shl192(x, -sh) : sar192(x, sh);
   }
   const u192 x = {v.x, v.y, (unsigned long long)((long long)v.y >> 63)};
@@ -538,7 +543,9 @@ __device__ __forceinline__ void gv_reduce_task(const GvReduceArgs& a, int bx, in
   const int t0 = by * a.tiles_per_cta;
   const int t1 = min(a.n_tiles, t0 + a.tiles_per_cta);
   const bool bin = a.has_bins && k >= 2 * a.nch;
-  const int pw = bin ? 2 : (k & 1) + 1;
+  // the histogram's sums of w: the last nhist slots
+  const bool hw = bin && a.nhist > 0 && k >= a.nacc - a.nhist;
+  const int pw = hw ? 1 : (bin ? 2 : (k & 1) + 1);
   const int empty = bin ? 0 : GV_EMPTY;
   const int ch = k >> 1;
   constexpr int G = GV_RED_TILES_PER_LOAD;
@@ -577,12 +584,12 @@ __device__ __forceinline__ void gv_reduce_task(const GvReduceArgs& a, int bx, in
     if (cached) {
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        if (et[g] != empty && (v[g].x | v[g].y)) add192(r, align_tile(v[g], et[g], em, bin, pw));
+        if (et[g] != empty && (v[g].x | v[g].y)) add192(r, align_tile(v[g], et[g], em, bin, pw, hw));
     } else {
       for (int t = t0 + wid; t < t1; t += 8) {
         const ulonglong2 x = a.part[(size_t)t * a.nacc + k];
         const int e = bin ? (int)(x.y >> 32) : a.tileE[(size_t)t * a.nch + ch];
-        if (e != empty && (x.x | x.y)) add192(r, align_tile(x, e, em, bin, pw));
+        if (e != empty && (x.x | x.y)) add192(r, align_tile(x, e, em, bin, pw, hw));
       }
     }
   }
@@ -639,8 +646,9 @@ __device__ __forceinline__ void gv_reduce_task(const GvReduceArgs& a, int bx, in
   s_part[wid][lane] = r;
   __syncthreads();
   const int N = a.nbins;
+  // the axis bins of this block (the histogram slots after them have no axis)
   const int j_first = max(0, bx * 32 - 2 * a.nch);
-  const int j_last = min(a.nacc - 1, bx * 32 + 31) - 2 * a.nch;
+  const int j_last = min(min(a.nacc - 1, bx * 32 + 31) - 2 * a.nch, a.ndim * N - 1);
   if (wid == 0) {
     u192 t = s_part[0][lane];
 #pragma unroll
@@ -648,12 +656,14 @@ __device__ __forceinline__ void gv_reduce_task(const GvReduceArgs& a, int bx, in
     // the slot's sum over all events, rounded once to FP64
     if (k < a.nacc)
       a.sums[k] = em == empty ? 0.0
-                              : u192_to_double(t, bin ? bin_q(em) : pw * em - GV_FB);
+                              : u192_to_double(t, bin ? pw * (em - GV_BINE_OFF) - GV_BIN_FB
+                                                      : pw * em - GV_FB);
     __threadfence();
     // second tickets, one lane per axis the block touches: the block whose
     // count completes an axis refines it
     const int ax0 = j_first / N;
-    const int nax = (a.has_bins && a.refine_follows && j_last >= 0) ? j_last / N - ax0 + 1 : 0;
+    const int nax =
+        (a.has_bins && a.refine_follows && j_last >= j_first) ? j_last / N - ax0 + 1 : 0;
     bool won = false;
     if (lane < nax) {
       const int ax = ax0 + lane;
@@ -718,6 +728,62 @@ __global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs
 }
 
 // ---------------------------------------------------------------------------
+// Histogram of the observable (the paper's differential distributions,
+// Section 3.2), after the reduce of iteration k of a call.  Per bin b, from
+// the once-rounded sums: H = sum w / C, V = (sum w^2 / C - H^2)/(C-1) (0 if
+// rounding makes it negative).  The call's iterations are weighted as the
+// integral is: u_k = 1/sigma_k^2, or, if any sigma_k is 0, 1 for those
+// iterations and 0 for the others, so that the bins add up to the combined
+// integral.  acc holds, in iteration order, sum u H and sum u^2 V over the
+// iterations with sigma_k > 0, and sum H and sum V over those with
+// sigma_k = 0; the last iteration writes value = sum u H / sum u and
+// error = sqrt(sum u^2 V) / sum u.  One thread per bin: nothing depends on
+// the launch shape.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gv_hist_kernel(const GvHistArgs a) {
+  const int nh = a.nhist;
+  const double sk = a.per_iter[2 * a.k + 1];
+  int nzero = 0;
+  double W = 0.0;
+  if (a.last) {
+    for (int j = 0; j <= a.k; ++j)
+      if (!(a.per_iter[2 * j + 1] > 0.0)) ++nzero;
+    for (int j = 0; j <= a.k; ++j) {
+      const double s = a.per_iter[2 * j + 1];
+      W += nzero > 0 ? (s > 0.0 ? 0.0 : 1.0) : 1.0 / (s * s);
+    }
+  }
+  for (int b = threadIdx.x; b < nh; b += blockDim.x) {
+    const double h = a.sums[nh + b] * a.inv_c;
+    double v = (a.sums[b] * a.inv_c - h * h) * a.inv_cm1;
+    v = v > 0.0 ? v : 0.0;
+    double A0 = 0.0, A1 = 0.0, A2 = 0.0, A3 = 0.0;
+    if (a.k > 0) {
+      A0 = a.acc[b];
+      A1 = a.acc[nh + b];
+      A2 = a.acc[2 * nh + b];
+      A3 = a.acc[3 * nh + b];
+    }
+    if (sk > 0.0) {
+      const double u = 1.0 / (sk * sk);
+      A0 += u * h;
+      A1 += u * u * v;
+    } else {
+      A2 += h;
+      A3 += v;
+    }
+    a.acc[b] = A0;
+    a.acc[nh + b] = A1;
+    a.acc[2 * nh + b] = A2;
+    a.acc[3 * nh + b] = A3;
+    if (a.last) {
+      a.out[b] = (nzero > 0 ? A2 : A0) / W;
+      a.out[nh + b] = sqrt(nzero > 0 ? A3 : A1) / W;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Derived constants of an integrand (launched when the parameters change).
 // p[GV_MAXPARAMS - 1] carries the number of user parameters.
 // ---------------------------------------------------------------------------
@@ -727,6 +793,7 @@ __global__ void gv_consts_kernel(int ig, const double* p, double* K) {
   for (int i = 0; i < GV_NCONST; ++i) K[i] = 0.0;
   if (ig == GV_GAUSS) {
     K[GK_INV2S2] = 1.0 / (2.0 * p[0] * p[0]);
+    K[GK_SHIFT] = np > 1 ? p[1] : 0.0;
   } else if (ig == GV_DY || ig == GV_DYNLO) {
     const double sqrt_s = p[0], MZ = p[1], GZ = p[2], sw2 = p[3], alpha = p[4];
     const double mlo = p[5], mhi = p[6];
@@ -850,6 +917,11 @@ cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int
   cudaError_t e = allow_smem((const void*)gv_reduce_batch_kernel, smem);
   if (e != cudaSuccess) return e;
   gv_reduce_batch_kernel<<<ntasks, 256, smem, s>>>(args, tasks, k, last, inv_m1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s) {
+  gv_hist_kernel<<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

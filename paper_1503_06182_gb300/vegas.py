@@ -28,6 +28,7 @@ VEGAS_NGRAD = 5
 VEGAS_MAX_PARAMS = 16
 VEGAS_TILE = 1024
 VEGAS_NOALLOC_MAX_WORDS = 1 << 18
+VEGAS_HIST_MAX_BINS = 1000
 
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +83,8 @@ def lib():
             "vegas_rng_words_noalloc": ([C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64,
                                          C.c_int, _u32p], C.c_int),
             "vegas_last_sums": ([_vp, _dp], C.c_int),
+            "vegas_hist_set": ([_vp, C.c_int, C.c_double, C.c_double], C.c_int),
+            "vegas_hist_get": ([_vp, _vp, _vp, _vp], C.c_int),
             "vegas_kernel_time": ([_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.c_int], C.c_int),
             "vegas_get_ept": ([_vp, C.POINTER(C.c_int)], C.c_int),
@@ -254,6 +257,19 @@ def vegas_last_sums(h, ndim: int, nbins: int) -> np.ndarray:
     return out
 
 
+def vegas_hist_set(h, nbins: int, lo: float = 0.0, hi: float = 1.0) -> None:
+    _check(lib().vegas_hist_set(h, int(nbins), float(lo), float(hi)), "vegas_hist_set")
+
+
+def vegas_hist_get(h, nbins: int):
+    """(value, error, last_sums[2, nbins + 2]) of the last stage's histogram;
+    index 0 is the underflow bin, nbins + 1 the overflow bin."""
+    hb = nbins + 2
+    val, err, last = np.zeros(hb), np.zeros(hb), np.zeros((2, hb))
+    _check(lib().vegas_hist_get(h, _ptr(val), _ptr(err), _ptr(last)), "vegas_hist_get")
+    return val, err, last
+
+
 def vegas_kernel_time(h, kernel: int, reset: bool = False):
     ms = C.c_double()
     n = C.c_int64()
@@ -382,6 +398,17 @@ class Vegas:
 
     def last_sums(self) -> np.ndarray:
         return vegas_last_sums(self.h, self.ndim, self.nbins)
+
+    def hist_set(self, nbins: int, lo: float = 0.0, hi: float = 1.0) -> "Vegas":
+        """Fill a histogram of the integrand's observable in later stages
+        (nbins = 0: none)."""
+        vegas_hist_set(self.h, nbins, lo, hi)
+        self._hist_n = int(nbins)
+        return self
+
+    def hist(self):
+        """(value, error, last_sums) of the last stage's histogram."""
+        return vegas_hist_get(self.h, getattr(self, "_hist_n", 0))
 
     def close(self) -> None:
         if self.h:

@@ -269,7 +269,7 @@ def test_invalid_arguments():
     g = v.Vegas(4, 10, 1)
     try:
         for args in [(1, 1, v.VEGAS_GAUSS, GAUSS_PARAMS), (100, 0, v.VEGAS_GAUSS, GAUSS_PARAMS),
-                     (100, 1, 9, GAUSS_PARAMS), (100, 1, v.VEGAS_GAUSS, (0.1, 0.2)),
+                     (100, 1, 9, GAUSS_PARAMS), (100, 1, v.VEGAS_GAUSS, (0.1, 0.2, 0.3)),
                      (100, 1, v.VEGAS_GAUSS, (-0.1,)), (100, 1, v.VEGAS_EE3J, EE3J_PARAMS),
                      (100, 1, v.VEGAS_DY, DY_PARAMS[:9])]:
             with pytest.raises(v.VegasError) as ei:
