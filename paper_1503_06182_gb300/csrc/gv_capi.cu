@@ -431,7 +431,7 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
     GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
-    if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream));
+    if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
   return VEGAS_OK;

@@ -421,7 +421,7 @@ cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_ti
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
 size_t reduce_smem_bytes(int N);  // dynamic shared memory of the reduce kernels
 cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl);
-cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s);
+cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_fill_hist(int ig, int fp32, const GvFillArgs& a, int n_tiles, size_t smem,
                              cudaStream_t s, bool pdl);
 cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,

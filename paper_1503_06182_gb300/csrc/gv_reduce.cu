@@ -742,6 +742,8 @@ __global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) gv_hist_kernel(const GvHistArgs a) {
   const int nh = a.nhist;
+  gv_wait_prior_grid();  // the reduce's sums and records
+  gv_allow_next_grid();  // the next fill touches nothing this kernel reads or writes
   const double sk = a.per_iter[2 * a.k + 1];
   int nzero = 0;
   double W = 0.0;
@@ -920,9 +922,8 @@ cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s) {
-  gv_hist_kernel<<<1, 256, 0, s>>>(a);
-  return cudaGetLastError();
+cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s, bool pdl) {
+  return gv_launch(gv_hist_kernel, dim3(1), dim3(256), 0, s, pdl, a);
 }
 
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s) {
