@@ -87,6 +87,19 @@ def _load():
                                           C.POINTER(C.c_double)]
         lib.oracle_hist_bin.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double]
         lib.oracle_hist_combine.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_plus_nstrat.argtypes = [C.c_int, C.c_int64]
+        lib.oracle_plus_word.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
+        lib.oracle_plus_word.restype = C.c_uint32
+        lib.oracle_plus_weight.argtypes = [C.c_double, C.c_int]
+        lib.oracle_plus_weight.restype = C.c_double
+        lib.oracle_plus_allocate.argtypes = [C.c_int64, C.c_int64, C.c_int, _dp, _ip]
+        lib.oracle_iterate_plus.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                            C.POINTER(C.c_uint64), C.c_int64, C.c_int, C.c_int,
+                                            _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                            _dp, _ip, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.POINTER(C.c_int64)]
         lib.oracle_adjoint.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32,
                                        C.POINTER(C.c_uint64), C.c_int64, C.c_int, C.c_int, _dp,
                                        C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double),
@@ -285,3 +298,64 @@ def adjoint(ndim, nbins, seed, ncall, itmx, params, *, edges=None, iteration=0, 
     _check(st, "adjoint")
     return Result(grad=grad, grad_err=gerr, integral=I.value, error=e.value, per_iter=per,
                   per_iter_grad=perg, iteration=it.value)
+
+
+# ---------------------------------------------------------------------------- VEGAS+
+def plus_nstrat(ndim: int, ncall: int) -> int:
+    """Strata per axis: the largest s with 4 s^ndim <= ncall (and s^ndim <= 2^22)."""
+    return int(_load().oracle_plus_nstrat(ndim, ncall))
+
+
+def plus_word(r: int, c: int, s: int) -> int:
+    """Stratified word floor((c 2^32 + r) / s)."""
+    return int(_load().oracle_plus_word(r, c, s))
+
+
+def plus_weight(v: float, beta: float) -> float:
+    """Allocation weight v^(beta/2) as the stage forms it."""
+    return float(_load().oracle_plus_weight(float(v), _beta_j(beta)))
+
+
+def _beta_j(beta: float) -> int:
+    j = int(round(4 * beta))
+    if not (0 <= j <= 4 and abs(4 * beta - j) < 1e-12):
+        raise ValueError("beta must be one of 0, 1/4, 1/2, 3/4, 1")
+    return j
+
+
+def plus_allocate(ncall: int, var, beta: float = 0.75) -> np.ndarray:
+    var = np.ascontiguousarray(var, np.float64)
+    n = np.zeros(len(var), np.int32)
+    _check(_load().oracle_plus_allocate(len(var), ncall, _beta_j(beta), var, n), "plus_allocate")
+    return n
+
+
+def iterate_plus(ndim, nbins, seed, ncall, itmx, iid, params, *, edges=None, alloc=None,
+                 iteration=0, batch=0, alpha=1.5, beta=0.75, nstrat=0, adapt=True) -> Result:
+    """itmx VEGAS+ iterations (one stage) from a grid and an allocation
+    (None: uniform).  Returns integral, error, chi2dof, per_iter, edges,
+    alloc (for the next iteration), calls per iteration, the last
+    iteration's sums and per-hypercube variances, nstrat."""
+    s = nstrat if nstrat > 0 else plus_nstrat(ndim, ncall)
+    nh = s ** ndim
+    if edges is None:
+        edges = uniform_edges(ndim, nbins)
+    edges = np.ascontiguousarray(np.array(edges, np.float64, copy=True))
+    a = np.zeros(nh, np.int32) if alloc is None else np.array(alloc, np.int32, copy=True)
+    params = np.ascontiguousarray(params, np.float64)
+    it = C.c_uint64(iteration)
+    I, e, c = C.c_double(), C.c_double(), C.c_double()
+    per = np.zeros((itmx, 2))
+    calls = np.zeros(itmx, np.int64)
+    sums = np.zeros(2 + ndim * nbins)
+    var = np.zeros(nh)
+    bad = C.c_int64()
+    st = _load().oracle_iterate_plus(ndim, nbins, seed, batch, C.byref(it), ncall, itmx, iid,
+                                     params, len(params), alpha, int(adapt), _beta_j(beta), s,
+                                     edges.reshape(-1), a, C.byref(I), C.byref(e), C.byref(c),
+                                     per.ctypes.data, calls.ctypes.data, sums.ctypes.data,
+                                     var.ctypes.data, C.byref(bad))
+    _check(st, "iterate_plus")
+    return Result(integral=I.value, error=e.value, chi2dof=c.value, per_iter=per, edges=edges,
+                  alloc=a, calls=calls, sums=sums, var=var, nstrat=s, iteration=it.value,
+                  nonfinite=bad.value)

@@ -975,3 +975,275 @@ int oracle_adjoint(int ndim, int nbins, uint64_t seed, uint32_t batch,
   free(sGk);
   return st;
 }
+
+/* ------------------------------------------------------------------------
+ * VEGAS+: adaptive stratified sampling on top of the VEGAS map (Lepage,
+ * J. Comput. Phys. 439 (2021) 110386, a later form of the method the paper
+ * cites in Section 2.1).  As restated here:
+ *   - the unit cube of the map's input y is cut into NH = s^d hypercubes,
+ *     s the largest integer with 4 s^d <= C and s^d <= ORACLE_PLUS_MAX_CUBES
+ *     (so at least 4 events per hypercube on average); hypercube h has
+ *     coordinates c_a = floor(h / s^a) mod s and volume 1/NH;
+ *   - hypercube h gets n_h >= 2 events (uniform floor(C/NH) at the start);
+ *     events are numbered hypercube by hypercube, so event e lies in the h
+ *     with o_h <= e < o_h + n_h (o the running sum of n);
+ *   - event e's word on axis a is the stratified word
+ *     r' = floor((c_a 2^32 + r_a) / s), y = r'/2^32 in [c_a/s, (c_a+1)/s),
+ *     with r_a its Philox word; then the VEGAS map as before: F = J g(x);
+ *   - per hypercube, the sample mean and variance of F (sequential sums in
+ *     event order): m_h = S1h/n_h, v_h = (S2h - S1h^2/n_h)/(n_h - 1) (>= 0);
+ *   - I_k = sum_h m_h/NH (as sum_e F a_h / C, a_h = C/(NH n_h)), and
+ *     sigma_k^2 = sum_h v_h/n_h / NH^2;
+ *   - the map is trained on d_{a,i} = sum over the events in bin i of axis a
+ *     of q^2, q = F b_h, b_h = sqrt(1/(NH n_h)): an estimate of the integral
+ *     of F^2 over the slab (each event stands for the volume 1/(NH n_h));
+ *   - the next allocation: d_h = v_h^(beta/2), n_h = max(2, floor(C d_h/D)),
+ *     D = sum_h d_h (uniform again if D = 0), with the damping
+ *     beta in {0, 1/4, 1/2, 3/4, 1}; v^(beta/2) is formed in FP32 from
+ *     correctly rounded operations only (three square roots and products)
+ *     after an exact split of v's exponent, so that the decision can be
+ *     reproduced exactly anywhere.
+ * ---------------------------------------------------------------------- */
+#define ORACLE_PLUS_MAX_CUBES (1 << 22)
+
+int oracle_plus_nstrat(int ndim, int64_t ncall) {
+  if (ndim < 1 || ncall < 8) return 1;
+  int64_t s = 1;
+  for (;;) {
+    int64_t t = s + 1, p = 1;
+    int over = 0;
+    for (int a = 0; a < ndim; ++a) {
+      p *= t;
+      if (p > ORACLE_PLUS_MAX_CUBES || 4 * p > ncall) {
+        over = 1;
+        break;
+      }
+    }
+    if (over) return (int)s;
+    s = t;
+  }
+}
+
+uint32_t oracle_plus_word(uint32_t r, uint32_t c, uint32_t s) {
+  return (uint32_t)((((uint64_t)c << 32) | (uint64_t)r) / (uint64_t)s);
+}
+
+/* v^(j/8) for v >= 0 finite (j = 4 beta): v = t 2^(8q), t in [1/2, 128),
+ * t rounded to FP32, y = sqrt(sqrt(sqrt(t))) in FP32, y^j by FP32 products,
+ * times 2^(q j) exactly. */
+double oracle_plus_weight(double v, int j) {
+  if (j == 0) return 1.0;
+  if (!(v > 0.0)) return 0.0;
+  int e;
+  double m = frexp(v, &e); /* v = m 2^e, m in [1/2, 1) */
+  int q = e >= 0 ? e / 8 : -((-e + 7) / 8);
+  int r = e - 8 * q; /* 0 <= r < 8 */
+  volatile float t = (float)ldexp(m, r);
+  volatile float y = sqrtf(sqrtf(sqrtf(t)));
+  volatile float p = y;
+  for (int k = 1; k < j; ++k) p = p * y;
+  return ldexp((double)p, q * j);
+}
+
+/* Allocation of the next iteration from the hypercubes' variances. */
+int oracle_plus_allocate(int64_t nh, int64_t ncall, int beta_j, const double* var,
+                         int32_t* n) {
+  if (nh < 1 || ncall < 2 * nh || beta_j < 0 || beta_j > 4) return OR_EINVAL;
+  double* d = (double*)malloc(sizeof(double) * (size_t)nh);
+  if (!d) return OR_ENOMEM;
+  csum_t D = {0.0, 0.0};
+  for (int64_t h = 0; h < nh; ++h) {
+    d[h] = oracle_plus_weight(var[h], beta_j);
+    csum_add(&D, d[h]);
+  }
+  double Dv = csum_value(&D);
+  for (int64_t h = 0; h < nh; ++h) {
+    int64_t k;
+    if (Dv > 0.0) {
+      double x = (double)ncall * d[h] / Dv;
+      k = (int64_t)floor(x);
+    } else {
+      k = ncall / nh;
+    }
+    n[h] = (int32_t)(k > 2 ? k : 2);
+  }
+  free(d);
+  return OR_OK;
+}
+
+/* itmx VEGAS+ iterations (one stage).  alloc (NH counts, in/out): the
+ * allocation of the first iteration (alloc[0] <= 0: uniform), on return the
+ * allocation for the next one.  nstrat: strata per axis (0: as above).
+ * calls (nullable): the events of each iteration.  last_sums (nullable):
+ * (sum w, sum w^2, d[ndim*nbins]) of the last iteration with w = F a_h;
+ * last_var (nullable): its per-hypercube variances v_h.  With adapt = 0 the
+ * grid and the allocation stay as they are. */
+int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
+                        uint64_t* iteration, int64_t ncall, int itmx, int id,
+                        const double* prm, int nparams, double alpha, int adapt,
+                        int beta_j, int nstrat, double* edges, int32_t* alloc,
+                        double* integral, double* error, double* chi2dof,
+                        double* per_iter, int64_t* calls, double* last_sums,
+                        double* last_var, int64_t* nonfinite) {
+  if (ndim < 1 || ndim > ORACLE_MAX_DIM || nbins < 2 || ncall < 8 ||
+      ncall > ((int64_t)1 << 30) || itmx < 1 || beta_j < 0 || beta_j > 4)
+    return OR_EINVAL;
+  int st = check_integrand(id, ndim, nparams);
+  if (st) return st;
+  const int s = nstrat > 0 ? nstrat : oracle_plus_nstrat(ndim, ncall);
+  int64_t NH = 1;
+  for (int a = 0; a < ndim; ++a) NH *= s;
+  if (NH > ORACLE_PLUS_MAX_CUBES || 4 * NH > ncall) return OR_EINVAL;
+  if (alloc[0] <= 0)
+    for (int64_t h = 0; h < NH; ++h) alloc[h] = (int32_t)(ncall / NH);
+  const int nd = 2 + ndim * nbins;
+  const double C = (double)ncall;
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(NH + 1));
+  double* var = (double*)malloc(sizeof(double) * (size_t)NH);
+  double* Ik = (double*)malloc(sizeof(double) * itmx);
+  double* sk = (double*)malloc(sizeof(double) * itmx);
+  double* sums = (double*)malloc(sizeof(double) * nd);
+  if (!off || !var || !Ik || !sk || !sums) {
+    free(off);
+    free(var);
+    free(Ik);
+    free(sk);
+    free(sums);
+    return OR_ENOMEM;
+  }
+  int64_t bad_all = 0;
+  for (int k = 0; k < itmx && !st; ++k) {
+    const uint32_t it = (uint32_t)(*iteration);
+    off[0] = 0;
+    for (int64_t h = 0; h < NH; ++h) off[h + 1] = off[h] + alloc[h];
+    const int64_t Cp = off[NH];
+    double* F = (double*)malloc(sizeof(double) * (size_t)(Cp > 0 ? Cp : 1));
+    csum_t* total = (csum_t*)calloc((size_t)nd, sizeof(csum_t));
+    if (!F || !total) {
+      free(F);
+      free(total);
+      st = OR_ENOMEM;
+      break;
+    }
+    const int64_t nchunks = (Cp + ORACLE_CHUNK - 1) / ORACLE_CHUNK;
+    int64_t bad_it = 0;
+    int fail = 0;
+#pragma omp parallel
+    {
+      csum_t* part = (csum_t*)malloc(sizeof(csum_t) * (size_t)nd);
+      if (!part) {
+#pragma omp atomic write
+        fail = 1;
+      }
+#pragma omp for ordered schedule(static, 1)
+      for (int64_t ch = 0; ch < nchunks; ++ch) {
+        int64_t bad = 0;
+        if (part) {
+          memset(part, 0, sizeof(csum_t) * (size_t)nd);
+          const int64_t e0 = ch * ORACLE_CHUNK;
+          const int64_t e1 = e0 + ORACLE_CHUNK < Cp ? e0 + ORACLE_CHUNK : Cp;
+          /* the hypercube of e0: the last h with off[h] <= e0 */
+          int64_t lo = 0, hi = NH;
+          while (hi - lo > 1) {
+            int64_t mid = (lo + hi) / 2;
+            if (off[mid] <= e0)
+              lo = mid;
+            else
+              hi = mid;
+          }
+          int64_t h = lo;
+          for (int64_t ev = e0; ev < e1; ++ev) {
+            while (ev >= off[h + 1]) ++h;
+            uint32_t words[ORACLE_MAX_DIM];
+            double x[ORACLE_MAX_DIM];
+            int32_t bins[ORACLE_MAX_DIM];
+            oracle_event_words(seed, it, batch, (uint64_t)ev, ndim, words);
+            int64_t rest = h;
+            double J = 1.0;
+            for (int a = 0; a < ndim; ++a) {
+              uint32_t c = (uint32_t)(rest % s);
+              rest /= s;
+              uint32_t rw = oracle_plus_word(words[a], c, (uint32_t)s);
+              double xa;
+              J *= oracle_grid_map(edges + (size_t)a * (nbins + 1), nbins, rw, &xa);
+              x[a] = xa;
+              int32_t bi;
+              double fr;
+              oracle_bin_map(rw, nbins, &bi, &fr);
+              bins[a] = bi;
+            }
+            double Fe = J * integrand_point(id, ndim, x, prm, nparams, NULL, NULL);
+            if (!isfinite(Fe)) {
+              ++bad;
+              F[ev] = 0.0;
+              continue;
+            }
+            F[ev] = Fe;
+            const double nhd = (double)NH * (double)alloc[h];
+            const double ah = C / nhd, bh = sqrt(1.0 / nhd);
+            const double w = Fe * ah, q = Fe * bh;
+            csum_add(&part[0], w);
+            csum_add(&part[1], w * w);
+            for (int a = 0; a < ndim; ++a) csum_add(&part[2 + a * nbins + bins[a]], q * q);
+          }
+        }
+#pragma omp ordered
+        {
+          if (part)
+            for (int j = 0; j < nd; ++j) csum_add(&total[j], csum_value(&part[j]));
+          bad_it += bad;
+        }
+      }
+      free(part);
+    }
+    if (fail) {
+      free(F);
+      free(total);
+      st = OR_ENOMEM;
+      break;
+    }
+    for (int j = 0; j < nd; ++j) sums[j] = csum_value(&total[j]);
+    free(total);
+    /* per hypercube: sequential sums over its events in order */
+#pragma omp parallel for schedule(static)
+    for (int64_t h = 0; h < NH; ++h) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int64_t ev = off[h]; ev < off[h + 1]; ++ev) {
+        s1 += F[ev];
+        s2 += F[ev] * F[ev];
+      }
+      const double n = (double)alloc[h];
+      double v = (s2 - s1 * s1 / n) / (n - 1.0);
+      var[h] = v > 0.0 ? v : 0.0;
+    }
+    free(F);
+    csum_t V = {0.0, 0.0};
+    for (int64_t h = 0; h < NH; ++h) csum_add(&V, var[h] / (double)alloc[h]);
+    const double var_k = csum_value(&V) / ((double)NH * (double)NH);
+    Ik[k] = sums[0] / C;
+    sk[k] = var_k > 0.0 ? sqrt(var_k) : 0.0;
+    if (per_iter) {
+      per_iter[2 * k] = Ik[k];
+      per_iter[2 * k + 1] = sk[k];
+    }
+    if (calls) calls[k] = Cp;
+    bad_all += bad_it;
+    *iteration += 1;
+    if (k == itmx - 1) {
+      if (last_sums) memcpy(last_sums, sums, sizeof(double) * nd);
+      if (last_var) memcpy(last_var, var, sizeof(double) * (size_t)NH);
+    }
+    if (adapt) {
+      oracle_refine(ndim, nbins, alpha, sums + 2, edges);
+      st = oracle_plus_allocate(NH, ncall, beta_j, var, alloc);
+    }
+  }
+  if (!st) oracle_combine(itmx, Ik, sk, integral, error, chi2dof);
+  if (nonfinite) *nonfinite = bad_all;
+  free(off);
+  free(var);
+  free(Ik);
+  free(sk);
+  free(sums);
+  return st;
+}
