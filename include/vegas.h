@@ -79,6 +79,9 @@ extern "C" {
 #define VEGAS_OPT_BATCH_ID 7  /* Philox batch word of this context (default 0; < 2^24) */
 #define VEGAS_OPT_PDL 8       /* 1 = chain the kernels of consecutive iterations with programmatic
                                  dependent launches (default), 0 = ordinary stream order */
+#define VEGAS_OPT_STRAT 9     /* 1 = VEGAS+ adaptive stratified sampling (see vegas_strat_get),
+                                 0 = plain VEGAS (default) */
+#define VEGAS_OPT_BETA 10     /* VEGAS+ damping of the allocation: 0, 0.25, 0.5, 0.75 (default), 1 */
 
 /* ---- kernel ids for vegas_kernel_time ---- */
 #define VEGAS_KERNEL_FILL 0   /* per-event kernel */
@@ -237,6 +240,32 @@ int vegas_last_sums(const vegas_ctx* ctx, double* sums);
 #define VEGAS_HIST_MAX_BINS 1000
 int vegas_hist_set(vegas_ctx* ctx, int nbins, double lo, double hi);
 int vegas_hist_get(vegas_ctx* ctx, double* value, double* error, double* last_sums);
+
+/* VEGAS+ (VEGAS_OPT_STRAT = 1): adaptive stratified sampling on the VEGAS map
+ * (Lepage, J. Comput. Phys. 439 (2021) 110386; a later form of the VEGAS
+ * method of Section 2.1).  For a stage of ncall events (8 <= ncall <= 2^30):
+ *   - the map's input cube is cut into nh = s^ndim hypercubes, s the largest
+ *     integer with 4 s^ndim <= ncall and s^ndim <= 2^22; hypercube h has the
+ *     base-s digits c_a of h as coordinates;
+ *   - hypercube h gets n_h >= 2 events, numbered hypercube by hypercube
+ *     (uniform floor(ncall/nh) at the start); event e's word on axis a is
+ *     floor((c_a 2^32 + r_a)/s), r_a its Philox word; F = J g as in VEGAS;
+ *   - per hypercube, the sample variance v_h of F; the iteration's estimate
+ *     I_k = sum_e F C/(nh n_h) / C and sigma_k^2 = sum_h v_h/n_h / nh^2; the
+ *     grid is trained on F^2/(nh n_h) per event;
+ *   - the next allocation: n_h = max(2, floor(ncall d_h / sum d)),
+ *     d_h = v_h^(beta/2) (formed in FP32 from correctly rounded operations),
+ *     so an iteration has between 2 nh and ncall + 2 nh events.
+ * The allocation persists across stages with the same ncall (and is frozen
+ * with VEGAS_OPT_ADAPT = 0); VEGAS+ excludes histograms and vegas_adjoint
+ * (EINVAL).  The fill runs at 4 events per thread.
+ * vegas_strat_get: after a VEGAS+ stage (blocks until done), s, nh, the
+ * allocation for the next iteration (counts, nh int32, nullable) and the last
+ * iteration's v_h (var, nh doubles, nullable).  EINVAL before any.
+ * vegas_strat_set: the allocation for stages of ncall events (counts: nh
+ * values >= 2 summing to at most ncall + 2 nh; EINVAL otherwise). */
+int vegas_strat_get(vegas_ctx* ctx, int* nstrat, int64_t* ncubes, int32_t* counts, double* var);
+int vegas_strat_set(vegas_ctx* ctx, int64_t ncall, const int32_t* counts);
 
 /* Accumulated device time of the VEGAS_KERNEL_* kernels since the last
  * reset (VEGAS_OPT_TIMING = 1 only); reset != 0 clears that kernel's totals

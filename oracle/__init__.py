@@ -99,7 +99,7 @@ def _load():
                                             _dp, _ip, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                            C.POINTER(C.c_int64)]
+                                            C.c_void_p, C.POINTER(C.c_int64)]
         lib.oracle_adjoint.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32,
                                        C.POINTER(C.c_uint64), C.c_int64, C.c_int, C.c_int, _dp,
                                        C.c_int, _dp, _dp, _dp, C.POINTER(C.c_double),
@@ -335,7 +335,7 @@ def iterate_plus(ndim, nbins, seed, ncall, itmx, iid, params, *, edges=None, all
     """itmx VEGAS+ iterations (one stage) from a grid and an allocation
     (None: uniform).  Returns integral, error, chi2dof, per_iter, edges,
     alloc (for the next iteration), calls per iteration, the last
-    iteration's sums and per-hypercube variances, nstrat."""
+    iteration's sums, per-hypercube variances and means, nstrat."""
     s = nstrat if nstrat > 0 else plus_nstrat(ndim, ncall)
     nh = s ** ndim
     if edges is None:
@@ -349,13 +349,14 @@ def iterate_plus(ndim, nbins, seed, ncall, itmx, iid, params, *, edges=None, all
     calls = np.zeros(itmx, np.int64)
     sums = np.zeros(2 + ndim * nbins)
     var = np.zeros(nh)
+    mean = np.zeros(nh)
     bad = C.c_int64()
     st = _load().oracle_iterate_plus(ndim, nbins, seed, batch, C.byref(it), ncall, itmx, iid,
                                      params, len(params), alpha, int(adapt), _beta_j(beta), s,
                                      edges.reshape(-1), a, C.byref(I), C.byref(e), C.byref(c),
                                      per.ctypes.data, calls.ctypes.data, sums.ctypes.data,
-                                     var.ctypes.data, C.byref(bad))
+                                     var.ctypes.data, mean.ctypes.data, C.byref(bad))
     _check(st, "iterate_plus")
     return Result(integral=I.value, error=e.value, chi2dof=c.value, per_iter=per, edges=edges,
-                  alloc=a, calls=calls, sums=sums, var=var, nstrat=s, iteration=it.value,
-                  nonfinite=bad.value)
+                  alloc=a, calls=calls, sums=sums, var=var, mean=mean, nstrat=s,
+                  iteration=it.value, nonfinite=bad.value)

@@ -1076,15 +1076,15 @@ int oracle_plus_allocate(int64_t nh, int64_t ncall, int beta_j, const double* va
  * allocation for the next one.  nstrat: strata per axis (0: as above).
  * calls (nullable): the events of each iteration.  last_sums (nullable):
  * (sum w, sum w^2, d[ndim*nbins]) of the last iteration with w = F a_h;
- * last_var (nullable): its per-hypercube variances v_h.  With adapt = 0 the
- * grid and the allocation stay as they are. */
+ * last_var, last_mean (nullable): its per-hypercube variances v_h and means
+ * m_h.  With adapt = 0 the grid and the allocation stay as they are. */
 int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
                         uint64_t* iteration, int64_t ncall, int itmx, int id,
                         const double* prm, int nparams, double alpha, int adapt,
                         int beta_j, int nstrat, double* edges, int32_t* alloc,
                         double* integral, double* error, double* chi2dof,
                         double* per_iter, int64_t* calls, double* last_sums,
-                        double* last_var, int64_t* nonfinite) {
+                        double* last_var, double* last_mean, int64_t* nonfinite) {
   if (ndim < 1 || ndim > ORACLE_MAX_DIM || nbins < 2 || ncall < 8 ||
       ncall > ((int64_t)1 << 30) || itmx < 1 || beta_j < 0 || beta_j > 4)
     return OR_EINVAL;
@@ -1100,12 +1100,14 @@ int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
   const double C = (double)ncall;
   int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(NH + 1));
   double* var = (double*)malloc(sizeof(double) * (size_t)NH);
+  double* mean = (double*)malloc(sizeof(double) * (size_t)NH);
   double* Ik = (double*)malloc(sizeof(double) * itmx);
   double* sk = (double*)malloc(sizeof(double) * itmx);
   double* sums = (double*)malloc(sizeof(double) * nd);
-  if (!off || !var || !Ik || !sk || !sums) {
+  if (!off || !var || !mean || !Ik || !sk || !sums) {
     free(off);
     free(var);
+    free(mean);
     free(Ik);
     free(sk);
     free(sums);
@@ -1215,6 +1217,7 @@ int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
       const double n = (double)alloc[h];
       double v = (s2 - s1 * s1 / n) / (n - 1.0);
       var[h] = v > 0.0 ? v : 0.0;
+      mean[h] = s1 / n;
     }
     free(F);
     csum_t V = {0.0, 0.0};
@@ -1232,6 +1235,7 @@ int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
     if (k == itmx - 1) {
       if (last_sums) memcpy(last_sums, sums, sizeof(double) * nd);
       if (last_var) memcpy(last_var, var, sizeof(double) * (size_t)NH);
+      if (last_mean) memcpy(last_mean, mean, sizeof(double) * (size_t)NH);
     }
     if (adapt) {
       oracle_refine(ndim, nbins, alpha, sums + 2, edges);
@@ -1242,6 +1246,7 @@ int oracle_iterate_plus(int ndim, int nbins, uint64_t seed, uint32_t batch,
   if (nonfinite) *nonfinite = bad_all;
   free(off);
   free(var);
+  free(mean);
   free(Ik);
   free(sk);
   free(sums);

@@ -151,6 +151,14 @@ struct vegas_ctx {
   double* hist_acc = nullptr;  // [4][GV_HIST_MAX + 2]
   double* hist_out = nullptr;  // [2][GV_HIST_MAX + 2]
   bool hist_valid = false;
+  // VEGAS+ (strat = 1): the allocation persists across stages with the same
+  // ncall (plus_C); plus_valid: it exists on the device
+  int strat = 0, beta_j = 3;
+  void* plus_mem = nullptr;
+  long long plus_nh = 0, plus_C = 0;
+  int plus_s = 0, plus_tiles = 0;
+  bool plus_valid = false;
+  GvPlusArgs pa;  // device arrays of the allocation (pointers only)
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -184,7 +192,10 @@ void clear_graphs(vegas_ctx* c) {
 
 size_t grid_doubles(int d, int N) { return GvGridLayout{d, N}.doubles(); }
 
-size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhist) {
+// events: the fill's capacity (ncall, or ncall + 2 nh with VEGAS+); plus_f:
+// room for the per-event J g of VEGAS+
+size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhist,
+                       bool plus_f = false) {
   const int64_t n_tiles = (ncall + GV_TILE - 1) / GV_TILE;
   const int nch = mode ? GV_MAXCH : 1;
   const int nacc = mode ? 2 * GV_MAXCH : 2 + d * N + 2 * nhist;
@@ -194,7 +205,29 @@ size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhis
   b += align256((size_t)n_tiles * nch * 4);
   b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
   b += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
+  if (plus_f) b += align256((size_t)ncall * 8);
   return b;
+}
+
+// VEGAS+ strata per axis: the largest s >= 1 with 4 s^d <= C and
+// s^d <= 2^22 (at least four events per hypercube on average).
+int plus_nstrat(int d, int64_t C) {
+  int64_t s = 1;
+  for (;;) {
+    const int64_t t = s + 1;
+    int64_t p = 1;
+    for (int a = 0; a < d; ++a) {
+      p *= t;
+      if (p > ((int64_t)1 << 22) || 4 * p > C) return (int)s;
+    }
+    s = t;
+  }
+}
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
 }
 
 int ensure_workspace(vegas_ctx* c, size_t need) {
@@ -233,6 +266,9 @@ int ensure_pinned(vegas_ctx* c, size_t need) {
 struct Plan {
   int ig, fp32, mode, itmx, n_tiles, nacc, nch, ept, reduce_ctas, tiles_per_cta;
   int nhist;  // histogram bins with underflow and overflow (0: none)
+  int plus, s;     // VEGAS+: strata per axis
+  long long nh;    // hypercubes
+  double* F;       // per-event J g (VEGAS+)
   int64_t ncall;
   size_t smem;
   ulonglong2* part;
@@ -263,7 +299,88 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
     a.h_lo_f = (float)c->hist_lo;
     a.h_invw_f = (float)invw;
   }
+  if (p.plus) {
+    a.p_s = p.s;
+    a.p_nh = p.nh;
+    a.p_magic = ~0ull / (unsigned long long)p.s;
+    a.p_inv_s = 1.0f / (float)p.s;
+    a.p_off = c->pa.off;
+    a.p_ab = c->pa.ab;
+    a.p_tile_h0 = c->pa.tile_h0;
+    a.p_ncall = c->pa.ncall_dev;
+    a.p_F = p.F;
+  }
   return a;
+}
+
+// VEGAS+ kernels' arguments for iteration k of a plan (k < 0: set-up).
+GvPlusArgs plus_args(const vegas_ctx* c, const Plan& p, int k) {
+  GvPlusArgs a = c->pa;
+  a.ncall = p.ncall;
+  a.beta_j = c->beta_j;
+  a.n_tiles = p.n_tiles;
+  a.k = k < 0 ? 0 : k;
+  a.last = k == p.itmx - 1;
+  a.inv_m1 = k > 0 ? 1.0 / (double)k : 0.0;
+  a.F = p.F;
+  a.per_iter = p.per_iter;
+  a.st = c->st;
+  return a;
+}
+
+// Device memory of a VEGAS+ allocation of nh hypercubes and n_tiles tiles
+// (zeroed; the allocation itself is made by the caller).
+int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
+  if (c->plus_mem && c->plus_nh == nh && c->plus_tiles >= n_tiles) return VEGAS_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->plus_mem) cudaFree(c->plus_mem);
+  c->plus_mem = nullptr;
+  c->plus_valid = false;
+  clear_graphs(c);
+  const long long nb = (nh + 255) / 256;
+  size_t off = 0;
+  const size_t o_off = off;
+  off = align256(off + (size_t)(nh + 1) * 8);
+  const size_t o_n = off;
+  off = align256(off + (size_t)nh * 4);
+  const size_t o_ab = off;
+  off = align256(off + (size_t)nh * 16);
+  const size_t o_t = off;
+  off = align256(off + (size_t)n_tiles * 4);
+  const size_t o_var = off;
+  off = align256(off + (size_t)nh * 8);
+  const size_t o_dw = off;
+  off = align256(off + (size_t)nh * 8);
+  const size_t o_part = off;
+  off = align256(off + (size_t)nb * 16);
+  const size_t o_np = off;
+  off = align256(off + (size_t)nb * 8);
+  const size_t o_sc = off;
+  off = align256(off + 64);
+  if (cudaMalloc(&c->plus_mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    c->plus_mem = nullptr;
+    return VEGAS_ENOMEM;
+  }
+  char* b = (char*)c->plus_mem;
+  GvPlusArgs& a = c->pa;
+  a.nh = nh;
+  a.inv_nh2 = 1.0 / ((double)nh * (double)nh);
+  a.off = (long long*)(b + o_off);
+  a.n = (int*)(b + o_n);
+  a.ab = (double2*)(b + o_ab);
+  a.tile_h0 = (int*)(b + o_t);
+  a.var = (double*)(b + o_var);
+  a.dw = (double*)(b + o_dw);
+  a.part = (double*)(b + o_part);
+  a.npart = (long long*)(b + o_np);
+  a.ncall_dev = (long long*)(b + o_sc);
+  a.scal = (double*)(b + o_sc + 8);
+  a.tickets = (int*)(b + o_sc + 24);
+  GV_TRY(cudaMemsetAsync(c->plus_mem, 0, off, c->stream));
+  c->plus_nh = nh;
+  c->plus_tiles = n_tiles;
+  return VEGAS_OK;
 }
 
 GvHistArgs hist_args(const vegas_ctx* c, const Plan& p, int k) {
@@ -288,6 +405,7 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.nacc = p.nacc;
   r.has_bins = p.mode == 0;
   r.nhist = p.nhist;
+  r.plus = p.plus;
   r.k = k;
   r.last = k == p.itmx - 1;
   r.refine_follows = (p.mode == 0 && c->adapt) ? 1 : 0;
@@ -331,6 +449,7 @@ cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pd
   const GvFillArgs a = fill_args(c, p);
   if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
   if (p.nhist) return gv::launch_fill_hist(p.ig, p.fp32, a, p.n_tiles, p.smem, c->stream, pdl);
+  if (p.plus) return gv::launch_fill_plus(p.ig, p.fp32, a, p.n_tiles, p.smem, c->stream, pdl);
   return launch_fill_any(p.ig, p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
 }
 
@@ -395,17 +514,32 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.mode = mode;
   p.itmx = itmx;
   p.ncall = ncall;
-  const int64_t nt = (ncall + GV_TILE - 1) / GV_TILE;
+  // VEGAS+: strata, and room for up to ncall + 2 nh events (each hypercube's
+  // share is floored, then raised to at least 2)
+  p.plus = (mode == 0 && c->strat) ? 1 : 0;
+  p.s = 0;
+  p.nh = 0;
+  p.F = nullptr;
+  int64_t cap = ncall;
+  if (p.plus) {
+    if (c->hist_nh > 0 || ncall < 8 || ncall > ((int64_t)1 << 30)) return VEGAS_EINVAL;
+    p.s = plus_nstrat(c->ndim, ncall);
+    p.nh = ipow(p.s, c->ndim);
+    cap = ncall + 2 * p.nh;
+  }
+  const int64_t nt = (cap + GV_TILE - 1) / GV_TILE;
   if (nt > 0x7fffffff) return VEGAS_EINVAL;
   p.n_tiles = (int)nt;
   p.nch = mode ? GV_MAXCH : 1;
   p.nhist = (mode == 0 && c->hist_nh > 0) ? c->hist_nh + 2 : 0;
   p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins + 2 * p.nhist;
-  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist).total;
+  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist,
+                      p.plus != 0)
+               .total;
   int gx = 0, gy = 0;
   gv::reduce_grid(p.n_tiles, p.nacc, &p.tiles_per_cta, &gx, &gy);
   p.reduce_ctas = gx * gy;
-  const size_t need = workspace_bytes(c->ndim, c->nbins, ncall, itmx, mode, p.nhist);
+  const size_t need = workspace_bytes(c->ndim, c->nbins, cap, itmx, mode, p.nhist, p.plus != 0);
   int st = ensure_workspace(c, need);
   if (st) return st;
   char* w = (char*)c->ws;
@@ -416,7 +550,26 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.per_iter = (double*)w;
   w += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
   p.cpart = (GvSlot*)w;
+  if (p.plus) {
+    w += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
+    p.F = (double*)w;
+  }
   p.ept = c->ept_opt;
+  return VEGAS_OK;
+}
+
+// VEGAS+: make sure the allocation for ncall exists (uniform if it is new).
+int ensure_allocation(vegas_ctx* c, const Plan& p) {
+  int st = ensure_plus(c, p.nh, p.n_tiles);
+  if (st) return st;
+  c->plus_s = p.s;
+  if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;
+  GvPlusArgs a = plus_args(c, p, -1);
+  a.uniform = 1;
+  GV_TRY(gv::launch_plus_alloc(a, c->stream, false));
+  GV_TRY(gv::launch_plus_layout(a, c->stream, false));
+  c->plus_valid = true;
+  c->plus_C = p.ncall;
   return VEGAS_OK;
 }
 
@@ -432,6 +585,16 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
     GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
     if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
+    if (p.plus) {
+      // the hypercubes' statistics (sigma_k, the stage's combination), then
+      // the next iteration's allocation and its layout
+      const GvPlusArgs a = plus_args(c, p, k);
+      GV_TRY(gv::launch_plus_stats(a, c->stream, pdl));
+      if (c->adapt) {
+        GV_TRY(gv::launch_plus_alloc(a, c->stream, pdl));
+        GV_TRY(gv::launch_plus_layout(a, c->stream, pdl));
+      }
+    }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
   return VEGAS_OK;
@@ -468,14 +631,18 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   if (ncall < 2 || ncall > ((int64_t)1 << 40) || itmx < 1 || itmx > 100000) return VEGAS_EINVAL;
   int st = check_params(ig, c->ndim, params, np);
   if (st) return st;
-  if (mode && ig != VEGAS_DY) return VEGAS_EINVAL;
+  if (mode && (ig != VEGAS_DY || c->strat)) return VEGAS_EINVAL;
   Plan p;
   st = make_plan(c, ncall, itmx, ig, mode, p);
   if (st) return st;
   st = ensure_consts(c, ig, params, np);
   if (st) return st;
-  if (p.nhist) {
-    p.ept = 4;  // the histogram fill has one shape
+  if (p.plus) {
+    st = ensure_allocation(c, p);
+    if (st) return st;
+  }
+  if (p.nhist || p.plus) {
+    p.ept = 4;  // the histogram and the stratified fills have one shape
   } else if (p.ept == 0) {
     st = autotune(c, p);
     if (st) return st;
@@ -510,10 +677,10 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
     return VEGAS_OK;
   }
   char kb[400];
-  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d%d:%llu:%u:%p:%p:h%d:%a:%a", ig, p.fp32,
-           mode, (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing, c->pdl,
+  snprintf(kb, sizeof kb, "graph:%d:%d:%d:%lld:%d:%d:%d:%a:%d%d:%llu:%u:%p:%p:h%d:%a:%a:p%d:%d:%p",
+           ig, p.fp32, mode, (long long)ncall, itmx, p.ept, c->adapt, c->alpha, c->timing, c->pdl,
            (unsigned long long)c->seed, c->batch, c->ws, (void*)c->stream, p.nhist, c->hist_lo,
-           c->hist_hi);
+           c->hist_hi, p.plus, c->beta_j, c->plus_mem);
   const std::string key(kb);
   GraphEntry* ge = find_entry(c, key);
   if (!ge) {
@@ -734,6 +901,7 @@ void vegas_free(vegas_ctx* c) {
   clear_graphs(c);
   if (c->ws && !c->ws_external) cudaFree(c->ws);
   if (c->fixed) cudaFree(c->fixed);
+  if (c->plus_mem) cudaFree(c->plus_mem);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -776,6 +944,20 @@ int vegas_set_option(vegas_ctx* c, int key, double v) {
       c->pdl = (int)v;
       clear_graphs(c);
       return VEGAS_OK;
+    case VEGAS_OPT_STRAT:
+      if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
+      if (c->stream) cudaStreamSynchronize(c->stream);
+      c->strat = (int)v;
+      clear_graphs(c);
+      return VEGAS_OK;
+    case VEGAS_OPT_BETA: {
+      const double j = 4.0 * v;
+      if (!(j >= 0.0 && j <= 4.0) || j != std::floor(j)) return VEGAS_EINVAL;
+      if (c->stream) cudaStreamSynchronize(c->stream);
+      c->beta_j = (int)j;
+      clear_graphs(c);
+      return VEGAS_OK;
+    }
     case VEGAS_OPT_BATCH_ID:
       if (v < 0.0 || v >= 16777216.0 || v != std::floor(v)) return VEGAS_EINVAL;
       c->batch = (uint32_t)v;
@@ -799,6 +981,53 @@ int vegas_workspace_size(const vegas_ctx* c, int64_t ncall, int itmx, size_t* by
   const int nhist = c->hist_nh > 0 ? c->hist_nh + 2 : 0;
   *bytes = std::max(workspace_bytes(c->ndim, c->nbins, ncall, itmx, 0, nhist),
                     workspace_bytes(c->ndim, c->nbins, ncall, itmx, 1, 0));
+  return VEGAS_OK;
+}
+
+int vegas_strat_get(vegas_ctx* c, int* nstrat, int64_t* ncubes, int32_t* counts, double* var) {
+  if (!c || !c->plus_valid) return VEGAS_EINVAL;
+  GV_TRY(cudaStreamSynchronize(c->stream));
+  if (nstrat) *nstrat = c->plus_s;
+  if (ncubes) *ncubes = c->plus_nh;
+  if (counts)
+    GV_TRY(cudaMemcpy(counts, c->pa.n, (size_t)c->plus_nh * 4, cudaMemcpyDeviceToHost));
+  if (var) GV_TRY(cudaMemcpy(var, c->pa.var, (size_t)c->plus_nh * 8, cudaMemcpyDeviceToHost));
+  return VEGAS_OK;
+}
+
+int vegas_strat_set(vegas_ctx* c, int64_t ncall, const int32_t* counts) {
+  if (!c || !counts || ncall < 8 || ncall > ((int64_t)1 << 30)) return VEGAS_EINVAL;
+  const int s = plus_nstrat(c->ndim, ncall);
+  const int64_t nh = ipow(s, c->ndim);
+  int64_t total = 0;
+  for (int64_t h = 0; h < nh; ++h) {
+    if (counts[h] < 2) return VEGAS_EINVAL;
+    total += counts[h];
+  }
+  if (total > ncall + 2 * nh) return VEGAS_EINVAL;
+  const int n_tiles = (int)((ncall + 2 * nh + GV_TILE - 1) / GV_TILE);
+  int st = ensure_plus(c, nh, n_tiles);
+  if (st) return st;
+  // the counts, the per-CTA exclusive bases and the total; then the layout
+  const int64_t nb = (nh + 255) / 256;
+  std::vector<long long> base((size_t)nb);
+  long long run = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    base[(size_t)b] = run;
+    for (int64_t h = b * 256; h < std::min(nh, (b + 1) * 256); ++h) run += counts[h];
+  }
+  GV_TRY(cudaMemcpyAsync(c->pa.n, counts, (size_t)nh * 4, cudaMemcpyHostToDevice, c->stream));
+  GV_TRY(cudaMemcpyAsync(c->pa.npart, base.data(), (size_t)nb * 8, cudaMemcpyHostToDevice,
+                         c->stream));
+  GV_TRY(cudaMemcpyAsync(c->pa.ncall_dev, &run, 8, cudaMemcpyHostToDevice, c->stream));
+  GvPlusArgs a = c->pa;
+  a.ncall = ncall;
+  a.n_tiles = n_tiles;
+  GV_TRY(gv::launch_plus_layout(a, c->stream, false));
+  GV_TRY(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+  c->plus_s = s;
+  c->plus_C = ncall;
+  c->plus_valid = true;
   return VEGAS_OK;
 }
 

@@ -102,6 +102,19 @@ struct GvFillArgs {
   int nhist = 0;
   double h_lo = 0.0, h_invw = 0.0;
   float h_lo_f = 0.0f, h_invw_f = 0.0f;
+  // VEGAS+ (stratified fill): s strata per axis, nh = s^d hypercubes; event
+  // e lies in the h with off[h] <= e < off[h+1]; tile t's first hypercube is
+  // tile_h0[t]; ab[h] = (C/(nh n_h), sqrt(1/(nh n_h))); *ncall_dev events in
+  // all; F[e] receives J g of event e
+  int p_s = 0;
+  long long p_nh = 0;
+  unsigned long long p_magic = 0ull;  // floor((2^64 - 1) / s)
+  float p_inv_s = 0.0f;
+  const long long* p_off = nullptr;
+  const double2* p_ab = nullptr;
+  const int* p_tile_h0 = nullptr;
+  const long long* p_ncall = nullptr;
+  double* p_F = nullptr;
 };
 
 // One slot's sum as a 192-bit two's complement integer with its exponent:
@@ -134,6 +147,7 @@ __host__ __device__ inline size_t gv_tickets_ints(int nacc) {
 struct GvReduceArgs {
   int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
   int nhist = 0;                 // histogram bins (0: none)
+  int plus = 0;                  // VEGAS+: sigma_k and the stage combination come later
   int refine_follows;            // 1: each axis is refined by the CTA that completes it
   long long ncall;
   double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration
@@ -415,7 +429,39 @@ struct GvHistArgs {
   double* out;             // [2][nhist] value, error (written at the last iteration)
 };
 
+// VEGAS+ after an iteration (see gv_plus.cu): per-hypercube statistics, the
+// next allocation, its layout.
+struct GvPlusArgs {
+  long long nh = 0;          // hypercubes
+  long long ncall = 0;       // the target C of the allocation
+  int beta_j = 3;            // damping beta = beta_j / 4
+  int uniform = 0;           // allocation: floor(C / nh) everywhere
+  int n_tiles = 0;           // tiles of the fill grid
+  int k = 0, last = 0;       // iteration in the stage
+  double inv_m1 = 0.0;       // 1 / (k) for chi2/dof at the last iteration
+  double inv_nh2 = 0.0;      // 1 / nh^2
+  const double* F = nullptr; // [events] J g per event
+  long long* off = nullptr;  // [nh + 1] first event of each hypercube, then the count
+  int* n = nullptr;          // [nh] events per hypercube
+  double2* ab = nullptr;     // [nh] (C/(nh n_h), sqrt(1/(nh n_h)))
+  int* tile_h0 = nullptr;    // [n_tiles] hypercube of each tile's first event
+  double* var = nullptr;     // [nh] sample variance of J g in each hypercube
+  double* dw = nullptr;      // [nh] allocation weights v^(beta/2)
+  double* part = nullptr;    // [CTAs][2] per-CTA sums of v/n and of the weights
+  long long* npart = nullptr;  // [CTAs] per-CTA sums of n, then their exclusive scan
+  long long* ncall_dev = nullptr;  // events of the allocation
+  double* scal = nullptr;    // [2] sigma_k^2 and the weights' sum D
+  int* tickets = nullptr;    // [2] last-CTA tickets (zero between uses)
+  double* per_iter = nullptr;  // [itmx][2]
+  GvState* st = nullptr;
+};
+
 namespace gv {
+cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl);
+cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl);
+cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl);
+cudaError_t launch_fill_plus(int ig, int fp32, const GvFillArgs& a, int n_tiles, size_t smem,
+                             cudaStream_t s, bool pdl);
 cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_tiles,
                                 size_t smem, cudaStream_t s, bool pdl);
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);

@@ -199,21 +199,66 @@ struct GvPair<double> {
 //   bins [d][GV_TILE] u16 (forward kernels of the d > 4 classes only)
 //   hh   [7][nhist] u32   histogram: w^2 limbs [3], w limbs [3] (the third
 //                         signed), the tile's bin exponents (with a histogram)
+//   po   [GV_PLUS_WIN] i32 hypercube offsets relative to the tile (VEGAS+)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// A tile of GV_TILE events meets at most GV_TILE/2 + 1 hypercubes (each has
+// at least 2 events): the window holds their offsets and the next one.
+#define GV_PLUS_WIN (GV_TILE / 2 + 4)
+
 struct GvFillSmem {
-  size_t hist, jac, ew, bins, hh, total;
+  size_t hist, jac, ew, bins, hh, po, total;
   __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem,
-                                 int nhist = 0) {
+                                 int nhist = 0, bool plus = false) {
     const size_t dN = (size_t)d * N;
     hist = 0;
     jac = gv_align16(hist + (forward ? dN * 16 : 0));
     ew = gv_align16(jac + (real_bytes == 8 ? dN * 8 : 0));
     bins = gv_align16(ew + dN * 16);
     hh = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
-    total = gv_align16(hh + (forward ? (size_t)nhist * 7 * 4 : 0));
+    po = gv_align16(hh + (forward ? (size_t)nhist * 7 * 4 : 0));
+    total = gv_align16(po + (plus ? (size_t)GV_PLUS_WIN * 4 : 0));
   }
 };
+
+// VEGAS+: the hypercube of the tile's local event `local` (the last window
+// entry at or below it), and the stratified words of hypercube h:
+// r' = floor((c_a 2^32 + r_a) / s) with c_a the base-s digits of h.
+__device__ __forceinline__ int gv_plus_cube(const int* s_off, int local) {
+  int lo = 0, hi = GV_PLUS_WIN;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_off[mid] <= local)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <int MAXD>
+__device__ __forceinline__ void gv_plus_words(unsigned h, int d, unsigned s, float inv_s,
+                                              unsigned long long magic, uint32_t (&r)[MAXD]) {
+#pragma unroll
+  for (int ax = 0; ax < MAXD; ++ax) {
+    if (ax < d) {
+      // h / s from a float estimate (h < 2^22 is exact in FP32), corrected to the floor
+      unsigned q = (unsigned)((float)h * inv_s);
+      if (q * s > h)
+        --q;
+      else if ((q + 1u) * s <= h)
+        ++q;
+      const unsigned c = h - q * s;
+      h = q;
+      // floor(X / s), X = c 2^32 + r < 2^54: the product with floor((2^64-1)/s)
+      // is the quotient or one less
+      const unsigned long long X = ((unsigned long long)c << 32) | r[ax];
+      unsigned long long t = __umul64hi(X, magic);
+      if ((t + 1ull) * s <= X) ++t;
+      r[ax] = (uint32_t)t;
+    }
+  }
+}
 
 // Stage the grid of one integration into shared memory.
 template <typename Real>
@@ -347,7 +392,7 @@ __device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
 // the persistent batched kernel, so that a tile's partial is the same
 // whichever kernel computes it.
 // ---------------------------------------------------------------------------
-template <int IG, typename Real, int EPT, int MAXD, bool HIST = false>
+template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
 __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile,
                                              unsigned char* smem, unsigned long long* red_u64,
                                              u128* red_128, uint32_t it) {
@@ -356,8 +401,12 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   using Pair = typename GvPair<Real>::T;
   const int d = a.ndim, N = a.nbins, dN = d * N;
   const int hb = HIST ? a.nhist : 0;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, hb);
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, hb, PLUS);
   unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);  // [6][hb] limbs
+  const int* s_off = reinterpret_cast<const int*>(smem + lay.po);
+  const long long ncall = PLUS ? *a.p_ncall : a.ncall;
+  const long long h0 = PLUS ? a.p_tile_h0[tile] : 0;
+  double qv[EPT];  // VEGAS+: the bins' quantity F b_h (w itself otherwise)
   int* hebin = reinterpret_cast<int*>(hh + 6 * hb);             // [hb] exponents
   Real h_lo, h_invw;
   if constexpr (sizeof(Real) == 4) {
@@ -387,10 +436,16 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     const int local = k * B + tid;
     const long long ev = tile0 + local;
     w[k] = 0.0;
+    qv[k] = 0.0;
     hbin[k] = 0;
-    if (ev < a.ncall) {
+    if (ev < ncall) {
       uint32_t r[MAXD];
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
+      long long hc = 0;
+      if constexpr (PLUS) {
+        hc = h0 + gv_plus_cube(s_off, local);
+        gv_plus_words<MAXD>((unsigned)hc, d, (unsigned)a.p_s, a.p_inv_s, a.p_magic, r);
+      }
       Real x[MAXD];
       int bin[MAXD];
       const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
@@ -398,13 +453,25 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
       if constexpr (HIST) hbin[k] = gv_hist_bin<Real>(gv_observable<IG, Real, MAXD>(x, K), h_lo,
                                                       h_invw, hb - 2);
-      const double wv = gv_weight(J, g);
+      double wv = gv_weight(J, g);
+      double qk = wv;
+      if constexpr (PLUS) {
+        // F = J g: stored for the hypercube statistics (0 if not finite); the
+        // estimate's weight F C/(nh n_h), the bins' F sqrt(1/(nh n_h))
+        const bool fin = gv_finite_bits(gv_abs_bits(wv));
+        a.p_F[ev] = fin ? wv : 0.0;
+        const double2 f = a.p_ab[hc];
+        qk = wv * f.y;
+        wv = wv * f.x;
+      }
       const unsigned long long ab = gv_abs_bits(wv);
-      if (gv_finite_bits(ab)) {
+      const unsigned long long qb = gv_abs_bits(qk);
+      if (gv_finite_bits(ab) && gv_finite_bits(qb)) {
         w[k] = wv;
+        qv[k] = qk;
         mx = ab > mx ? ab : mx;
-        if (ab != 0ull) {
-          const int F = gv_scale_exp(ab) + GV_BINE_OFF;
+        if (qb != 0ull) {
+          const int F = gv_scale_exp(qb) + GV_BINE_OFF;
 #pragma unroll
           for (int ax = 0; ax < MAXD; ++ax)
             if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
@@ -422,14 +489,17 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   if (E != GV_EMPTY) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      if (gv_abs_bits(w[k]) != 0ull) {
+      if (gv_abs_bits(w[k]) != 0ull || (PLUS && gv_abs_bits(qv[k]) != 0ull)) {
         const int local = k * B + tid;
         const GvDecoded dw = gv_decode(w[k]);
-        const unsigned long long P = gv_square_hi(dw.m);
+        const unsigned long long Pw = gv_square_hi(dw.m);
         s1 = add128(s1, gv_fixed_tile(dw, E));
-        s2 = add128(s2, gv_square_tile(dw, P, E));
-        // bins: w^2 at its bin's scale, a 56-bit value, as three 22-bit limbs
-        const int c = 2 * dw.e2 + 98 + 2 * GV_BINE_OFF;
+        s2 = add128(s2, gv_square_tile(dw, Pw, E));
+        // bins: w^2 (VEGAS+: q^2) at its bin's scale, a 56-bit value, as three
+        // 22-bit limbs
+        const GvDecoded dq = PLUS ? gv_decode(qv[k]) : dw;
+        const unsigned long long P = PLUS ? gv_square_hi(dq.m) : Pw;
+        const int c = 2 * dq.e2 + 98 + 2 * GV_BINE_OFF;
 #pragma unroll
         for (int ax = 0; ax < MAXD; ++ax) {
           if (ax < d) {
@@ -505,7 +575,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   }
 }
 
-template <int IG, typename Real, int EPT, int MAXD, bool HIST = false>
+template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
 __global__ void __launch_bounds__(GV_TILE / EPT)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
@@ -514,7 +584,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0);
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0, PLUS);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
   for (int k = threadIdx.x; k < 4 * d * N; k += B) hist[k] = 0u;
   if constexpr (HIST) {
@@ -524,9 +594,24 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
   gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
   gv_stage_grid<Real>(a.grid, d, N, reinterpret_cast<double*>(smem + lay.jac),
                       reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew), threadIdx.x, B);
+  if constexpr (PLUS) {
+    // the offsets of the hypercubes this tile can meet, relative to its first
+    // event and clamped to [-1, GV_TILE + 1]
+    int* s_off = reinterpret_cast<int*>(smem + lay.po);
+    const long long h0 = a.p_tile_h0[blockIdx.x];
+    const long long t0 = (long long)blockIdx.x * GV_TILE;
+    for (int j = threadIdx.x; j < GV_PLUS_WIN; j += B) {
+      int v = GV_TILE + 1;
+      if (h0 + j <= a.p_nh) {
+        const long long o = a.p_off[h0 + j] - t0;
+        v = o < -1 ? -1 : (o > GV_TILE ? GV_TILE + 1 : (int)o);
+      }
+      s_off[j] = v;
+    }
+  }
   const uint32_t it = (uint32_t)a.st->it;
   __syncthreads();
-  gv_fill_tile<IG, Real, EPT, MAXD, HIST>(a, blockIdx.x, smem, red_u64, red_128, it);
+  gv_fill_tile<IG, Real, EPT, MAXD, HIST, PLUS>(a, blockIdx.x, smem, red_u64, red_128, it);
 }
 
 // ---------------------------------------------------------------------------

@@ -9,10 +9,10 @@ static cudaError_t gv_prepare(KernelT k, size_t smem) {
   return cudaSuccess;
 }
 
-template <int IG, typename Real, int EPT, int MAXD, bool HIST = false>
+template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
 static cudaError_t gv_launch_fill_t(const GvFillArgs& a, int n_tiles, size_t smem,
                                     cudaStream_t s, bool pdl) {
-  auto k = gv_fill_kernel<IG, Real, EPT, MAXD, HIST>;
+  auto k = gv_fill_kernel<IG, Real, EPT, MAXD, HIST, PLUS>;
   cudaError_t e = gv_prepare(k, smem);
   if (e != cudaSuccess) return e;
   return gv_launch(k, dim3(n_tiles), dim3(GV_TILE / EPT), smem, s, pdl, a);
@@ -51,6 +51,32 @@ static cudaError_t gv_launch_fill_hist_t(const GvFillArgs& a, int n_tiles, size_
   if (a.ndim <= 16) return gv_launch_fill_t<IG, Real, 4, 16, true>(a, n_tiles, smem, s, pdl);
   return cudaErrorInvalidValue;
 }
+
+// The stratified (VEGAS+) fill: 4 events per thread.
+template <int IG, typename Real>
+static cudaError_t gv_launch_fill_plus_t(const GvFillArgs& a, int n_tiles, size_t smem,
+                                         cudaStream_t s, bool pdl) {
+  if (a.ndim <= 4 && IG != GV_EE3J)
+    return gv_launch_fill_t<IG, Real, 4, 4, false, true>(a, n_tiles, smem, s, pdl);
+  if (a.ndim <= 8) return gv_launch_fill_t<IG, Real, 4, 8, false, true>(a, n_tiles, smem, s, pdl);
+  if (a.ndim <= 16)
+    return gv_launch_fill_t<IG, Real, 4, 16, false, true>(a, n_tiles, smem, s, pdl);
+  return cudaErrorInvalidValue;
+}
+
+#define GV_DEFINE_FILL_PLUS_LAUNCHER(REAL, SUF)                                               \
+  namespace gv {                                                                              \
+  cudaError_t launch_fill_plus_##SUF(int ig, const GvFillArgs& a, int n_tiles, size_t smem,   \
+                                     cudaStream_t s, bool pdl) {                              \
+    switch (ig) {                                                                             \
+      case GV_GAUSS: return gv_launch_fill_plus_t<GV_GAUSS, REAL>(a, n_tiles, smem, s, pdl);  \
+      case GV_DY: return gv_launch_fill_plus_t<GV_DY, REAL>(a, n_tiles, smem, s, pdl);        \
+      case GV_EE3J: return gv_launch_fill_plus_t<GV_EE3J, REAL>(a, n_tiles, smem, s, pdl);    \
+      case GV_DYNLO: return gv_launch_fill_plus_t<GV_DYNLO, REAL>(a, n_tiles, smem, s, pdl);  \
+    }                                                                                         \
+    return cudaErrorInvalidValue;                                                             \
+  }                                                                                           \
+  }
 
 #define GV_DEFINE_FILL_HIST_LAUNCHER(REAL, SUF)                                               \
   namespace gv {                                                                              \

@@ -1,0 +1,222 @@
+// gv_plus.cu -- VEGAS+ (adaptive stratified sampling on the VEGAS map;
+// Lepage, J. Comput. Phys. 439 (2021) 110386, a later form of the VEGAS
+// method cited in Section 2.1) after each iteration:
+//   stats:  one thread per hypercube sums J g over its events in event order
+//           (FP64, sequential: the same sums the oracle forms), its sample
+//           variance v_h, v_h/n_h and the allocation weight v_h^(beta/2);
+//           the CTA that completes the grid (ticket) forms
+//           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights, writes
+//           sigma_k and, at the last iteration, combines the stage;
+//   alloc:  n_h = max(2, floor(C d_h / D)) (floor(C/nh) if D = 0 or for the
+//           uniform start), per-CTA event counts; the completing CTA scans
+//           them (exact integers);
+//   layout: the offsets of the hypercubes, (C/(nh n_h), sqrt(1/(nh n_h))) and
+//           each tile's first hypercube for the next fill.
+// Every sum over hypercubes has a shape fixed by nh alone, every count is an
+// integer, and no CTA waits for another: the last one to arrive does the rest.
+#include "gv_combine.cuh"
+
+namespace {
+
+constexpr int kT = 256;  // threads per CTA, one hypercube each
+
+// v^(j/8) (beta = j/4) from correctly rounded operations only: v = t 2^(8q)
+// with t in [1/2, 128) rounded to FP32, three FP32 square roots, j - 1 FP32
+// products, and 2^(q j) exactly.
+__device__ __forceinline__ double plus_weight(double v, int j) {
+  if (j == 0) return 1.0;
+  if (!(v > 0.0)) return 0.0;
+  int e;
+  const double m = frexp(v, &e);
+  const int q = e >= 0 ? e / 8 : -((-e + 7) / 8);
+  const int r = e - 8 * q;
+  const float t = __double2float_rn(ldexp(m, r));
+  const float y = __fsqrt_rn(__fsqrt_rn(__fsqrt_rn(t)));
+  float p = y;
+  for (int k = 1; k < j; ++k) p = __fmul_rn(p, y);
+  return ldexp((double)p, q * j);
+}
+
+// Sum over the CTA in a fixed tree; the result in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* s) {
+  const int t = threadIdx.x;
+  s[t] = v;
+  for (int w = kT / 2; w > 0; w >>= 1) {
+    __syncthreads();
+    if (t < w) s[t] += s[t + w];
+  }
+  __syncthreads();
+  const double r = s[0];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive prefix sum over the CTA (integers: any order is exact).
+__device__ __forceinline__ long long block_exscan(long long v, long long* s, long long* total) {
+  const int t = threadIdx.x;
+  s[t] = v;
+  __syncthreads();
+  for (int w = 1; w < kT; w <<= 1) {
+    const long long add = t >= w ? s[t - w] : 0ll;
+    __syncthreads();
+    s[t] += add;
+    __syncthreads();
+  }
+  const long long incl = s[t];
+  *total = s[kT - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// The completing CTA: the sum of nb per-CTA values in CTA order, each thread
+// taking a contiguous run, then the fixed tree.
+__device__ __forceinline__ double sum_parts(const double* part, int stride, int nb, double* s) {
+  const int chunk = (nb + kT - 1) / kT;
+  const int i0 = threadIdx.x * chunk, i1 = min(nb, i0 + chunk);
+  double v = 0.0;
+  for (int i = i0; i < i1; ++i) v += __ldcg(part + (size_t)i * stride);
+  return block_sum(v, s);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
+  __shared__ double s_red[kT];
+  __shared__ int s_last;
+  gv_wait_prior_grid();  // the fill's J g values and the reduce's I_k
+  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
+  double vn = 0.0, dd = 0.0;
+  if (h < a.nh) {
+    const long long o = a.off[h];
+    const int m = a.n[h];
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double f = a.F[o + j];
+      s1 += f;
+      s2 += f * f;
+    }
+    const double nd = (double)m;
+    double v = (s2 - s1 * s1 / nd) / (nd - 1.0);
+    v = v > 0.0 ? v : 0.0;
+    a.var[h] = v;
+    vn = v / nd;
+    dd = plus_weight(v, a.beta_j);
+    a.dw[h] = dd;
+  }
+  gv_allow_next_grid();
+  vn = block_sum(vn, s_red);
+  dd = block_sum(dd, s_red);
+  if (threadIdx.x == 0) {
+    a.part[2 * (size_t)blockIdx.x] = vn;
+    a.part[2 * (size_t)blockIdx.x + 1] = dd;
+    __threadfence();
+    s_last = atomicAdd(a.tickets, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();  // the other CTAs' sums, published before their tickets
+  const int nb = gridDim.x;
+  const double V = sum_parts(a.part, 2, nb, s_red);
+  const double D = sum_parts(a.part + 1, 2, nb, s_red);
+  if (threadIdx.x == 0) {
+    a.tickets[0] = 0;
+    const double var_k = V * a.inv_nh2;
+    a.scal[0] = var_k;
+    a.scal[1] = D;
+    a.per_iter[2 * a.k + 1] = var_k > 0.0 ? sqrt(var_k) : 0.0;
+    __threadfence_block();
+  }
+  __syncthreads();
+  if (a.last && threadIdx.x < 32)
+    combine_stage_warp(a.per_iter, 2, a.k + 1, a.inv_m1, a.st, false);
+}
+
+__global__ void __launch_bounds__(kT) gv_plus_alloc_kernel(const GvPlusArgs a) {
+  __shared__ long long s_scan[kT];
+  __shared__ int s_last;
+  gv_wait_prior_grid();  // the weights and their sum
+  const double D = a.uniform ? 0.0 : __ldcg(a.scal + 1);
+  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
+  long long m = 0;
+  if (h < a.nh) {
+    long long k;
+    if (D > 0.0) {
+      const double x = (double)a.ncall * __ldcg(a.dw + h) / D;
+      k = (long long)floor(x);
+    } else {
+      k = a.ncall / a.nh;
+    }
+    m = k > 2 ? k : 2;
+    a.n[h] = (int)m;
+  }
+  gv_allow_next_grid();
+  long long tot;
+  block_exscan(m, s_scan, &tot);
+  if (threadIdx.x == 0) {
+    a.npart[blockIdx.x] = tot;
+    __threadfence();
+    s_last = atomicAdd(a.tickets + 1, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // exclusive scan of the per-CTA counts, in place
+  const int nb = gridDim.x;
+  const int chunk = (nb + kT - 1) / kT;
+  const int i0 = threadIdx.x * chunk, i1 = min(nb, i0 + chunk);
+  long long run = 0;
+  for (int i = i0; i < i1; ++i) run += __ldcg(a.npart + i);
+  long long all;
+  long long base = block_exscan(run, s_scan, &all);
+  for (int i = i0; i < i1; ++i) {
+    const long long v = __ldcg(a.npart + i);
+    a.npart[i] = base;
+    base += v;
+  }
+  if (threadIdx.x == 0) {
+    a.tickets[1] = 0;
+    *a.ncall_dev = all;
+  }
+}
+
+__global__ void __launch_bounds__(kT) gv_plus_layout_kernel(const GvPlusArgs a) {
+  __shared__ long long s_scan[kT];
+  gv_wait_prior_grid();  // the counts and the per-CTA bases
+  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
+  const long long m = h < a.nh ? (long long)a.n[h] : 0ll;
+  long long tot;
+  const long long o = __ldcg(a.npart + blockIdx.x) + block_exscan(m, s_scan, &tot);
+  if (h < a.nh) {
+    a.off[h] = o;
+    const double nhd = (double)a.nh * (double)m;
+    a.ab[h] = make_double2((double)a.ncall / nhd, sqrt(1.0 / nhd));
+    // the tiles whose first event lies in this hypercube
+    for (long long t = (o + GV_TILE - 1) / GV_TILE; t * GV_TILE < o + m; ++t)
+      a.tile_h0[t] = (int)h;
+    if (h == a.nh - 1) {
+      a.off[a.nh] = o + m;
+      // tiles past the last event start in the last hypercube (they hold no event)
+      for (long long t = (o + m + GV_TILE - 1) / GV_TILE; t < a.n_tiles; ++t)
+        a.tile_h0[t] = (int)h;
+    }
+  }
+}
+
+namespace gv {
+
+cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
+  const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
+  return gv_launch(gv_plus_stats_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+}
+
+cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
+  const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
+  return gv_launch(gv_plus_alloc_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+}
+
+cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
+  const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
+  return gv_launch(gv_plus_layout_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+}
+
+}  // namespace gv

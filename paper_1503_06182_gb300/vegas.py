@@ -22,7 +22,7 @@ VEGAS_ENONFINITE, VEGAS_EDEVICE, VEGAS_ESTATE = -5, -6, -7
 VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J, VEGAS_DY_NLO = 0, 1, 2, 3
 VEGAS_OPT_ALPHA, VEGAS_OPT_PRECISION, VEGAS_OPT_ADAPT, VEGAS_OPT_EPT = 0, 1, 2, 3
 VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH, VEGAS_OPT_TIMING, VEGAS_OPT_BATCH_ID = 4, 5, 6, 7
-VEGAS_OPT_PDL = 8
+VEGAS_OPT_PDL, VEGAS_OPT_STRAT, VEGAS_OPT_BETA = 8, 9, 10
 VEGAS_KERNEL_FILL, VEGAS_KERNEL_REDUCE, VEGAS_KERNEL_REFINE = 0, 1, 2
 VEGAS_NGRAD = 5
 VEGAS_MAX_PARAMS = 16
@@ -84,6 +84,8 @@ def lib():
                                          C.c_int, _u32p], C.c_int),
             "vegas_last_sums": ([_vp, _dp], C.c_int),
             "vegas_hist_set": ([_vp, C.c_int, C.c_double, C.c_double], C.c_int),
+            "vegas_strat_get": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), _vp, _vp], C.c_int),
+            "vegas_strat_set": ([_vp, C.c_int64, _vp], C.c_int),
             "vegas_hist_get": ([_vp, _vp, _vp, _vp], C.c_int),
             "vegas_kernel_time": ([_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                    C.c_int], C.c_int),
@@ -270,6 +272,21 @@ def vegas_hist_get(h, nbins: int):
     return val, err, last
 
 
+def vegas_strat_get(h):
+    """(strata per axis, counts[nh] for the next iteration, var[nh] of the last)."""
+    s, nh = C.c_int(), C.c_int64()
+    _check(lib().vegas_strat_get(h, C.byref(s), C.byref(nh), None, None), "vegas_strat_get")
+    counts = np.zeros(nh.value, np.int32)
+    var = np.zeros(nh.value)
+    _check(lib().vegas_strat_get(h, None, None, _ptr(counts), _ptr(var)), "vegas_strat_get")
+    return s.value, counts, var
+
+
+def vegas_strat_set(h, ncall: int, counts) -> None:
+    counts = np.ascontiguousarray(counts, np.int32)
+    _check(lib().vegas_strat_set(h, int(ncall), _ptr(counts)), "vegas_strat_set")
+
+
 def vegas_kernel_time(h, kernel: int, reset: bool = False):
     ms = C.c_double()
     n = C.c_int64()
@@ -405,6 +422,13 @@ class Vegas:
         vegas_hist_set(self.h, nbins, lo, hi)
         self._hist_n = int(nbins)
         return self
+
+    def strat(self):
+        """VEGAS+ state: (strata per axis, allocation, last per-hypercube variances)."""
+        return vegas_strat_get(self.h)
+
+    def strat_set(self, ncall: int, counts) -> None:
+        vegas_strat_set(self.h, ncall, counts)
 
     def hist(self):
         """(value, error, last_sums) of the last stage's histogram."""
