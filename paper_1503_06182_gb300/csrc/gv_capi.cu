@@ -158,7 +158,9 @@ struct vegas_ctx {
   long long plus_nh = 0, plus_C = 0;
   int plus_s = 0, plus_tiles = 0;
   bool plus_valid = false;
+  long long plus_tab_C = 0;  // the C of the ab table on the device (0: none)
   GvPlusArgs pa;  // device arrays of the allocation (pointers only)
+  GvPlusFill* plus_fill = nullptr;  // the stratified fill's data (device)
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -299,17 +301,7 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
     a.h_lo_f = (float)c->hist_lo;
     a.h_invw_f = (float)invw;
   }
-  if (p.plus) {
-    a.p_s = p.s;
-    a.p_nh = p.nh;
-    a.p_magic = ~0ull / (unsigned long long)p.s;
-    a.p_inv_s = 1.0f / (float)p.s;
-    a.p_off = c->pa.off;
-    a.p_ab = c->pa.ab;
-    a.p_tile_h0 = c->pa.tile_h0;
-    a.p_ncall = c->pa.ncall_dev;
-    a.p_F = p.F;
-  }
+  if (p.plus) a.plus = c->plus_fill;
   return a;
 }
 
@@ -357,6 +349,10 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   off = align256(off + (size_t)nb * 8);
   const size_t o_sc = off;
   off = align256(off + 64);
+  const size_t o_pf = off;
+  off = align256(off + sizeof(GvPlusFill));
+  const size_t o_tab = off;
+  off = align256(off + (size_t)GV_PLUS_NTAB * 8 * 3);
   if (cudaMalloc(&c->plus_mem, off) != cudaSuccess) {
     cudaGetLastError();
     c->plus_mem = nullptr;
@@ -374,11 +370,21 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   a.dw = (double*)(b + o_dw);
   a.part = (double*)(b + o_part);
   a.npart = (long long*)(b + o_np);
+  // 64 bytes: the event count, three scalars, two tickets
   a.ncall_dev = (long long*)(b + o_sc);
   a.scal = (double*)(b + o_sc + 8);
-  a.tickets = (int*)(b + o_sc + 24);
+  a.tickets = (int*)(b + o_sc + 32);
+  c->plus_fill = (GvPlusFill*)(b + o_pf);
+  a.inv = (const double*)(b + o_tab);
+  a.abtab = (const double2*)(b + o_tab + (size_t)GV_PLUS_NTAB * 8);
   GV_TRY(cudaMemsetAsync(c->plus_mem, 0, off, c->stream));
+  std::vector<double> inv(GV_PLUS_NTAB, 0.0);
+  for (int n = 1; n < GV_PLUS_NTAB; ++n) inv[n] = 1.0 / (double)n;
+  // a pageable copy is staged before cudaMemcpyAsync returns
+  GV_TRY(cudaMemcpyAsync((void*)a.inv, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice,
+                         c->stream));
   c->plus_nh = nh;
+  c->plus_tab_C = 0;
   c->plus_tiles = n_tiles;
   return VEGAS_OK;
 }
@@ -558,11 +564,43 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   return VEGAS_OK;
 }
 
+// VEGAS+: the table of (C/(nh n), sqrt(1/(nh n))) for n < GV_PLUS_NTAB, in
+// the same FP64 operations as for any other n.
+int upload_abtab(vegas_ctx* c, long long C, long long nh) {
+  if (c->plus_tab_C == C) return VEGAS_OK;
+  std::vector<double> t(2 * (size_t)GV_PLUS_NTAB, 0.0);
+  for (int n = 1; n < GV_PLUS_NTAB; ++n) {
+    const double nhd = (double)nh * (double)n;
+    t[2 * (size_t)n] = (double)C / nhd;
+    t[2 * (size_t)n + 1] = std::sqrt(1.0 / nhd);
+  }
+  // a pageable copy is staged before cudaMemcpyAsync returns
+  GV_TRY(cudaMemcpyAsync((void*)c->pa.abtab, t.data(), t.size() * 8, cudaMemcpyHostToDevice,
+                         c->stream));
+  c->plus_tab_C = C;
+  return VEGAS_OK;
+}
+
 // VEGAS+: make sure the allocation for ncall exists (uniform if it is new).
 int ensure_allocation(vegas_ctx* c, const Plan& p) {
   int st = ensure_plus(c, p.nh, p.n_tiles);
   if (st) return st;
+  st = upload_abtab(c, p.ncall, p.nh);
+  if (st) return st;
   c->plus_s = p.s;
+  // the fill's view of the allocation (the workspace may have moved)
+  GvPlusFill f;
+  f.s = p.s;
+  f.inv_s = 1.0f / (float)p.s;
+  f.nh = p.nh;
+  f.magic = ~0ull / (unsigned long long)p.s;
+  f.off = c->pa.off;
+  f.ab = c->pa.ab;
+  f.tile_h0 = c->pa.tile_h0;
+  f.ncall = c->pa.ncall_dev;
+  f.F = p.F;
+  // a pageable copy is staged before cudaMemcpyAsync returns
+  GV_TRY(cudaMemcpyAsync(c->plus_fill, &f, sizeof f, cudaMemcpyHostToDevice, c->stream));
   if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;
   GvPlusArgs a = plus_args(c, p, -1);
   a.uniform = 1;
@@ -1007,6 +1045,8 @@ int vegas_strat_set(vegas_ctx* c, int64_t ncall, const int32_t* counts) {
   if (total > ncall + 2 * nh) return VEGAS_EINVAL;
   const int n_tiles = (int)((ncall + 2 * nh + GV_TILE - 1) / GV_TILE);
   int st = ensure_plus(c, nh, n_tiles);
+  if (st) return st;
+  st = upload_abtab(c, ncall, nh);
   if (st) return st;
   // the counts, the per-CTA exclusive bases and the total; then the layout
   const int64_t nb = (nh + 255) / 256;

@@ -85,6 +85,22 @@ struct GvGridLayout {
   }
 };
 
+// VEGAS+ data of the stratified fill: s strata per axis, nh = s^d
+// hypercubes; event e lies in the h with off[h] <= e < off[h+1]; tile t's
+// first hypercube is tile_h0[t]; ab[h] = (C/(nh n_h), sqrt(1/(nh n_h)));
+// *ncall events in all; F[e] receives J g of event e.
+struct GvPlusFill {
+  int s;
+  float inv_s;
+  long long nh;
+  unsigned long long magic;  // floor((2^64 - 1) / s)
+  const long long* off;
+  const double2* ab;
+  const int* tile_h0;
+  const long long* ncall;
+  double* F;
+};
+
 // Arguments of the fill kernels (forward and adjoint).
 struct GvFillArgs {
   int ndim, nbins, nch, nacc;
@@ -102,19 +118,10 @@ struct GvFillArgs {
   int nhist = 0;
   double h_lo = 0.0, h_invw = 0.0;
   float h_lo_f = 0.0f, h_invw_f = 0.0f;
-  // VEGAS+ (stratified fill): s strata per axis, nh = s^d hypercubes; event
-  // e lies in the h with off[h] <= e < off[h+1]; tile t's first hypercube is
-  // tile_h0[t]; ab[h] = (C/(nh n_h), sqrt(1/(nh n_h))); *ncall_dev events in
-  // all; F[e] receives J g of event e
-  int p_s = 0;
-  long long p_nh = 0;
-  unsigned long long p_magic = 0ull;  // floor((2^64 - 1) / s)
-  float p_inv_s = 0.0f;
-  const long long* p_off = nullptr;
-  const double2* p_ab = nullptr;
-  const int* p_tile_h0 = nullptr;
-  const long long* p_ncall = nullptr;
-  double* p_F = nullptr;
+  // VEGAS+: the stratified fill's data (device memory; nullptr otherwise).
+  // Kept behind one pointer: the fields inline cost the plain fill kernels
+  // registers.
+  const struct GvPlusFill* plus = nullptr;
 };
 
 // One slot's sum as a 192-bit two's complement integer with its exponent:
@@ -429,6 +436,8 @@ struct GvHistArgs {
   double* out;             // [2][nhist] value, error (written at the last iteration)
 };
 
+#define GV_PLUS_NTAB 4096  // per-count tables of the VEGAS+ kernels (larger counts: computed)
+
 // VEGAS+ after an iteration (see gv_plus.cu): per-hypercube statistics, the
 // next allocation, its layout.
 struct GvPlusArgs {
@@ -450,7 +459,9 @@ struct GvPlusArgs {
   double* part = nullptr;    // [CTAs][2] per-CTA sums of v/n and of the weights
   long long* npart = nullptr;  // [CTAs] per-CTA sums of n, then their exclusive scan
   long long* ncall_dev = nullptr;  // events of the allocation
-  double* scal = nullptr;    // [2] sigma_k^2 and the weights' sum D
+  double* scal = nullptr;    // [2] sigma_k^2, the weights' sum D
+  const double* inv = nullptr;    // [GV_PLUS_NTAB] 1/n (entry 0 unused)
+  const double2* abtab = nullptr; // [GV_PLUS_NTAB] ab for n_h = n (C and nh of the allocation)
   int* tickets = nullptr;    // [2] last-CTA tickets (zero between uses)
   double* per_iter = nullptr;  // [itmx][2]
   GvState* st = nullptr;

@@ -404,8 +404,9 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, hb, PLUS);
   unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);  // [6][hb] limbs
   const int* s_off = reinterpret_cast<const int*>(smem + lay.po);
-  const long long ncall = PLUS ? *a.p_ncall : a.ncall;
-  const long long h0 = PLUS ? a.p_tile_h0[tile] : 0;
+  const GvPlusFill* pf = a.plus;
+  const long long ncall = PLUS ? *pf->ncall : a.ncall;
+  const long long h0 = PLUS ? pf->tile_h0[tile] : 0;
   double qv[EPT];  // VEGAS+: the bins' quantity F b_h (w itself otherwise)
   int* hebin = reinterpret_cast<int*>(hh + 6 * hb);             // [hb] exponents
   Real h_lo, h_invw;
@@ -436,7 +437,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     const int local = k * B + tid;
     const long long ev = tile0 + local;
     w[k] = 0.0;
-    qv[k] = 0.0;
+    if constexpr (PLUS) qv[k] = 0.0;
     hbin[k] = 0;
     if (ev < ncall) {
       uint32_t r[MAXD];
@@ -444,7 +445,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       long long hc = 0;
       if constexpr (PLUS) {
         hc = h0 + gv_plus_cube(s_off, local);
-        gv_plus_words<MAXD>((unsigned)hc, d, (unsigned)a.p_s, a.p_inv_s, a.p_magic, r);
+        gv_plus_words<MAXD>((unsigned)hc, d, (unsigned)pf->s, pf->inv_s, pf->magic, r);
       }
       Real x[MAXD];
       int bin[MAXD];
@@ -454,24 +455,28 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       if constexpr (HIST) hbin[k] = gv_hist_bin<Real>(gv_observable<IG, Real, MAXD>(x, K), h_lo,
                                                       h_invw, hb - 2);
       double wv = gv_weight(J, g);
-      double qk = wv;
+      [[maybe_unused]] double qk = 0.0;
       if constexpr (PLUS) {
         // F = J g: stored for the hypercube statistics (0 if not finite); the
         // estimate's weight F C/(nh n_h), the bins' F sqrt(1/(nh n_h))
-        const bool fin = gv_finite_bits(gv_abs_bits(wv));
-        a.p_F[ev] = fin ? wv : 0.0;
-        const double2 f = a.p_ab[hc];
+        pf->F[ev] = gv_finite_bits(gv_abs_bits(wv)) ? wv : 0.0;
+        const double2 f = pf->ab[hc];
         qk = wv * f.y;
         wv = wv * f.x;
       }
       const unsigned long long ab = gv_abs_bits(wv);
-      const unsigned long long qb = gv_abs_bits(qk);
-      if (gv_finite_bits(ab) && gv_finite_bits(qb)) {
+      unsigned long long bb = ab;  // |the bins' quantity|
+      bool fin = gv_finite_bits(ab);
+      if constexpr (PLUS) {
+        bb = gv_abs_bits(qk);
+        fin = fin && gv_finite_bits(bb);
+      }
+      if (fin) {
         w[k] = wv;
-        qv[k] = qk;
+        if constexpr (PLUS) qv[k] = qk;
         mx = ab > mx ? ab : mx;
-        if (qb != 0ull) {
-          const int F = gv_scale_exp(qb) + GV_BINE_OFF;
+        if (bb != 0ull) {
+          const int F = gv_scale_exp(bb) + GV_BINE_OFF;
 #pragma unroll
           for (int ax = 0; ax < MAXD; ++ax)
             if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
@@ -592,18 +597,30 @@ __global__ void __launch_bounds__(GV_TILE / EPT)
     for (int k = threadIdx.x; k < 7 * a.nhist; k += B) hh[k] = 0u;
   }
   gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
+  if constexpr (PLUS) {
+    // VEGAS+ sizes the grid for the most events an allocation can have: a
+    // tile past this iteration's last event only leaves an empty partial
+    const long long t0 = (long long)blockIdx.x * GV_TILE;
+    if (t0 >= *a.plus->ncall) {
+      ulonglong2* out = a.part + (size_t)blockIdx.x * a.nacc;
+      for (int k = threadIdx.x; k < a.nacc; k += B) out[k] = make_ulonglong2(0ull, 0ull);
+      if (threadIdx.x == 0) a.tileE[blockIdx.x] = GV_EMPTY;
+      return;
+    }
+  }
   gv_stage_grid<Real>(a.grid, d, N, reinterpret_cast<double*>(smem + lay.jac),
                       reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew), threadIdx.x, B);
   if constexpr (PLUS) {
     // the offsets of the hypercubes this tile can meet, relative to its first
     // event and clamped to [-1, GV_TILE + 1]
     int* s_off = reinterpret_cast<int*>(smem + lay.po);
-    const long long h0 = a.p_tile_h0[blockIdx.x];
+    const GvPlusFill* pf = a.plus;
+    const long long h0 = pf->tile_h0[blockIdx.x];
     const long long t0 = (long long)blockIdx.x * GV_TILE;
     for (int j = threadIdx.x; j < GV_PLUS_WIN; j += B) {
       int v = GV_TILE + 1;
-      if (h0 + j <= a.p_nh) {
-        const long long o = a.p_off[h0 + j] - t0;
+      if (h0 + j <= pf->nh) {
+        const long long o = pf->off[h0 + j] - t0;
         v = o < -1 ? -1 : (o > GV_TILE ? GV_TILE + 1 : (int)o);
       }
       s_off[j] = v;

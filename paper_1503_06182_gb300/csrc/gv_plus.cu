@@ -3,7 +3,9 @@
 // method cited in Section 2.1) after each iteration:
 //   stats:  one thread per hypercube sums J g over its events in event order
 //           (FP64, sequential: the same sums the oracle forms), its sample
-//           variance v_h, v_h/n_h and the allocation weight v_h^(beta/2);
+//           variance v_h, v_h/n_h and the allocation weight v_h^(beta/2)
+//           (divisions by n and n - 1 as products with tabulated reciprocals:
+//           FP64 division is a long sequence on this chip's FP64 pipe);
 //           the CTA that completes the grid (ticket) forms
 //           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights, writes
 //           sigma_k and, at the last iteration, combines the stage;
@@ -23,49 +25,81 @@ constexpr int kT = 256;  // threads per CTA, one hypercube each
 // v^(j/8) (beta = j/4) from correctly rounded operations only: v = t 2^(8q)
 // with t in [1/2, 128) rounded to FP32, three FP32 square roots, j - 1 FP32
 // products, and 2^(q j) exactly.
+// The exponent split and the final scaling are exact edits of the exponent
+// field (frexp and ldexp, written as integer operations: their library forms
+// spend FP64 instructions, which this chip has few of); a subnormal v takes
+// the library path.
 __device__ __forceinline__ double plus_weight(double v, int j) {
   if (j == 0) return 1.0;
   if (!(v > 0.0)) return 0.0;
+  const long long bits = __double_as_longlong(v);
+  const int eb = (int)(bits >> 52);  // biased exponent (v > 0)
   int e;
-  const double m = frexp(v, &e);
-  const int q = e >= 0 ? e / 8 : -((-e + 7) / 8);
-  const int r = e - 8 * q;
-  const float t = __double2float_rn(ldexp(m, r));
+  double m2r;  // m 2^r, m in [1/2, 1)
+  int q, r;
+  if (eb == 0) {
+    const double m = frexp(v, &e);
+    q = e >= 0 ? e / 8 : -((-e + 7) / 8);
+    r = e - 8 * q;
+    m2r = ldexp(m, r);
+  } else {
+    e = eb - 1022;  // v = m 2^e
+    q = e >= 0 ? e / 8 : -((-e + 7) / 8);
+    r = e - 8 * q;
+    m2r = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | ((long long)(1022 + r) << 52));
+  }
+  const float t = __double2float_rn(m2r);
   const float y = __fsqrt_rn(__fsqrt_rn(__fsqrt_rn(t)));
   float p = y;
   for (int k = 1; k < j; ++k) p = __fmul_rn(p, y);
-  return ldexp((double)p, q * j);
+  // (double)p 2^(q j): p is normal and so is the product (|q j| <= 520)
+  const long long pb = __double_as_longlong((double)p);
+  return __longlong_as_double(pb + ((long long)(q * j) << 52));
 }
 
-// Sum over the CTA in a fixed tree; the result in thread 0.
+// Sum over the CTA in a fixed order: a butterfly within each warp, then the
+// eight warp sums in warp order (every thread gets the result).
 __device__ __forceinline__ double block_sum(double v, double* s) {
-  const int t = threadIdx.x;
-  s[t] = v;
-  for (int w = kT / 2; w > 0; w >>= 1) {
-    __syncthreads();
-    if (t < w) s[t] += s[t + w];
-  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s[wid] = v;
   __syncthreads();
-  const double r = s[0];
+  double r = s[0];
+#pragma unroll
+  for (int w = 1; w < kT / 32; ++w) r += s[w];
   __syncthreads();
   return r;
 }
 
 // Exclusive prefix sum over the CTA (integers: any order is exact).
 __device__ __forceinline__ long long block_exscan(long long v, long long* s, long long* total) {
-  const int t = threadIdx.x;
-  s[t] = v;
-  __syncthreads();
-  for (int w = 1; w < kT; w <<= 1) {
-    const long long add = t >= w ? s[t - w] : 0ll;
-    __syncthreads();
-    s[t] += add;
-    __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
   }
-  const long long incl = s[t];
-  *total = s[kT - 1];
+  if (lane == 31) s[wid] = x;
   __syncthreads();
-  return incl - v;
+  long long base = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kT / 32; ++w) {
+    const long long sw = s[w];
+    base += w < wid ? sw : 0ll;
+    all += sw;
+  }
+  __syncthreads();
+  *total = all;
+  return base + x - v;
+}
+
+// 1/n and 1/(n - 1) beyond the tables (kept out of line, so that the common
+// path does not carry two FP64 divisions)
+__device__ __noinline__ void plus_recips(double n, double* inv_n, double* inv_m1) {
+  *inv_n = 1.0 / n;
+  *inv_m1 = 1.0 / (n - 1.0);
 }
 
 // The completing CTA: the sum of nb per-CTA values in CTA order, each thread
@@ -81,7 +115,7 @@ __device__ __forceinline__ double sum_parts(const double* part, int stride, int 
 }  // namespace
 
 __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
-  __shared__ double s_red[kT];
+  __shared__ double s_red[kT / 32];
   __shared__ int s_last;
   gv_wait_prior_grid();  // the fill's J g values and the reduce's I_k
   const long long h = (long long)blockIdx.x * kT + threadIdx.x;
@@ -96,10 +130,17 @@ __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
       s2 += f * f;
     }
     const double nd = (double)m;
-    double v = (s2 - s1 * s1 / nd) / (nd - 1.0);
+    double inv_n, inv_m1;
+    if (m < GV_PLUS_NTAB) {
+      inv_n = __ldg(a.inv + m);
+      inv_m1 = __ldg(a.inv + m - 1);
+    } else {
+      plus_recips(nd, &inv_n, &inv_m1);
+    }
+    double v = (s2 - s1 * s1 * inv_n) * inv_m1;
     v = v > 0.0 ? v : 0.0;
     a.var[h] = v;
-    vn = v / nd;
+    vn = v * inv_n;
     dd = plus_weight(v, a.beta_j);
     a.dw[h] = dd;
   }
@@ -132,7 +173,7 @@ __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
 }
 
 __global__ void __launch_bounds__(kT) gv_plus_alloc_kernel(const GvPlusArgs a) {
-  __shared__ long long s_scan[kT];
+  __shared__ long long s_scan[kT / 32];
   __shared__ int s_last;
   gv_wait_prior_grid();  // the weights and their sum
   const double D = a.uniform ? 0.0 : __ldcg(a.scal + 1);
@@ -141,6 +182,9 @@ __global__ void __launch_bounds__(kT) gv_plus_alloc_kernel(const GvPlusArgs a) {
   if (h < a.nh) {
     long long k;
     if (D > 0.0) {
+      // a true division, as the rule states it: shares land on integers
+      // exactly (one hypercube, equal weights), where a product with 1/D
+      // would fall an ulp short and floor one event lower
       const double x = (double)a.ncall * __ldcg(a.dw + h) / D;
       k = (long long)floor(x);
     } else {
@@ -180,7 +224,7 @@ __global__ void __launch_bounds__(kT) gv_plus_alloc_kernel(const GvPlusArgs a) {
 }
 
 __global__ void __launch_bounds__(kT) gv_plus_layout_kernel(const GvPlusArgs a) {
-  __shared__ long long s_scan[kT];
+  __shared__ long long s_scan[kT / 32];
   gv_wait_prior_grid();  // the counts and the per-CTA bases
   const long long h = (long long)blockIdx.x * kT + threadIdx.x;
   const long long m = h < a.nh ? (long long)a.n[h] : 0ll;
@@ -188,8 +232,12 @@ __global__ void __launch_bounds__(kT) gv_plus_layout_kernel(const GvPlusArgs a) 
   const long long o = __ldcg(a.npart + blockIdx.x) + block_exscan(m, s_scan, &tot);
   if (h < a.nh) {
     a.off[h] = o;
-    const double nhd = (double)a.nh * (double)m;
-    a.ab[h] = make_double2((double)a.ncall / nhd, sqrt(1.0 / nhd));
+    if (m < GV_PLUS_NTAB) {
+      a.ab[h] = __ldg(a.abtab + m);
+    } else {
+      const double nhd = (double)a.nh * (double)m;
+      a.ab[h] = make_double2((double)a.ncall / nhd, sqrt(1.0 / nhd));
+    }
     // the tiles whose first event lies in this hypercube
     for (long long t = (o + GV_TILE - 1) / GV_TILE; t * GV_TILE < o + m; ++t)
       a.tile_h0[t] = (int)h;
