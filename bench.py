@@ -39,10 +39,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 72_192
+FILL_TRAFFIC_BYTES = 72_448
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "17108804428fdfa05074be1d68754cad1472bec79ee1da5974cf59b729838723"
+FILL_SOURCES_SHA256 = "93473324374847623a1538fcbbe157bc26b723c57e64e4917677dca854ef4a30"
 
 
 def _fill_traffic():
