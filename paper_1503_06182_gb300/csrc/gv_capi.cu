@@ -207,7 +207,9 @@ size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhis
   b += align256((size_t)n_tiles * nch * 4);
   b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
   b += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
-  if (plus_f) b += align256((size_t)ncall * 8);
+  // VEGAS+: per event J g (8 B), its hypercube (4 B), the segment sums (16 B)
+  if (plus_f) b += align256((size_t)ncall * 8) + align256((size_t)ncall * 4) +
+                   align256((size_t)ncall * 16);
   return b;
 }
 
@@ -270,7 +272,10 @@ struct Plan {
   int nhist;  // histogram bins with underflow and overflow (0: none)
   int plus, s;     // VEGAS+: strata per axis
   long long nh;    // hypercubes
+  long long cap;   // events the fill's grid can hold
   double* F;       // per-event J g (VEGAS+)
+  int* hc;         // per-event hypercube (VEGAS+)
+  double2* seg;    // segment sums (VEGAS+)
   int64_t ncall;
   size_t smem;
   ulonglong2* part;
@@ -315,6 +320,9 @@ GvPlusArgs plus_args(const vegas_ctx* c, const Plan& p, int k) {
   a.last = k == p.itmx - 1;
   a.inv_m1 = k > 0 ? 1.0 / (double)k : 0.0;
   a.F = p.F;
+  a.hc = p.hc;
+  a.seg = p.seg;
+  a.cap = p.cap;
   a.per_iter = p.per_iter;
   a.st = c->st;
   return a;
@@ -526,6 +534,8 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.s = 0;
   p.nh = 0;
   p.F = nullptr;
+  p.hc = nullptr;
+  p.seg = nullptr;
   int64_t cap = ncall;
   if (p.plus) {
     if (c->hist_nh > 0 || ncall < 8 || ncall > ((int64_t)1 << 30)) return VEGAS_EINVAL;
@@ -533,6 +543,7 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
     p.nh = ipow(p.s, c->ndim);
     cap = ncall + 2 * p.nh;
   }
+  p.cap = cap;
   const int64_t nt = (cap + GV_TILE - 1) / GV_TILE;
   if (nt > 0x7fffffff) return VEGAS_EINVAL;
   p.n_tiles = (int)nt;
@@ -559,6 +570,10 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   if (p.plus) {
     w += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
     p.F = (double*)w;
+    w += align256((size_t)cap * 8);
+    p.hc = (int*)w;
+    w += align256((size_t)cap * 4);
+    p.seg = (double2*)w;
   }
   p.ept = c->ept_opt;
   return VEGAS_OK;
@@ -599,6 +614,7 @@ int ensure_allocation(vegas_ctx* c, const Plan& p) {
   f.tile_h0 = c->pa.tile_h0;
   f.ncall = c->pa.ncall_dev;
   f.F = p.F;
+  f.hc = p.hc;
   // a pageable copy is staged before cudaMemcpyAsync returns
   GV_TRY(cudaMemcpyAsync(c->plus_fill, &f, sizeof f, cudaMemcpyHostToDevice, c->stream));
   if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;
@@ -627,6 +643,7 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
       // the hypercubes' statistics (sigma_k, the stage's combination), then
       // the next iteration's allocation and its layout
       const GvPlusArgs a = plus_args(c, p, k);
+      GV_TRY(gv::launch_plus_seg(a, c->stream, pdl));
       GV_TRY(gv::launch_plus_stats(a, c->stream, pdl));
       if (c->adapt) {
         GV_TRY(gv::launch_plus_alloc(a, c->stream, pdl));

@@ -99,6 +99,7 @@ struct GvPlusFill {
   const int* tile_h0;
   const long long* ncall;
   double* F;
+  int* hc;  // [events] the hypercube of each event
 };
 
 // Arguments of the fill kernels (forward and adjoint).
@@ -437,6 +438,7 @@ struct GvHistArgs {
 };
 
 #define GV_PLUS_NTAB 4096  // per-count tables of the VEGAS+ kernels (larger counts: computed)
+#define GV_PLUS_SEG 8      // events per lane in the VEGAS+ segment sums
 
 // VEGAS+ after an iteration (see gv_plus.cu): per-hypercube statistics, the
 // next allocation, its layout.
@@ -450,6 +452,10 @@ struct GvPlusArgs {
   double inv_m1 = 0.0;       // 1 / (k) for chi2/dof at the last iteration
   double inv_nh2 = 0.0;      // 1 / nh^2
   const double* F = nullptr; // [events] J g per event
+  const int* hc = nullptr;   // [events] hypercube per event
+  double2* seg = nullptr;    // [events] per GV_PLUS_SEG-event range: the sums of its
+                             // hypercube segments (sum F, sum F^2), in order
+  long long cap = 0;         // events the buffers hold
   long long* off = nullptr;  // [nh + 1] first event of each hypercube, then the count
   int* n = nullptr;          // [nh] events per hypercube
   double2* ab = nullptr;     // [nh] (C/(nh n_h), sqrt(1/(nh n_h)))
@@ -468,6 +474,7 @@ struct GvPlusArgs {
 };
 
 namespace gv {
+cudaError_t launch_plus_seg(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl);

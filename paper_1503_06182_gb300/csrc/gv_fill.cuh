@@ -460,6 +460,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
         // F = J g: stored for the hypercube statistics (0 if not finite); the
         // estimate's weight F C/(nh n_h), the bins' F sqrt(1/(nh n_h))
         pf->F[ev] = gv_finite_bits(gv_abs_bits(wv)) ? wv : 0.0;
+        pf->hc[ev] = (int)hc;
         const double2 f = pf->ab[hc];
         qk = wv * f.y;
         wv = wv * f.x;

@@ -1,11 +1,14 @@
 // gv_plus.cu -- VEGAS+ (adaptive stratified sampling on the VEGAS map;
 // Lepage, J. Comput. Phys. 439 (2021) 110386, a later form of the VEGAS
 // method cited in Section 2.1) after each iteration:
-//   stats:  one thread per hypercube sums J g over its events in event order
-//           (FP64, sequential: the same sums the oracle forms), its sample
-//           variance v_h, v_h/n_h and the allocation weight v_h^(beta/2)
-//           (divisions by n and n - 1 as products with tabulated reciprocals:
-//           FP64 division is a long sequence on this chip's FP64 pipe);
+//   seg:    each lane sums J g and its square over GV_PLUS_SEG consecutive
+//           events, in event order, split where the hypercube changes (every
+//           lane does the same number of steps: the FP64 pipe, which this chip
+//           has little of, does no work for idle lanes);
+//   stats:  one thread per hypercube adds its segments in range order, then
+//           forms its sample variance v_h, v_h/n_h and the allocation weight
+//           v_h^(beta/2) (divisions by n and n - 1 as products with tabulated
+//           reciprocals: FP64 division is a long sequence on the FP64 pipe);
 //           the CTA that completes the grid (ticket) forms
 //           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights, writes
 //           sigma_k and, at the last iteration, combines the stage;
@@ -57,17 +60,21 @@ __device__ __forceinline__ double plus_weight(double v, int j) {
   return __longlong_as_double(pb + ((long long)(q * j) << 52));
 }
 
-// Sum over the CTA in a fixed order: a butterfly within each warp, then the
-// eight warp sums in warp order (every thread gets the result).
+// Sum over the CTA in a fixed order, with few FP64 instructions (this chip's
+// FP64 pipe is narrow): warp 0's lane l adds the values of threads 8l..8l+7
+// in order, then a butterfly over the warp.  The result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* s) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) s[wid] = v;
+  s[threadIdx.x] = v;
   __syncthreads();
-  double r = s[0];
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    const double* q = s + 8 * threadIdx.x;
+    r = q[0];
 #pragma unroll
-  for (int w = 1; w < kT / 32; ++w) r += s[w];
+    for (int i = 1; i < 8; ++i) r += q[i];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) r += __shfl_xor_sync(0xffffffffu, r, m);
+  }
   __syncthreads();
   return r;
 }
@@ -114,20 +121,53 @@ __device__ __forceinline__ double sum_parts(const double* part, int stride, int 
 
 }  // namespace
 
+// Range r = events [r K, r K + K) (K = GV_PLUS_SEG): its segments, one per
+// hypercube it meets, at seg[r K + j] for the j-th hypercube from hc[r K].
+__global__ void __launch_bounds__(kT) gv_plus_seg_kernel(const GvPlusArgs a) {
+  gv_wait_prior_grid();  // the fill's J g values and hypercubes
+  const long long ncall = __ldcg(a.ncall_dev);
+  const long long r = (long long)blockIdx.x * kT + threadIdx.x;
+  const long long e0 = r * GV_PLUS_SEG;
+  gv_allow_next_grid();
+  if (e0 >= ncall) return;
+  const long long e1 = e0 + GV_PLUS_SEG < ncall ? e0 + GV_PLUS_SEG : ncall;
+  int hp = a.hc[e0];
+  long long j = e0;
+  double s1 = 0.0, s2 = 0.0;
+  for (long long e = e0; e < e1; ++e) {
+    const int h = a.hc[e];
+    if (h != hp) {
+      a.seg[j++] = make_double2(s1, s2);
+      s1 = 0.0;
+      s2 = 0.0;
+      hp = h;
+    }
+    const double f = a.F[e];
+    s1 += f;
+    s2 += f * f;
+  }
+  a.seg[j] = make_double2(s1, s2);
+}
+
 __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
-  __shared__ double s_red[kT / 32];
+  __shared__ double s_red[kT];
   __shared__ int s_last;
-  gv_wait_prior_grid();  // the fill's J g values and the reduce's I_k
+  gv_wait_prior_grid();  // the segments and the reduce's I_k
   const long long h = (long long)blockIdx.x * kT + threadIdx.x;
   double vn = 0.0, dd = 0.0;
   if (h < a.nh) {
     const long long o = a.off[h];
     const int m = a.n[h];
-    double s1 = 0.0, s2 = 0.0;
-    for (int j = 0; j < m; ++j) {
-      const double f = a.F[o + j];
-      s1 += f;
-      s2 += f * f;
+    // the hypercube's segments, range by range: in its first range it is the
+    // (h - hc[first event])-th segment; every later range starts inside it
+    const long long r0 = o / GV_PLUS_SEG, r1 = (o + m - 1) / GV_PLUS_SEG;
+    const long long b0 = r0 * GV_PLUS_SEG;
+    double2 sg = a.seg[b0 + (h - a.hc[b0])];
+    double s1 = sg.x, s2 = sg.y;
+    for (long long r = r0 + 1; r <= r1; ++r) {
+      sg = a.seg[r * GV_PLUS_SEG];
+      s1 += sg.x;
+      s2 += sg.y;
     }
     const double nd = (double)m;
     double inv_n, inv_m1;
@@ -251,6 +291,12 @@ __global__ void __launch_bounds__(kT) gv_plus_layout_kernel(const GvPlusArgs a) 
 }
 
 namespace gv {
+
+cudaError_t launch_plus_seg(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
+  const long long ranges = (a.cap + GV_PLUS_SEG - 1) / GV_PLUS_SEG;
+  const unsigned nb = (unsigned)((ranges + kT - 1) / kT);
+  return gv_launch(gv_plus_seg_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+}
 
 cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
   const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
