@@ -102,6 +102,10 @@ int maxd_class(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : 16); }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+constexpr int kHostRecMax = 64;  // iterations whose records fit the mapped result block
+constexpr size_t kHostRecOff = 256;  // byte offset of the records in it
+static_assert(sizeof(GvState) <= kHostRecOff, "state fits before the records");
+
 // Autotuner cache: best events-per-thread per (integrand, precision, mode,
 // d class, nbins, log2 tiles).  Results are identical for every choice.
 std::mutex g_tune_mu;
@@ -168,6 +172,12 @@ struct vegas_ctx {
   // pinned host staging for results
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  // mapped pinned memory the finalising thread writes a plain forward stage's
+  // results into (state, then up to kHostRecMax iteration records), so that
+  // fetching them is a synchronisation, not two copies
+  void* hres = nullptr;
+  void* hres_dev = nullptr;
+  bool last_zero_copy = false;
   // derived constants currently on the device
   int consts_ig = -1;
   double consts_params[GV_MAXPARAMS] = {0};
@@ -411,6 +421,13 @@ GvHistArgs hist_args(const vegas_ctx* c, const Plan& p, int k) {
   return h;
 }
 
+// A plain forward stage of at most kHostRecMax iterations hands its results
+// over through the mapped block (VEGAS+ finishes its iterations in another
+// kernel, and the adjoint has more channels).
+bool zero_copy(const vegas_ctx* c, const Plan& p) {
+  return c->hres_dev && p.mode == 0 && !p.plus && p.itmx <= kHostRecMax;
+}
+
 GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   GvReduceArgs r;
   r.ndim = c->ndim;
@@ -420,6 +437,10 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.has_bins = p.mode == 0;
   r.nhist = p.nhist;
   r.plus = p.plus;
+  if (zero_copy(c, p)) {
+    r.host_st = (GvState*)c->hres_dev;
+    r.host_rec = (double*)((char*)c->hres_dev + kHostRecOff);
+  }
   r.k = k;
   r.last = k == p.itmx - 1;
   r.refine_follows = (p.mode == 0 && c->adapt) ? 1 : 0;
@@ -707,6 +728,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   c->last_mode = mode;
   c->last_ept = p.ept;
   c->last_per_iter = p.per_iter;
+  c->last_zero_copy = zero_copy(c, p);
   c->pending_events.clear();
   const bool graph_ok = c->use_graph && c->stream != nullptr;
   if (!graph_ok) {
@@ -773,17 +795,36 @@ int fetch_stage(vegas_ctx* c, GvState* hs, std::vector<double>* per_iter) {
   if (!c->pending) return VEGAS_EINVAL;
   const int stride = c->last_mode ? 2 + 2 * GV_NGRAD : 2;
   const size_t nrec = (size_t)c->last_itmx * stride;
-  const size_t need = sizeof(GvState) + nrec * sizeof(double) + 64;
-  int st = ensure_pinned(c, need);
-  if (st) return st;
-  char* pin = (char*)c->pinned;
-  GV_TRY(cudaMemcpyAsync(pin, c->st, sizeof(GvState), cudaMemcpyDeviceToHost, c->stream));
-  double* pin_rec = (double*)(pin + ((sizeof(GvState) + 63) & ~(size_t)63));
-  GV_TRY(cudaMemcpyAsync(pin_rec, c->last_per_iter, nrec * sizeof(double), cudaMemcpyDeviceToHost,
-                         c->stream));
-  GV_TRY(cudaStreamSynchronize(c->stream));
-  memcpy(hs, pin, sizeof(GvState));
-  if (per_iter) per_iter->assign(pin_rec, pin_rec + nrec);
+  if (c->last_zero_copy) {
+    // the finalising thread wrote the state and the records into the mapped
+    // block; they are visible once the stream is done
+    GV_TRY(cudaStreamSynchronize(c->stream));
+    const volatile GvState* hv = (const volatile GvState*)c->hres;
+    memset(hs, 0, sizeof *hs);
+    hs->it = hv->it;
+    hs->nonfinite = hv->nonfinite;
+    hs->status = hv->status;
+    hs->integral = hv->integral;
+    hs->error = hv->error;
+    hs->chi2 = hv->chi2;
+    if (per_iter) {
+      const volatile double* rv = (const volatile double*)((char*)c->hres + kHostRecOff);
+      per_iter->resize(nrec);
+      for (size_t i = 0; i < nrec; ++i) (*per_iter)[i] = rv[i];
+    }
+  } else {
+    const size_t need = sizeof(GvState) + nrec * sizeof(double) + 64;
+    int st = ensure_pinned(c, need);
+    if (st) return st;
+    char* pin = (char*)c->pinned;
+    GV_TRY(cudaMemcpyAsync(pin, c->st, sizeof(GvState), cudaMemcpyDeviceToHost, c->stream));
+    double* pin_rec = (double*)(pin + ((sizeof(GvState) + 63) & ~(size_t)63));
+    GV_TRY(cudaMemcpyAsync(pin_rec, c->last_per_iter, nrec * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+    GV_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(hs, pin, sizeof(GvState));
+    if (per_iter) per_iter->assign(pin_rec, pin_rec + nrec);
+  }
   if (!c->pending_events.empty()) {
     for (size_t k = 0; k + 2 < c->pending_events.size(); k += 3) {
       float t[2] = {0.f, 0.f};
@@ -893,6 +934,19 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
     return VEGAS_ECUDA;
   }
   c->own_stream = true;
+  // the mapped result block (without it, results are copied)
+  if (cudaHostAlloc(&c->hres, kHostRecOff + kHostRecMax * 2 * sizeof(double),
+                    cudaHostAllocMapped) == cudaSuccess) {
+    if (cudaHostGetDevicePointer(&c->hres_dev, c->hres, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(c->hres);
+      c->hres = nullptr;
+      c->hres_dev = nullptr;
+    }
+  } else {
+    cudaGetLastError();
+    c->hres = nullptr;
+  }
   // slots: channel sums, bin sums, the largest histogram's sums
   c->nacc_max = std::max(2 * GV_MAXCH, 2 + ndim * nbins + 2 * (GV_HIST_MAX + 2));
   const size_t gd = grid_doubles(ndim, nbins);
@@ -958,6 +1012,7 @@ void vegas_free(vegas_ctx* c) {
   if (c->fixed) cudaFree(c->fixed);
   if (c->plus_mem) cudaFree(c->plus_mem);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->hres) cudaFreeHost(c->hres);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

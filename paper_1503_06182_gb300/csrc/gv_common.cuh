@@ -156,6 +156,10 @@ struct GvReduceArgs {
   int ndim, nbins, nch, nacc, has_bins, k, last, mode;  // k: iteration in the stage, last: k == itmx-1
   int nhist = 0;                 // histogram bins (0: none)
   int plus = 0;                  // VEGAS+: sigma_k and the stage combination come later
+  // results written straight to mapped host memory as well (plain forward
+  // stages): the iteration records, and the state after the last iteration
+  GvState* host_st = nullptr;
+  double* host_rec = nullptr;
   int refine_follows;            // 1: each axis is refined by the CTA that completes it
   long long ncall;
   double inv_c, inv_cm1, inv_m1; // 1/C, 1/(C-1), 1/(k) for chi2/dof at the last iteration

@@ -224,8 +224,15 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
     const int stride = a.mode ? 2 + 2 * GV_NGRAD : 2;
     if (lane < a.nch) {
       double* rec = a.per_iter + (size_t)a.k * stride + 2 * lane;
+      double I, s;
       mean_sigma(__ldcg(a.sums + 2 * lane), __ldcg(a.sums + 2 * lane + 1), a.inv_c, a.inv_cm1,
-                 &rec[0], &rec[1]);
+                 &I, &s);
+      rec[0] = I;
+      rec[1] = s;
+      if (a.host_rec) {
+        a.host_rec[(size_t)a.k * stride + 2 * lane] = I;
+        a.host_rec[(size_t)a.k * stride + 2 * lane + 1] = s;
+      }
     }
     __syncwarp();
     if (a.last && !a.plus) combine_stage_warp(a.per_iter, stride, a.k + 1, a.inv_m1, st, a.mode != 0);
@@ -236,7 +243,18 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
       st->nonfinite_iter = 0ull;
     }
   }
-  if (tid == 0) st->it = st->it + 1ull;
+  if (tid == 0) {
+    st->it = st->it + 1ull;
+    if (a.last && a.host_st) {
+      // the state the host reads after the stage: this thread wrote all of it
+      a.host_st->it = st->it;
+      a.host_st->nonfinite = st->nonfinite;
+      a.host_st->status = st->status;
+      a.host_st->integral = st->integral;
+      a.host_st->error = st->error;
+      a.host_st->chi2 = st->chi2;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

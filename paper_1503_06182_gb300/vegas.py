@@ -47,6 +47,22 @@ _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 _vp = C.c_void_p
 
 
+_RAW = None
+
+
+def _raw():
+    """A second handle on the library whose per-stage entry points take plain
+    pointers (the checked signatures of lib() cost microseconds per call)."""
+    global _RAW
+    if _RAW is None:
+        R = C.CDLL(lib()._name)
+        R.vegas_iterate.argtypes = [_vp, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        R.vegas_iterate.restype = C.c_int
+        _RAW = R
+    return _RAW
+
+
 def lib():
     """The loaded library (raises if it is not built)."""
     global _lib
@@ -158,15 +174,24 @@ def vegas_set_workspace(h, device_ptr: int | None, nbytes: int) -> None:
     _check(lib().vegas_set_workspace(h, device_ptr or None, nbytes), "vegas_set_workspace")
 
 
+def _params_fast(params) -> np.ndarray:
+    if (type(params) is np.ndarray and params.dtype == np.float64 and params.ndim == 1
+            and params.flags.c_contiguous):
+        return params
+    return _params(params)
+
+
 def vegas_iterate(h, ncall: int, itmx: int, integrand_id: int, params, allow_nonfinite=False):
-    """Returns (integral, error, chi2_dof, per_iter[itmx, 2], status)."""
-    p = _params(params)
-    I, e, c = C.c_double(), C.c_double(), C.c_double()
-    per = np.zeros((itmx, 2))
-    st = lib().vegas_iterate(h, ncall, itmx, integrand_id, p, len(p), C.byref(I), C.byref(e),
-                             C.byref(c), _ptr(per))
+    """Returns (integral, error, chi2_dof, per_iter[itmx, 2], status).  This is
+    the per-stage call, so it passes raw pointers (no per-call argument
+    checking by ctypes)."""
+    p = _params_fast(params)
+    out = (C.c_double * 3)()
+    per = np.empty((itmx, 2))
+    st = _raw().vegas_iterate(h, ncall, itmx, integrand_id, p.ctypes.data, p.shape[0], out,
+                              C.byref(out, 8), C.byref(out, 16), per.ctypes.data)
     _check(st, "vegas_iterate", (VEGAS_ENONFINITE,) if allow_nonfinite else ())
-    return I.value, e.value, c.value, per, st
+    return out[0], out[1], out[2], per, st
 
 
 def vegas_launch(h, ncall: int, itmx: int, integrand_id: int, params) -> None:
