@@ -1,13 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark: VEGAS events/s on one GB300 (LO Drell-Yan, 4 dims, 100 bins,
-1e6 calls per iteration, FP32 integrand with FP64/exact accumulation).
+10 iterations x 1e6 calls, FP32 integrand with FP64/exact accumulation).
 
-A step is one VEGAS iteration -- every step of the hot path: Philox uniforms,
-grid map, phase space and matrix element, the combination of all events and
-the grid refinement (Section 2.1) -- over 1e6 events.  Steps are timed with
-CUDA events on the library's launching stream (torch's current stream), the
-L2 cache is flushed between steps, and the whole timed region is bracketed by
-a barrier and a device synchronisation.  See ``--help`` for the options;
+A step is one stage of that workload, one vegas_iterate call: 10 VEGAS
+iterations, each every step of the hot path (Philox uniforms, grid map,
+phase space and matrix element, the combination of all events and the grid
+refinement; Section 2.1) over 1e6 events.  Steps are timed with CUDA events
+on the library's launching stream (torch's current stream), the L2 cache is
+flushed between steps, and the whole timed region is bracketed by a barrier
+and a device synchronisation.  The same measurement with one iteration per
+step is reported beside it (single_iteration).  See ``--help`` for the options;
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
@@ -25,8 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NCALL = 1_000_000
+ITMX = 10  # iterations per step: the workload's 10 x 1e6 calls
 NDIM, NBINS = 4, 100
-METRIC = "VEGAS events/s (LO Drell-Yan, d=4, 100 bins, 1e6 calls/iteration)"
+METRIC = "VEGAS events/s (LO Drell-Yan, d=4, 100 bins, 10 iterations x 1e6 calls)"
+WORKLOAD = "drell_yan_lo_14tev_d4_n100_10x1e6calls"
 UNIT = "events/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 floating-point operations per event of the FP32 Drell-Yan fill, counted
@@ -172,8 +176,9 @@ def run_gpu(args):
             g.set(v.VEGAS_OPT_EPT, args.ept)
         return g
 
-    def timed_steps(g, nsteps, flush_between=True):
-        """Device time (ms) of each of nsteps iterations, L2 flushed in between."""
+    def timed_steps(g, nsteps, itmx=ITMX, flush_between=True):
+        """Device time (ms) of each of nsteps stages of itmx iterations, L2
+        flushed in between."""
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(nsteps)]
         with torch.cuda.stream(stream):
@@ -181,16 +186,17 @@ def run_gpu(args):
                 if flush_between:
                     flush.fill_(1)
                 a.record(stream)
-                g.launch(NCALL, 1, DY, DY_PARAMS)
+                g.launch(NCALL, itmx, DY, DY_PARAMS)
                 b.record(stream)
         stream.synchronize()
-        res = g.fetch(1)
+        res = g.fetch(itmx)
         return [a.elapsed_time(b) for a, b in evs], res
 
     sampler = ClockSampler(torch.cuda.current_device()).start() if rank == 0 else None
     g32 = make("fp32")
-    # warm-up (also autotunes events per thread and captures the graph)
+    # warm-up (also autotunes events per thread and captures the graphs)
     for _ in range(W):
+        g32.iterate(NCALL, ITMX, DY, DY_PARAMS)
         g32.iterate(NCALL, 1, DY, DY_PARAMS)
     barrier()
     t_wall0 = time.time()
@@ -198,7 +204,7 @@ def run_gpu(args):
     barrier()
     t_wall1 = time.time()
     tot_ms = max_over_ranks(sum(step_ms), dev)
-    value = world * K * NCALL / (tot_ms * 1e-3)
+    value = world * K * ITMX * NCALL / (tot_ms * 1e-3)
 
     # end to end through the blocking C ABI: host params in, host results out
     e2e_ms = []
@@ -208,10 +214,13 @@ def run_gpu(args):
             flush.fill_(1)
         stream.synchronize()
         t0 = time.perf_counter()
-        g32.iterate(NCALL, 1, DY, p)
+        g32.iterate(NCALL, ITMX, DY, p)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_tot = max_over_ranks(sum(e2e_ms), dev)
-    e2e_value = world * K * NCALL / (e2e_tot * 1e-3)
+    e2e_value = world * K * ITMX * NCALL / (e2e_tot * 1e-3)
+    # the same with one iteration per step (each iteration a stage of its own)
+    one_ms, _ = timed_steps(g32, K, itmx=1)
+    one_tot = max_over_ranks(sum(one_ms), dev)
     t_wall2 = time.time()
 
     # roofline of the dominant kernel (fill): library-side CUDA events on the
@@ -220,10 +229,10 @@ def run_gpu(args):
     kernels = (v.VEGAS_KERNEL_FILL, v.VEGAS_KERNEL_REDUCE)  # the refinement is in the reduce
     for kid in kernels:
         v.vegas_kernel_time(g32.h, kid, reset=True)
-    for _ in range(max(K, 5)):
+    for _ in range(max(K // ITMX, 5)):
         with torch.cuda.stream(stream):
             flush.fill_(1)
-        g32.iterate(NCALL, 1, DY, DY_PARAMS)
+        g32.iterate(NCALL, ITMX, DY, DY_PARAMS)
     kavg = []
     for kid in kernels:
         ms, n = v.vegas_kernel_time(g32.h, kid)
@@ -237,10 +246,10 @@ def run_gpu(args):
     # form from the same grid and seed (the same events)
     g64 = make("fp64")
     for _ in range(max(2, W // 2)):
-        g64.iterate(NCALL, 1, DY, DY_PARAMS)
-    k64 = max(3, min(K, 20))
+        g64.iterate(NCALL, ITMX, DY, DY_PARAMS)
+    k64 = max(3, min(K, 10))
     ms64, _ = timed_steps(g64, k64)
-    value64 = world * NCALL / (sum(ms64) / k64 * 1e-3)
+    value64 = world * ITMX * NCALL / (sum(ms64) / k64 * 1e-3)
     sig = {}
     for prec in ("fp32", "fp64"):
         g = v.Vegas(NDIM, NBINS, 4321, precision=prec)
@@ -271,15 +280,22 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": tot_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
-        "config": {"workload": "drell_yan_lo_14tev_d4_n100_1e6calls", "integrand": "drell_yan",
-                   "ndim": NDIM, "nbins": NBINS, "ncall_per_step": NCALL, "itmx_per_step": 1,
+        "config": {"workload": WORKLOAD, "integrand": "drell_yan",
+                   "ndim": NDIM, "nbins": NBINS, "ncall_per_iteration": NCALL,
+                   "itmx_per_step": ITMX,
+                   "step": "one vegas_iterate stage of 10 iterations x 1e6 calls",
                    "precision": "fp32 integrand, fp64 Jacobian, exact integer sums",
                    "seed": 1234, "events_per_thread": ept,
                    "l2": "flushed between steps (256 MiB device write)",
                    "parallelism": "replicas" if world > 1 else "single"},
+        # per step: the 10 parameters in; the state (44 B) and 10 iteration
+        # records (160 B) written by the device into mapped host memory
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 128,
-                "d2h_bytes_per_step": 176},
-        "gpu_launches": 2 * K,
+                "d2h_bytes_per_step": 44 + 16 * ITMX},
+        "gpu_launches": 2 * ITMX * K,
+        "single_iteration": {"value": world * K * NCALL / (one_tot * 1e-3), "unit": UNIT,
+                             "ms_per_iteration": one_tot / K,
+                             "note": "one iteration per step (a stage of its own), L2 flushed"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": _fill_traffic(),
                      "kernel": "gv_fill_kernel<drell_yan, float>",
@@ -441,8 +457,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp64",
         "data": "synthetic",
-        "config": {"workload": "drell_yan_lo_14tev_d4_n100_1e6calls", "integrand": "drell_yan",
-                   "ndim": NDIM, "nbins": NBINS, "ncall_per_step": NCALL, "itmx_per_step": 1,
+        "config": {"workload": WORKLOAD, "integrand": "drell_yan",
+                   "ndim": NDIM, "nbins": NBINS, "ncall_per_iteration": NCALL,
+                   "itmx_per_step": 1,
+                   "step": "a bounded sample of the stage: one whole 1e6-event iteration",
                    "precision": "fp64 oracle (C + OpenMP), compensated sums"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} whole 1e6-event iterations"},
