@@ -162,3 +162,22 @@ def test_hist_set_validation_and_off():
         g.iterate(5000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS)  # runs without a histogram
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("hist", [(1, 0.0, 1.0), (v.VEGAS_HIST_MAX_BINS, 0.0, 1.0),
+                                  (10, 2.0, 3.0), (10, -3.0, -2.0)])
+def test_hist_edge_binnings_match_oracle(hist):
+    """One bin, the most bins, and ranges no event reaches (everything in the
+    underflow, or in the overflow): the FP64 form against the oracle."""
+    iid, params, ndim, nbins, _ = CASES["gauss"]
+    gpu = gpu_stage(iid, params, ndim, nbins, hist, 20 * 1024 + 37, 2)
+    ref = oracle.iterate(ndim, nbins, 1234, 20 * 1024 + 37, 2, iid, params, edges=gpu["edges"],
+                         iteration=2, adapt=False, want_sums=True, hist=hist)
+    close_with_zeros(gpu["last"][0], ref.hist_last[0], 1e-12)
+    close_with_zeros(gpu["last"][1], ref.hist_last[1], 1e-12)
+    close_with_zeros(gpu["value"], ref.hist_value, 1e-12)
+    close_with_zeros(gpu["err"], ref.hist_error, 1e-11)
+    if hist[1] >= 1.0:  # x_0 < 1 <= lo: everything is underflow
+        assert np.count_nonzero(gpu["value"]) == 1 and gpu["value"][0] != 0
+    if hist[2] <= 0.0:  # hi <= 0 < x_0: everything is overflow
+        assert np.count_nonzero(gpu["value"]) == 1 and gpu["value"][-1] != 0

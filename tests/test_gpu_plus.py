@@ -196,3 +196,46 @@ def test_plus_fp32_form_against_oracle(name):
                               iteration=2)
     assert rel(per[:, 0], ref.per_iter[:, 0]) < 2e-5
     assert rel(per[:, 1], ref.per_iter[:, 1]) < 2e-4
+
+
+@pytest.mark.parametrize("ndim,ncall", [(1, 2 ** 20), (16, 300_000), (1, 8), (3, 10)])
+def test_plus_extreme_shapes_match_oracle(ndim, ncall):
+    """One axis with a quarter of a million strata, sixteen axes, and the
+    smallest call counts: a stage from the uniform start, then one iteration
+    from the GPU's state, against the oracle."""
+    iid, params = v.VEGAS_GAUSS, GAUSS_PARAMS
+    nbins = 20
+    g = gpu_state(iid, params, ndim, nbins, ncall, 2)
+    try:
+        edges = g.grid
+        s, alloc, _ = g.strat()
+        I, e, c, per, _ = g.iterate(ncall, 1, iid, params)
+        s2, alloc2, var = g.strat()
+    finally:
+        g.close()
+    ref = oracle.iterate_plus(ndim, nbins, 1234, ncall, 1, iid, params, edges=edges, alloc=alloc,
+                              iteration=2)
+    assert s == ref.nstrat and len(alloc) == s ** ndim
+    assert rel(per, ref.per_iter) < 1e-12
+    var_agrees(var, ref, alloc)
+    assert np.array_equal(alloc2, oracle.plus_allocate(ncall, var))
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.25, 0.5, 1.0])
+def test_plus_damping_values_match_oracle(beta):
+    iid, params, ndim, nbins = CASES["dy"]
+    g = gpu_state(iid, params, ndim, nbins, 20_000, 2, beta=beta)
+    try:
+        edges = g.grid
+        s, alloc, _ = g.strat()
+        I, e, c, per, _ = g.iterate(20_000, 1, iid, params)
+        s2, alloc2, var = g.strat()
+    finally:
+        g.close()
+    ref = oracle.iterate_plus(ndim, nbins, 1234, 20_000, 1, iid, params, edges=edges, alloc=alloc,
+                              iteration=2, beta=beta)
+    assert rel(per, ref.per_iter) < 1e-12
+    var_agrees(var, ref, alloc)
+    assert np.array_equal(alloc2, oracle.plus_allocate(20_000, var, beta=beta))
+    if beta == 0.0:  # every hypercube weighs the same: the allocation stays uniform
+        assert np.all(alloc2 == 20_000 // len(alloc2))
