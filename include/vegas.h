@@ -263,7 +263,10 @@ int vegas_hist_get(vegas_ctx* ctx, double* value, double* error, double* last_su
  * allocation for the next iteration (counts, nh int32, nullable) and the last
  * iteration's v_h (var, nh doubles, nullable).  EINVAL before any.
  * vegas_strat_set: the allocation for stages of ncall events (counts: nh
- * values >= 2 summing to at most ncall + 2 nh; EINVAL otherwise). */
+ * values >= 2 summing to at most ncall + 2 nh; EINVAL otherwise).
+ * The allocation is not part of a checkpoint: after vegas_state_set the next
+ * VEGAS+ stage starts from the uniform allocation, unless one saved with
+ * vegas_strat_get is restored with vegas_strat_set. */
 int vegas_strat_get(vegas_ctx* ctx, int* nstrat, int64_t* ncubes, int32_t* counts, double* var);
 int vegas_strat_set(vegas_ctx* ctx, int64_t ncall, const int32_t* counts);
 

@@ -1307,6 +1307,7 @@ int vegas_state_set(vegas_ctx* c, const void* buf, size_t bytes) {
   hs.it = h.it;
   GV_TRY(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));
   clear_graphs(c);
+  c->plus_valid = false;  // a VEGAS+ allocation is not part of a checkpoint
   return upload_grid(c, e.data());
 }
 

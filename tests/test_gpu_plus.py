@@ -239,3 +239,27 @@ def test_plus_damping_values_match_oracle(beta):
     assert np.array_equal(alloc2, oracle.plus_allocate(20_000, var, beta=beta))
     if beta == 0.0:  # every hypercube weighs the same: the allocation stays uniform
         assert np.all(alloc2 == 20_000 // len(alloc2))
+
+
+def test_plus_checkpoint_with_saved_allocation_continues_bit_exactly():
+    """A checkpoint plus the allocation saved beside it (vegas_strat_get /
+    vegas_strat_set) continue a VEGAS+ run bit for bit in a new context."""
+    iid, params, ndim, nbins = CASES["dy"]
+    a = gpu_state(iid, params, ndim, nbins, 20_000, 2)
+    try:
+        blob = a.state()
+        s, alloc, _ = a.strat()
+        ref = a.iterate(20_000, 2, iid, params)
+        ref_grid = a.grid
+    finally:
+        a.close()
+    b = v.Vegas(ndim, nbins, 99)
+    try:
+        b.restore(blob)
+        b.set(v.VEGAS_OPT_STRAT, 1)
+        b.strat_set(20_000, alloc)
+        got = b.iterate(20_000, 2, iid, params)
+        assert np.array_equal(got[3], ref[3]) and got[:3] == ref[:3]
+        assert np.array_equal(b.grid, ref_grid)
+    finally:
+        b.close()
