@@ -43,10 +43,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 72_448
+FILL_TRAFFIC_BYTES = 72_192
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "93473324374847623a1538fcbbe157bc26b723c57e64e4917677dca854ef4a30"
+FILL_SOURCES_SHA256 = "ee53db081c6399261e1c8d1a6449fc67957e4724e46a04d23c9cdd9b72e6aa7d"
 
 
 def _fill_traffic():
