@@ -5,6 +5,8 @@
 // workspace (tile partials, per-iteration records).  A stage of itmx
 // iterations (Section 2.1; the two-stage runs of Section 3.2) is enqueued as
 //   itmx x [fill -> reduce (with the per-axis grid refinement)]
+// (with a histogram, its kernel after each reduce; with VEGAS+, the
+// segment, statistics, allocation and layout kernels after each reduce),
 // and, by default, captured once into a CUDA graph that is replayed by later
 // calls with the same shape; the iteration counter, the derived integrand
 // constants and the grid are read from device memory, so a replay needs no

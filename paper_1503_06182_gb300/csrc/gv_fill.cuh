@@ -10,10 +10,15 @@
 //   tile scale: block max of |w| (order-free) -> E_t;
 //   pass 2: w and the exact square w^2 rounded once to fixed point at the tile
 //           scale; sums in 128-bit integer registers (warp shuffle + block
-//           reduction); per-bin sums of w^2 at 88 bits below the tile's max^2
-//           as four 22-bit limbs in 32-bit shared-memory atomics (32-bit
-//           shared atomics run several times faster than 64-bit ones here,
-//           and 10 bits of headroom cover the 1024 events of a tile).
+//           reduction); per-bin sums of w^2, each bin with its own exponent F
+//           (an order-free shared atomicMax in pass 1), w^2 rounded once to
+//           2^(2F - 56) and added as three 22-bit limbs with 32-bit shared
+//           atomics (32-bit shared atomics run several times faster than
+//           64-bit ones here, and 10 bits of headroom cover the 1024 events of
+//           a tile).
+// With VEGAS+ (PLUS), each event first finds its hypercube and takes
+// stratified words; the estimate's weight is F C/(nh n_h) and the bins'
+// quantity F sqrt(1/(nh n_h)), F = J g, which is also stored per event.
 // With a histogram of the observable (HIST), every event with w != 0 also
 // adds w and w^2 to its observable's bin, in the same limb scheme: a per-bin
 // exponent from pass 1, then w^2 as three unsigned 22-bit limbs and w as two

@@ -2,16 +2,16 @@
 // optimisation (Section 2.1: the grid optimisation is serial so that it can
 // use the results of all events).
 //
-// gv_reduce_kernel sums the 128-bit tile partials exactly.  Its grid is
-// (accumulator blocks of 32) x (tile ranges): each CTA owns 32 accumulators
-// and a range of tiles, its 8 warps stride over the tiles, the warps' sums
-// are combined in shared memory, and the CTA adds the result to the
-// iteration's accumulators with one fire-and-forget integer atomic per limb
-// (a handful of CTAs per cache line, so no line becomes a hot spot).  Every
-// tile partial is first aligned to its slot's scale (channel sums: the max
-// over tiles; bin sums: the bin's own exponent -- both formed by the fill
-// kernel with order-free atomicMax).  Integer addition is associative: the
-// totals do not depend on the grid or on timing.
+// gv_reduce_kernel sums the tile partials exactly.  Its grid is (slot blocks
+// of 32) x (tile ranges): each CTA owns 32 slots and a range of tiles; its 8
+// warps stride over the tiles, align every partial to the largest exponent
+// the slot has in the range (channel sums: the tiles' scales; bin sums: the
+// bins' own exponents, formed by the fill kernel with order-free atomicMax)
+// and add in 192-bit integers; the warps' sums are combined in shared memory
+// and published with that exponent.  No sum is formed with atomics.  Integer
+// addition is associative, and the alignment depends only on the data and on
+// the reduce grid, a function of the tile count alone: the totals do not
+// depend on the fill's launch shape or on timing.
 //
 // Tickets instead of waiting: each CTA publishes its sums and counts itself
 // on its block of 32 slots; the CTA that completes a block combines the
@@ -24,10 +24,10 @@
 // sums) records I_k and sigma_k and combines the stage.  No CTA ever waits
 // for another.
 //
-// On this chip an FP64 instruction occupies a warp's FP64 pipe for ~64 cycles
-// and the FP64 library log takes ~2000 cycles: the serial code here keeps its
-// FP64 chains short (reciprocals passed in, a table-driven log, one thread
-// per bin).
+// On this chip a dependent FP64 operation waits ~56-64 cycles, a warp-wide
+// FP64 instruction occupies the SM's FP64 pipe for ~19 cycles, and the FP64
+// library log takes ~2000 cycles: the serial code here keeps its FP64 chains
+// short (reciprocals passed in, a table-driven log, one thread per bin).
 #include <algorithm>
 
 #include "gv_combine.cuh"
