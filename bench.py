@@ -46,7 +46,7 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FILL_TRAFFIC_BYTES = 72_192
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "ee53db081c6399261e1c8d1a6449fc67957e4724e46a04d23c9cdd9b72e6aa7d"
+FILL_SOURCES_SHA256 = "2e3cdaa01aa71307ab56bab354aba2ca89a7916c1f935aade74c1d5300896177"
 
 
 def _fill_traffic():
