@@ -28,36 +28,44 @@ constexpr int kT = 256;  // threads per CTA, one hypercube each
 // v^(j/8) (beta = j/4) from correctly rounded operations only: v = t 2^(8q)
 // with t in [1/2, 128) rounded to FP32, three FP32 square roots, j - 1 FP32
 // products, and 2^(q j) exactly.
-// The exponent split and the final scaling are exact edits of the exponent
-// field (frexp and ldexp, written as integer operations: their library forms
-// spend FP64 instructions, which this chip has few of); a subnormal v takes
-// the library path.
+// The exponent split, the FP32 rounding of t, the widening of the FP32
+// result and the final scaling are exact bit operations here (frexp, a
+// conversion to nearest, a widening and ldexp, written with integers: their
+// library and hardware forms run on the FP64 pipe, which this chip has little
+// of); a subnormal v takes the library path.
 __device__ __forceinline__ double plus_weight(double v, int j) {
-  if (j == 0) return 1.0;
-  if (!(v > 0.0)) return 0.0;
   const long long bits = __double_as_longlong(v);
-  const int eb = (int)(bits >> 52);  // biased exponent (v > 0)
-  int e;
-  double m2r;  // m 2^r, m in [1/2, 1)
-  int q, r;
+  if (j == 0) return 1.0;
+  if (bits <= 0) return 0.0;  // +0 (v is finite and not negative)
+  const int eb = (int)(bits >> 52);  // biased exponent
+  int e, q, r;
+  unsigned tb;  // FP32 bits of t = m 2^r in [1/2, 128), m in [1/2, 1)
   if (eb == 0) {
     const double m = frexp(v, &e);
     q = e >= 0 ? e / 8 : -((-e + 7) / 8);
     r = e - 8 * q;
-    m2r = ldexp(m, r);
+    tb = __float_as_uint(__double2float_rn(ldexp(m, r)));
   } else {
     e = eb - 1022;  // v = m 2^e
     q = e >= 0 ? e / 8 : -((-e + 7) / 8);
     r = e - 8 * q;
-    m2r = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | ((long long)(1022 + r) << 52));
+    // round the 52-bit mantissa to 23 bits, to nearest, ties to even (a carry
+    // runs into the exponent, as it should)
+    const unsigned long long M = (unsigned long long)bits & 0x000FFFFFFFFFFFFFull;
+    tb = ((unsigned)(126 + r) << 23) | (unsigned)(M >> 29);
+    const unsigned half = (unsigned)(M >> 28) & 1u;
+    const unsigned sticky = (M & ((1ull << 28) - 1ull)) != 0ull ? 1u : 0u;
+    tb += half & (sticky | (tb & 1u));
   }
-  const float t = __double2float_rn(m2r);
+  const float t = __uint_as_float(tb);
   const float y = __fsqrt_rn(__fsqrt_rn(__fsqrt_rn(t)));
   float p = y;
   for (int k = 1; k < j; ++k) p = __fmul_rn(p, y);
-  // (double)p 2^(q j): p is normal and so is the product (|q j| <= 520)
-  const long long pb = __double_as_longlong((double)p);
-  return __longlong_as_double(pb + ((long long)(q * j) << 52));
+  // (double)p 2^(q j): p is normal and so is the product (|q j| <= 540)
+  const unsigned pb = __float_as_uint(p);
+  const long long db = ((long long)(((pb >> 23) & 0xFFu) - 127 + 1023) << 52) |
+                       ((long long)(pb & 0x7FFFFFu) << 29);
+  return __longlong_as_double(db + ((long long)(q * j) << 52));
 }
 
 // Sum over the CTA in a fixed order, with few FP64 instructions (this chip's
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
       plus_recips(nd, &inv_n, &inv_m1);
     }
     double v = (s2 - s1 * s1 * inv_n) * inv_m1;
-    v = v > 0.0 ? v : 0.0;
+    v = __double_as_longlong(v) > 0ll ? v : 0.0;  // negative (rounding) or -0 -> 0
     a.var[h] = v;
     vn = v * inv_n;
     dd = plus_weight(v, a.beta_j);
