@@ -68,7 +68,8 @@ extern "C" {
 
 /* ---- options (vegas_set_option / vegas_batch_set_option) ---- */
 #define VEGAS_OPT_ALPHA 0     /* grid damping exponent alpha >= 0 (default 1.5) */
-#define VEGAS_OPT_PRECISION 1 /* 0 = FP64 integrand (default), 1 = FP32 integrand, FP64 sums */
+#define VEGAS_OPT_PRECISION 1 /* 0 = FP64 integrand (default), 1 = FP32 integrand; the sums are
+                                 exact integer sums in both forms */
 #define VEGAS_OPT_ADAPT 2     /* 1 = refine the grid after every iteration (default), 0 = frozen */
 #define VEGAS_OPT_EPT 3       /* events per thread of the fill kernel: 0 = autotuned, or 1, 2, 4, 8
                                  (8 only for ndim <= 8: VEGAS_EINVAL above) */
@@ -128,7 +129,7 @@ int vegas_set_workspace(vegas_ctx* ctx, void* device_ptr, size_t bytes);
  *   integral = sum(I_k/sigma_k^2)/sum(1/sigma_k^2), error = sum(1/sigma_k^2)^(-1/2),
  *   chi2_dof = sum((I_k - integral)^2/sigma_k^2)/(itmx - 1)  (0 when itmx = 1);
  * iterations with sigma_k = 0, if any, are averaged alone with error 0.
- * integrand_id / params: VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J as described above.
+ * integrand_id / params: VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J, VEGAS_DY_NLO as above.
  * per_iter (nullable): itmx x (I_k, sigma_k).  Blocking.
  * Errors: EINVAL (ncall < 2, itmx < 1, unknown id, wrong nparams or a
  * parameter outside its range), ENOMEM, ECUDA, ENONFINITE (results valid,
