@@ -43,10 +43,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 72_192
+FILL_TRAFFIC_BYTES = 71_936
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "2e3cdaa01aa71307ab56bab354aba2ca89a7916c1f935aade74c1d5300896177"
+FILL_SOURCES_SHA256 = "153f50bfc51746e5cfca65643c0bc3c14badd8124e279a20788cf7af608d4b38"
 
 
 def _fill_traffic():
