@@ -46,7 +46,7 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FILL_TRAFFIC_BYTES = 71_936
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "153f50bfc51746e5cfca65643c0bc3c14badd8124e279a20788cf7af608d4b38"
+FILL_SOURCES_SHA256 = "ce2206db1d5429ca38bdfbd4baef27de794c41efbf4b35800c4eed093b036333"
 
 
 def _fill_traffic():
@@ -382,7 +382,8 @@ def forms(v, stream, seed):
     try:
         g.iterate(NCALL, 5, DY, DY_PARAMS)
         g.set(v.VEGAS_OPT_ADAPT, 0)
-        g.adjoint(10_000_000, 1, DY_PARAMS)  # tunes and sizes the workspace
+        # warm-up stage of the timed size: events per thread are tuned per size
+        g.adjoint(100_000_000, 10, DY_PARAMS)
         ms, (grad, gerr, _, _, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
     finally:
         g.close()

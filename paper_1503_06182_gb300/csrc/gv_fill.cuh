@@ -637,96 +637,6 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (PLUS && MAXD <= 8 && sizeof(Re
   gv_fill_tile<IG, Real, EPT, MAXD, HIST, PLUS>(a, blockIdx.x, smem, red_u64, red_128, it);
 }
 
-// ---------------------------------------------------------------------------
-// Adjoint fill (Drell-Yan): channels w, dw/dM_Z, dw/dGamma_Z, dw/dsw2, dw/da,
-// dw/db; no bin sums.  Each channel has its own tile scale.
-// ---------------------------------------------------------------------------
-template <typename Real, int EPT, int MAXD>
-__global__ void __launch_bounds__(GV_TILE / EPT)
-    gv_fill_adjoint_kernel(const GvFillArgs a) {
-  constexpr int B = GV_TILE / EPT;
-  constexpr int NW = B / 32;
-  constexpr int NCH = GV_MAXCH;
-  using Pair = typename GvPair<Real>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red_u64[NW];
-  __shared__ u128 red_128[NW];
-  const int d = a.ndim, N = a.nbins;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), false, false);
-  double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
-  Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
-  const int tid = threadIdx.x;
-  gv_wait_prior_grid();
-  gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
-  GvConst<Real, DK_NK> K;
-  K.load(a.kconst);
-  const uint32_t it = (uint32_t)a.st->it;
-  __syncthreads();
-
-  const long long tile = blockIdx.x;
-  const long long tile0 = tile * GV_TILE;
-  double v[EPT][NCH];
-  unsigned long long mx[NCH];
-#pragma unroll
-  for (int c = 0; c < NCH; ++c) mx[c] = 0ull;
-  unsigned long long nbad = 0ull;
-#pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const long long ev = tile0 + k * B + tid;
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) v[k][c] = 0.0;
-    if (ev < a.ncall) {
-      uint32_t r[MAXD];
-      gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
-      Real x[MAXD];
-      int bin[MAXD];
-      const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
-      Real gr[GV_NGRAD];
-      const Real g = gv_drell_yan<Real, true>(x, K, gr);
-      double vals[NCH];
-      vals[0] = gv_weight(J, g);
-#pragma unroll
-      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = gv_weight(J, gr[p]);
-      bool finite = true;
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) finite &= gv_finite_bits(gv_abs_bits(vals[c]));
-      if (!finite) ++nbad;
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        v[k][c] = finite ? vals[c] : 0.0;
-        const unsigned long long bits = gv_abs_bits(v[k][c]);
-        mx[c] = bits > mx[c] ? bits : mx[c];
-      }
-    }
-  }
-  ulonglong2* out = a.part + (size_t)tile * a.nacc;
-  gv_allow_next_grid();
-#pragma unroll
-  for (int c = 0; c < NCH; ++c) {
-    const unsigned long long M = gv_block_max<NW>(mx[c], red_u64);
-    const int E = gv_scale_exp(M);
-    u128 s1 = {0ull, 0ull}, s2 = {0ull, 0ull};
-    if (E != GV_EMPTY) {
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        if (gv_abs_bits(v[k][c]) != 0ull) {
-          const GvDecoded dv = gv_decode(v[k][c]);
-          s1 = add128(s1, gv_fixed_tile(dv, E));
-          s2 = add128(s2, gv_square_tile(dv, gv_square_hi(dv.m), E));
-        }
-      }
-    }
-    const u128 t1 = gv_block_sum128<NW>(s1, red_128);
-    const u128 t2 = gv_block_sum128<NW>(s2, red_128);
-    if (tid == 0) {
-      out[2 * c] = make_ulonglong2(t1.lo, t1.hi);
-      out[2 * c + 1] = make_ulonglong2(t2.lo, t2.hi);
-      a.tileE[tile * NCH + c] = E;
-    }
-  }
-  if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
-}
-
 // Single-event diagnostics (no shared memory): weight and bins of the given
 // events at iteration `it`, with the same map and integrand code as the fill.
 template <int IG, typename Real>
