@@ -7,9 +7,14 @@
 // fixed-point sums (values and squares) to the tile's partial, as the forward
 // fill does for its one channel.
 //
-// The six values of each event are staged in shared memory (48 KB a tile),
-// not held in registers across the tile's maximum, so that two 512-thread or
-// three 256-thread CTAs share an SM.  All six channels share the block-wide
+// The six values of each event are staged in shared memory (FP32 form: the
+// FP32 products J.m g and the exponent J.e, 28 KB a tile; FP64 form: the
+// weights, 48 KB), not held in registers across the tile's maximum, so that
+// two 512-thread or three 256-thread CTAs share an SM.  In the FP32 form a
+// weight is a 24-bit significand times a power of two, and its fixed-point
+// terms are formed from that significand (one 32 x 32 -> 64 bit square):
+// the same exactly rounded integers as through the double, with less
+// integer work.  All six channels share the block-wide
 // steps: one barrier after the per-warp maxima, one after the tile scales,
 // one after the per-warp sums.  Each warp's twelve 128-bit sums leave the warp
 // by a reduce-scatter (every shuffle step halves the values a lane carries),
@@ -37,9 +42,79 @@ __device__ __forceinline__ void rs_step(const u128 (&x)[2 * N], u128 (&y)[N], in
   }
 }
 
-// Bytes of the per-event values staged in shared memory after the grid:
-// all six channels of the tile's GV_TILE events, as doubles.
-constexpr size_t kStageBytes = (size_t)GV_TILE * kNch * sizeof(double);
+// Bytes of the per-event values staged in shared memory after the grid, for
+// the tile's GV_TILE events: FP64 form, the six weights; FP32 form, the six
+// FP32 products J.m g and the event's Jacobian exponent J.e.
+template <typename Real>
+constexpr size_t stage_bytes() {
+  return sizeof(Real) == 8 ? (size_t)GV_TILE * kNch * 8 : (size_t)GV_TILE * (kNch + 1) * 4;
+}
+
+// FP32 form: the weight J g = p 2^e of an FP32 product p = J.m g, as the
+// forward fill forms it.  Where p is normal and p 2^e is a normal double
+// ("direct"), the weight is m 2^e2 with m the 24-bit significand of p and
+// e2 = nf - 1046, nf its FP64 exponent field; every other case forms the
+// double itself.
+struct AdjWeight {
+  bool direct;
+  unsigned m;
+  int e2;
+  bool neg;
+};
+__device__ __forceinline__ AdjWeight adj_classify(unsigned u, int e) {
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const int nf = ef + 896 + e;
+  AdjWeight w;
+  w.direct = ef != 0 && ef != 0xFF && nf > 0 && nf < 0x7FF;
+  w.m = (u & 0x7FFFFFu) | 0x800000u;
+  w.e2 = nf - 1046;
+  w.neg = (u >> 31) != 0u;
+  return w;
+}
+__device__ __forceinline__ double adj_weight_double(unsigned u, int e) {
+  return gv_ldexp_bits(gv_widen(__uint_as_float(u)), e);
+}
+
+// round(m 2^s), half up, for m < 2^24 and s <= 72, with the sign: the
+// tile's fixed-point value of a direct weight (|w| < 2^E, s = e2 - E + GV_FB).
+// The same exact rounding as gv_fixed_tile applies to the equal double.
+__device__ __forceinline__ u128 adj_fixed24(unsigned long long m, int s, bool neg) {
+  u128 v;
+  if (s >= 0) {
+    v.lo = s < 64 ? m << s : 0ull;
+    v.hi = s > 40 ? (s < 64 ? m >> (64 - s) : m << (s - 64)) : 0ull;
+  } else {
+    const int r = -s;
+    v.lo = r < 64 ? ((m >> (r - 1)) + 1ull) >> 1 : 0ull;
+    v.hi = 0ull;
+  }
+  return gv_negate_if(v, neg);
+}
+
+// round(m^2 2^t), half up, for m < 2^24 and t <= 48: the tile's fixed-point
+// square of a direct weight (t = 2 e2 - 2E + GV_FB), from one 32 x 32 -> 64
+// bit product.
+__device__ __forceinline__ u128 adj_square24(unsigned m, int t) {
+  const unsigned long long M = (unsigned long long)m * m;
+  u128 v;
+  if (t >= 0) {
+    v.lo = M << t;
+    v.hi = t > 16 ? M >> (64 - t) : 0ull;
+  } else {
+    const int r = -t;
+    v.lo = r < 64 ? ((M >> (r - 1)) + 1ull) >> 1 : 0ull;
+    v.hi = 0ull;
+  }
+  return v;
+}
+
+// A weight's two fixed-point terms through the general FP64 route.
+__device__ __forceinline__ void adj_add_double(double x, int E, u128& s1, u128& s2) {
+  if (gv_abs_bits(x) == 0ull) return;
+  const GvDecoded dv = gv_decode(x);
+  s1 = add128(s1, gv_fixed_tile(dv, E));
+  s2 = add128(s2, gv_square_tile(dv, gv_square_hi(dv.m), E));
+}
 
 // Register budget of the FP32 kernels: 64 registers at 1024 or 512 threads
 // (one or two CTAs per SM), 80 at 256 (three CTAs; the staging buffer allows
@@ -56,17 +131,21 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
     gv_fill_adjoint_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
+  constexpr bool F32 = sizeof(Real) == 4;
   using Pair = typename GvPair<Real>::T;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long red_max[NW][kNch];
+  __shared__ int red_max[NW][kNch];
   __shared__ u128 red_sum[NW][kNsum];
   __shared__ int s_E[kNch];
   const int d = a.ndim, N = a.nbins;
   const GvFillSmem lay(d, N, (int)sizeof(Real), false, false);
   double* s_jac = reinterpret_cast<double*>(smem + lay.jac);
   Pair* s_ew = reinterpret_cast<Pair*>(smem + lay.ew);
-  // value of channel c of the thread's k-th event at s_v[(k kNch + c) B + tid]
+  // channel c of the thread's k-th event at [(k kNch + c) B + tid]: FP64
+  // form, the weight; FP32 form, the bits of J.m g, and J.e at s_je[k B + tid]
   double* s_v = reinterpret_cast<double*>(smem + lay.total);
+  unsigned* s_p = reinterpret_cast<unsigned*>(smem + lay.total);
+  int* s_je = reinterpret_cast<int*>(smem + lay.total + (size_t)GV_TILE * kNch * 4);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   gv_wait_prior_grid();
   gv_stage_grid<Real>(a.grid, d, N, s_jac, s_ew, tid, B);
@@ -77,16 +156,26 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
 
   const long long tile = blockIdx.x;
   const long long tile0 = tile * GV_TILE;
-  unsigned long long mx[kNch];
+  // per channel the largest scale gv_scale_exp(|w|) of the thread's weights
+  // (the scale of the largest |w|: the scale is monotonic in |w|)
+  int mE[kNch];
 #pragma unroll
-  for (int c = 0; c < kNch; ++c) mx[c] = 0ull;
+  for (int c = 0; c < kNch; ++c) mE[c] = GV_EMPTY;
   unsigned long long nbad = 0ull;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const long long ev = tile0 + k * B + tid;
-    double vals[kNch];
+    int Ev[kNch];
 #pragma unroll
-    for (int c = 0; c < kNch; ++c) vals[c] = 0.0;
+    for (int c = 0; c < kNch; ++c) Ev[c] = GV_EMPTY;
+    [[maybe_unused]] unsigned pu[kNch];
+    [[maybe_unused]] double vals[kNch];
+    [[maybe_unused]] int je = 0;
+#pragma unroll
+    for (int c = 0; c < kNch; ++c) {
+      pu[c] = 0u;
+      vals[c] = 0.0;
+    }
     if (ev < a.ncall) {
       uint32_t r[MAXD];
       gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
@@ -95,39 +184,69 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
       const GvJac<Real> J = gv_map_event<Real, MAXD>(r, d, N, s_jac, s_ew, x, bin);
       Real gr[GV_NGRAD];
       const Real g = gv_drell_yan<Real, true>(x, K, gr);
-      vals[0] = gv_weight(J, g);
-#pragma unroll
-      for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = gv_weight(J, gr[p]);
       bool finite = true;
+      if constexpr (F32) {
+        je = J.e;
+        pu[0] = __float_as_uint(__fmul_rn(J.m, g));
 #pragma unroll
-      for (int c = 0; c < kNch; ++c) finite &= gv_finite_bits(gv_abs_bits(vals[c]));
+        for (int p = 0; p < GV_NGRAD; ++p) pu[1 + p] = __float_as_uint(__fmul_rn(J.m, gr[p]));
+#pragma unroll
+        for (int c = 0; c < kNch; ++c) {
+          if ((pu[c] & 0x7FFFFFFFu) == 0u) continue;
+          const AdjWeight w = adj_classify(pu[c], je);
+          if (w.direct) {
+            Ev[c] = w.e2 + 24;  // the double's exponent field - 1022
+          } else {
+            const unsigned long long bits = gv_abs_bits(adj_weight_double(pu[c], je));
+            finite &= gv_finite_bits(bits);
+            Ev[c] = gv_scale_exp(bits);
+          }
+        }
+      } else {
+        vals[0] = gv_weight(J, g);
+#pragma unroll
+        for (int p = 0; p < GV_NGRAD; ++p) vals[1 + p] = gv_weight(J, gr[p]);
+#pragma unroll
+        for (int c = 0; c < kNch; ++c) {
+          const unsigned long long bits = gv_abs_bits(vals[c]);
+          finite &= gv_finite_bits(bits);
+          Ev[c] = gv_scale_exp(bits);
+        }
+      }
       if (!finite) {
         ++nbad;
 #pragma unroll
-        for (int c = 0; c < kNch; ++c) vals[c] = 0.0;
+        for (int c = 0; c < kNch; ++c) {
+          pu[c] = 0u;
+          vals[c] = 0.0;
+          Ev[c] = GV_EMPTY;
+        }
       }
     }
 #pragma unroll
     for (int c = 0; c < kNch; ++c) {
-      const unsigned long long bits = gv_abs_bits(vals[c]);
-      mx[c] = bits > mx[c] ? bits : mx[c];
-      s_v[(k * kNch + c) * B + tid] = vals[c];
+      mE[c] = max(mE[c], Ev[c]);
+      if constexpr (F32)
+        s_p[(k * kNch + c) * B + tid] = pu[c];
+      else
+        s_v[(k * kNch + c) * B + tid] = vals[c];
     }
+    if constexpr (F32) s_je[k * B + tid] = je;
   }
   gv_allow_next_grid();
 
   // tile scales: warp maxima, then one thread per channel over the warps
 #pragma unroll
   for (int c = 0; c < kNch; ++c) {
-    const unsigned long long m = warp_max_u64(mx[c]);
+    const int m = __reduce_max_sync(0xffffffffu, mE[c]);
     if (lane == 0) red_max[wid][c] = m;
   }
   __syncthreads();
   if (tid < kNch) {
-    unsigned long long M = red_max[0][tid];
+    int E = red_max[0][tid];
 #pragma unroll
-    for (int w = 1; w < NW; ++w) M = red_max[w][tid] > M ? red_max[w][tid] : M;
-    s_E[tid] = gv_scale_exp(M);
+    for (int w = 1; w < NW; ++w) E = max(E, red_max[w][tid]);
+    s_E[tid] = E;
   }
   __syncthreads();
 
@@ -135,6 +254,11 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
   // hold sums 2c, 2c+1 and 2c+6, 2c+7, which meet in the first step of the
   // warp's reduce-scatter (lane distance 16), so that step runs as soon as
   // the pair is formed.
+  [[maybe_unused]] int jek[EPT];
+  if constexpr (F32) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) jek[k] = s_je[k * B + tid];
+  }
   const bool up16 = (lane & 16) != 0;
   u128 a6[6];
 #pragma unroll
@@ -148,11 +272,19 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
       if (E != GV_EMPTY) {
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-          const double x = s_v[(k * kNch + ch) * B + tid];
-          if (gv_abs_bits(x) != 0ull) {
-            const GvDecoded dv = gv_decode(x);
-            s1 = add128(s1, gv_fixed_tile(dv, E));
-            s2 = add128(s2, gv_square_tile(dv, gv_square_hi(dv.m), E));
+          if constexpr (F32) {
+            const unsigned u = s_p[(k * kNch + ch) * B + tid];
+            if ((u & 0x7FFFFFFFu) != 0u) {
+              const AdjWeight w = adj_classify(u, jek[k]);
+              if (w.direct) {
+                s1 = add128(s1, adj_fixed24(w.m, w.e2 - E + GV_FB, w.neg));
+                s2 = add128(s2, adj_square24(w.m, 2 * (w.e2 - E) + GV_FB));
+              } else {
+                adj_add_double(adj_weight_double(u, jek[k]), E, s1, s2);
+              }
+            }
+          } else {
+            adj_add_double(s_v[(k * kNch + ch) * B + tid], E, s1, s2);
           }
         }
       }
@@ -195,7 +327,7 @@ template <typename Real, int EPT, int MAXD>
 static cudaError_t gv_launch_adj_t(const GvFillArgs& a, int n_tiles, size_t smem, cudaStream_t s,
                                    bool pdl) {
   auto k = gv_fill_adjoint_kernel<Real, EPT, MAXD>;
-  const size_t total = smem + kStageBytes;  // the grid, then the staged values
+  const size_t total = smem + stage_bytes<Real>();  // the grid, then the staged values
   cudaError_t e = gv_prepare(k, total);
   if (e != cudaSuccess) return e;
   return gv_launch(k, dim3(n_tiles), dim3(GV_TILE / EPT), total, s, pdl, a);
