@@ -185,6 +185,65 @@ __device__ __forceinline__ double gv_weight(const GvJac<float>& J, float g) {
   return gv_ldexp_bits(gv_widen(p), J.e);
 }
 
+// FP32 form, for the exact sums: the weight p 2^e of an FP32 product
+// p = J.m g.  Where p is normal and p 2^e a normal double ("direct"), the
+// weight is m 2^e2 with m the 24-bit significand of p and e2 = nf - 1046, nf
+// its FP64 exponent field (the double gv_weight assembles holds m << 29).
+// Its tile fixed-point terms are formed from m (a 32 x 32 -> 64 bit square):
+// the same exactly rounded integers as through the double, with less integer
+// work.  Every other case takes the double, formed as gv_weight forms it.
+struct GvDirect {
+  bool direct;
+  unsigned m;
+  int e2;
+  bool neg;
+};
+__device__ __forceinline__ GvDirect gv_direct(unsigned u, int e) {
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const int nf = ef + 896 + e;
+  GvDirect w;
+  w.direct = ef != 0 && ef != 0xFF && nf > 0 && nf < 0x7FF;
+  w.m = (u & 0x7FFFFFu) | 0x800000u;
+  w.e2 = nf - 1046;
+  w.neg = (u >> 31) != 0u;
+  return w;
+}
+__device__ __forceinline__ double gv_weight_bits(unsigned u, int e) {
+  return gv_ldexp_bits(gv_widen(__uint_as_float(u)), e);
+}
+
+// round(m 2^s), half up, for m < 2^24 and s <= 72, with the sign: the tile's
+// fixed-point value of a direct weight (|w| < 2^E, s = e2 - E + GV_FB), as
+// gv_fixed_tile rounds the equal double.
+__device__ __forceinline__ u128 gv_direct_fixed(unsigned long long m, int s, bool neg) {
+  u128 v;
+  if (s >= 0) {
+    v.lo = s < 64 ? m << s : 0ull;
+    v.hi = s > 40 ? (s < 64 ? m >> (64 - s) : m << (s - 64)) : 0ull;
+  } else {
+    const int r = -s;
+    v.lo = r < 64 ? ((m >> (r - 1)) + 1ull) >> 1 : 0ull;
+    v.hi = 0ull;
+  }
+  return gv_negate_if(v, neg);
+}
+
+// round(M 2^t), half up, for the square M = m^2 < 2^48 of a direct weight's
+// significand and t = 2 (e2 - E) + GV_FB <= 48: the tile's fixed-point square,
+// as gv_square_tile rounds it.
+__device__ __forceinline__ u128 gv_direct_square(unsigned long long M, int t) {
+  u128 v;
+  if (t >= 0) {
+    v.lo = M << t;
+    v.hi = t > 16 ? M >> (64 - t) : 0ull;
+  } else {
+    const int r = -t;
+    v.lo = r < 64 ? ((M >> (r - 1)) + 1ull) >> 1 : 0ull;
+    v.hi = 0ull;
+  }
+  return v;
+}
+
 template <typename Real>
 struct GvPair;
 template <>
@@ -343,6 +402,19 @@ __device__ __forceinline__ unsigned long long gv_block_max(unsigned long long v,
 }
 
 template <int NW>
+__device__ __forceinline__ int gv_block_max_int(int v, int* scratch) {
+  v = __reduce_max_sync(0xffffffffu, v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  int m = scratch[0];
+#pragma unroll
+  for (int w = 1; w < NW; ++w) m = max(m, scratch[w]);
+  __syncthreads();
+  return m;
+}
+
+template <int NW>
 __device__ __forceinline__ u128 gv_block_sum128(u128 v, u128* scratch) {
   v = warp_sum128(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -432,16 +504,27 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
 
+  // FP32 form without VEGAS+ or a histogram: each weight is kept as its FP32
+  // product and Jacobian exponent and summed through gv_direct
+  constexpr bool DIRECT = sizeof(Real) == 4 && !PLUS && !HIST;
   const long long tile0 = tile * GV_TILE;
-  double w[EPT];
+  [[maybe_unused]] double w[EPT];
+  [[maybe_unused]] unsigned wp[EPT];
+  [[maybe_unused]] int wj[EPT];
   GvBinStore<MAXD> bs[EPT];
   unsigned long long mx = 0ull;
+  int mE = GV_EMPTY;  // the direct form's largest weight scale
   unsigned long long nbad = 0ull;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int local = k * B + tid;
     const long long ev = tile0 + local;
-    w[k] = 0.0;
+    if constexpr (DIRECT) {
+      wp[k] = 0u;
+      wj[k] = 0;
+    } else {
+      w[k] = 0.0;
+    }
     if constexpr (PLUS) qv[k] = 0.0;
     hbin[k] = 0;
     if (ev < ncall) {
@@ -459,6 +542,35 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       const Real g = gv_eval<IG, Real, MAXD>(x, d, K);
       if constexpr (HIST) hbin[k] = gv_hist_bin<Real>(gv_observable<IG, Real, MAXD>(x, K), h_lo,
                                                       h_invw, hb - 2);
+      if constexpr (DIRECT) {
+        const unsigned u = __float_as_uint(__fmul_rn(J.m, g));
+        if ((u & 0x7FFFFFFFu) != 0u) {
+          const GvDirect dd = gv_direct(u, J.e);
+          bool fin = true;
+          int Ev;
+          if (dd.direct) {
+            Ev = dd.e2 + 24;  // gv_scale_exp of the double
+          } else {
+            const unsigned long long ab = gv_abs_bits(gv_weight_bits(u, J.e));
+            fin = gv_finite_bits(ab);
+            Ev = gv_scale_exp(ab);
+          }
+          if (fin) {
+            wp[k] = u;
+            wj[k] = J.e;
+            if (Ev != GV_EMPTY) {
+              mE = max(mE, Ev);
+              const int F = Ev + GV_BINE_OFF;
+#pragma unroll
+              for (int ax = 0; ax < MAXD; ++ax)
+                if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
+            }
+          } else {
+            ++nbad;  // counted, contributes nothing
+          }
+        }
+        continue;
+      }
       double wv = gv_weight(J, g);
       [[maybe_unused]] double qk = 0.0;
       if constexpr (PLUS) {
@@ -493,24 +605,58 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       }
     }
   }
-  const unsigned long long M = gv_block_max<NW>(mx, red_u64);  // also orders ebin
-  const int E = gv_scale_exp(M);
+  // the tile's scale (the barrier also orders ebin)
+  int E;
+  if constexpr (DIRECT)
+    E = gv_block_max_int<NW>(mE, reinterpret_cast<int*>(red_u64));
+  else
+    E = gv_scale_exp(gv_block_max<NW>(mx, red_u64));
 
   u128 s1 = {0ull, 0ull}, s2 = {0ull, 0ull};
   if (E != GV_EMPTY) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      if (gv_abs_bits(w[k]) != 0ull || (PLUS && gv_abs_bits(qv[k]) != 0ull)) {
+      bool any;
+      if constexpr (DIRECT)
+        any = (wp[k] & 0x7FFFFFFFu) != 0u;
+      else
+        any = gv_abs_bits(w[k]) != 0ull || (PLUS && gv_abs_bits(qv[k]) != 0ull);
+      if (any) {
         const int local = k * B + tid;
-        const GvDecoded dw = gv_decode(w[k]);
-        const unsigned long long Pw = gv_square_hi(dw.m);
-        s1 = add128(s1, gv_fixed_tile(dw, E));
-        s2 = add128(s2, gv_square_tile(dw, Pw, E));
         // bins: w^2 (VEGAS+: q^2) at its bin's scale, a 56-bit value, as three
-        // 22-bit limbs
-        const GvDecoded dq = PLUS ? gv_decode(qv[k]) : dw;
-        const unsigned long long P = PLUS ? gv_square_hi(dq.m) : Pw;
-        const int c = 2 * dq.e2 + 98 + 2 * GV_BINE_OFF;
+        // 22-bit limbs, from P = floor(m^2 2^-42) of its 53-bit significand m
+        // and c = 2 e2 + 98 + 2 GV_BINE_OFF
+        unsigned long long P;
+        int c;
+        [[maybe_unused]] GvDecoded dw;
+        if constexpr (DIRECT) {
+          const GvDirect dd = gv_direct(wp[k], wj[k]);
+          if (dd.direct) {
+            const unsigned long long M = (unsigned long long)dd.m * dd.m;
+            s1 = add128(s1, gv_direct_fixed(dd.m, dd.e2 - E + GV_FB, dd.neg));
+            s2 = add128(s2, gv_direct_square(M, 2 * (dd.e2 - E) + GV_FB));
+            P = M << 16;  // m = dd.m 2^29
+            c = 2 * (dd.e2 - 29) + 98 + 2 * GV_BINE_OFF;
+          } else {
+            dw = gv_decode(gv_weight_bits(wp[k], wj[k]));
+            P = gv_square_hi(dw.m);
+            c = 2 * dw.e2 + 98 + 2 * GV_BINE_OFF;
+            if (dw.m != 0ull) {
+              s1 = add128(s1, gv_fixed_tile(dw, E));
+              s2 = add128(s2, gv_square_tile(dw, P, E));
+            } else {
+              continue;  // below the FP64 range: zero
+            }
+          }
+        } else {
+          dw = gv_decode(w[k]);
+          const unsigned long long Pw = gv_square_hi(dw.m);
+          s1 = add128(s1, gv_fixed_tile(dw, E));
+          s2 = add128(s2, gv_square_tile(dw, Pw, E));
+          const GvDecoded dq = PLUS ? gv_decode(qv[k]) : dw;
+          P = PLUS ? gv_square_hi(dq.m) : Pw;
+          c = 2 * dq.e2 + 98 + 2 * GV_BINE_OFF;
+        }
 #pragma unroll
         for (int ax = 0; ax < MAXD; ++ax) {
           if (ax < d) {
@@ -587,7 +733,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
 }
 
 template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
-__global__ void __launch_bounds__(GV_TILE / EPT, (PLUS && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
+__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || (!HIST && EPT <= 4)) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
