@@ -504,9 +504,9 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
 
-  // FP32 form without VEGAS+ or a histogram: each weight is kept as its FP32
-  // product and Jacobian exponent and summed through gv_direct
-  constexpr bool DIRECT = sizeof(Real) == 4 && !PLUS && !HIST;
+  // FP32 form without VEGAS+: each weight is kept as its FP32 product and
+  // Jacobian exponent and summed through gv_direct
+  constexpr bool DIRECT = sizeof(Real) == 4 && !PLUS;
   const long long tile0 = tile * GV_TILE;
   [[maybe_unused]] double w[EPT];
   [[maybe_unused]] unsigned wp[EPT];
@@ -564,6 +564,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
 #pragma unroll
               for (int ax = 0; ax < MAXD; ++ax)
                 if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
+              if constexpr (HIST) atomicMax(hebin + hbin[k], F);
             }
           } else {
             ++nbad;  // counted, contributes nothing
@@ -637,6 +638,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
             s2 = add128(s2, gv_direct_square(M, 2 * (dd.e2 - E) + GV_FB));
             P = M << 16;  // m = dd.m 2^29
             c = 2 * (dd.e2 - 29) + 98 + 2 * GV_BINE_OFF;
+            if constexpr (HIST) dw = GvDecoded{(unsigned long long)dd.m << 29, dd.e2 - 29, dd.neg};
           } else {
             dw = gv_decode(gv_weight_bits(wp[k], wj[k]));
             P = gv_square_hi(dw.m);
@@ -733,7 +735,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
 }
 
 template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
-__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || (!HIST && EPT <= 4)) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
+__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || EPT <= 4) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
