@@ -43,10 +43,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 71_936
+FILL_TRAFFIC_BYTES = 80_384
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "ce2206db1d5429ca38bdfbd4baef27de794c41efbf4b35800c4eed093b036333"
+FILL_SOURCES_SHA256 = "2bf8b49e9a3b320f5dfa41a3aa24182557a72bb8bd9b95025c838aa777994115"
 
 
 def _fill_traffic():

@@ -735,7 +735,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
 }
 
 template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
-__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || EPT <= 4) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
+__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || EPT <= 8) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
