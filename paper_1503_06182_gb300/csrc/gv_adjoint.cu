@@ -12,9 +12,9 @@
 // weights, 48 KB), not held in registers across the tile's maximum, so that
 // two 512-thread or three 256-thread CTAs share an SM.  In the FP32 form a
 // weight is a 24-bit significand times a power of two, and its fixed-point
-// terms are formed from that significand (one 32 x 32 -> 64 bit square):
-// the same exactly rounded integers as through the double, with less
-// integer work.  All six channels share the block-wide
+// terms are formed from that significand (gv_direct*: one 32 x 32 -> 64 bit
+// square), the same exactly rounded integers as through the double, with
+// less integer work.  All six channels share the block-wide
 // steps: one barrier after the per-warp maxima, one after the tile scales,
 // one after the per-warp sums.  Each warp's twelve 128-bit sums leave the warp
 // by a reduce-scatter (every shuffle step halves the values a lane carries),
@@ -48,64 +48,6 @@ __device__ __forceinline__ void rs_step(const u128 (&x)[2 * N], u128 (&y)[N], in
 template <typename Real>
 constexpr size_t stage_bytes() {
   return sizeof(Real) == 8 ? (size_t)GV_TILE * kNch * 8 : (size_t)GV_TILE * (kNch + 1) * 4;
-}
-
-// FP32 form: the weight J g = p 2^e of an FP32 product p = J.m g, as the
-// forward fill forms it.  Where p is normal and p 2^e is a normal double
-// ("direct"), the weight is m 2^e2 with m the 24-bit significand of p and
-// e2 = nf - 1046, nf its FP64 exponent field; every other case forms the
-// double itself.
-struct AdjWeight {
-  bool direct;
-  unsigned m;
-  int e2;
-  bool neg;
-};
-__device__ __forceinline__ AdjWeight adj_classify(unsigned u, int e) {
-  const int ef = (int)((u >> 23) & 0xFFu);
-  const int nf = ef + 896 + e;
-  AdjWeight w;
-  w.direct = ef != 0 && ef != 0xFF && nf > 0 && nf < 0x7FF;
-  w.m = (u & 0x7FFFFFu) | 0x800000u;
-  w.e2 = nf - 1046;
-  w.neg = (u >> 31) != 0u;
-  return w;
-}
-__device__ __forceinline__ double adj_weight_double(unsigned u, int e) {
-  return gv_ldexp_bits(gv_widen(__uint_as_float(u)), e);
-}
-
-// round(m 2^s), half up, for m < 2^24 and s <= 72, with the sign: the
-// tile's fixed-point value of a direct weight (|w| < 2^E, s = e2 - E + GV_FB).
-// The same exact rounding as gv_fixed_tile applies to the equal double.
-__device__ __forceinline__ u128 adj_fixed24(unsigned long long m, int s, bool neg) {
-  u128 v;
-  if (s >= 0) {
-    v.lo = s < 64 ? m << s : 0ull;
-    v.hi = s > 40 ? (s < 64 ? m >> (64 - s) : m << (s - 64)) : 0ull;
-  } else {
-    const int r = -s;
-    v.lo = r < 64 ? ((m >> (r - 1)) + 1ull) >> 1 : 0ull;
-    v.hi = 0ull;
-  }
-  return gv_negate_if(v, neg);
-}
-
-// round(m^2 2^t), half up, for m < 2^24 and t <= 48: the tile's fixed-point
-// square of a direct weight (t = 2 e2 - 2E + GV_FB), from one 32 x 32 -> 64
-// bit product.
-__device__ __forceinline__ u128 adj_square24(unsigned m, int t) {
-  const unsigned long long M = (unsigned long long)m * m;
-  u128 v;
-  if (t >= 0) {
-    v.lo = M << t;
-    v.hi = t > 16 ? M >> (64 - t) : 0ull;
-  } else {
-    const int r = -t;
-    v.lo = r < 64 ? ((M >> (r - 1)) + 1ull) >> 1 : 0ull;
-    v.hi = 0ull;
-  }
-  return v;
 }
 
 // A weight's two fixed-point terms through the general FP64 route.
@@ -193,11 +135,11 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
 #pragma unroll
         for (int c = 0; c < kNch; ++c) {
           if ((pu[c] & 0x7FFFFFFFu) == 0u) continue;
-          const AdjWeight w = adj_classify(pu[c], je);
+          const GvDirect w = gv_direct(pu[c], je);
           if (w.direct) {
             Ev[c] = w.e2 + 24;  // the double's exponent field - 1022
           } else {
-            const unsigned long long bits = gv_abs_bits(adj_weight_double(pu[c], je));
+            const unsigned long long bits = gv_abs_bits(gv_weight_bits(pu[c], je));
             finite &= gv_finite_bits(bits);
             Ev[c] = gv_scale_exp(bits);
           }
@@ -275,12 +217,13 @@ __global__ void __launch_bounds__(GV_TILE / EPT, AdjBlocks<Real, EPT>::value)
           if constexpr (F32) {
             const unsigned u = s_p[(k * kNch + ch) * B + tid];
             if ((u & 0x7FFFFFFFu) != 0u) {
-              const AdjWeight w = adj_classify(u, jek[k]);
+              const GvDirect w = gv_direct(u, jek[k]);
               if (w.direct) {
-                s1 = add128(s1, adj_fixed24(w.m, w.e2 - E + GV_FB, w.neg));
-                s2 = add128(s2, adj_square24(w.m, 2 * (w.e2 - E) + GV_FB));
+                s1 = add128(s1, gv_direct_fixed(w.m, w.e2 - E + GV_FB, w.neg));
+                s2 = add128(s2, gv_direct_square((unsigned long long)w.m * w.m,
+                                                   2 * (w.e2 - E) + GV_FB));
               } else {
-                adj_add_double(adj_weight_double(u, jek[k]), E, s1, s2);
+                adj_add_double(gv_weight_bits(u, jek[k]), E, s1, s2);
               }
             }
           } else {

@@ -80,6 +80,56 @@ def test_adjoint_fp64_matches_oracle_six_axes():
     assert rel(e, ref.error) < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("ept", [4, 8])
+def test_sums_equal_exact_sums_of_event_weights_with_subnormal_products(precision, ept):
+    """The fill's once-rounded sums against the exact sums of its own weights
+    (the per-event diagnostics form each weight as a double).  A narrow
+    Gaussian minus 1e-40: almost every event's FP32 product is subnormal, so
+    the FP32 fill takes its general route for it (the bins far from the peak
+    hold nothing else), the few central events its direct route."""
+    from fractions import Fraction
+
+    ndim, nbins, ncall = 4, 50, 200_003
+    params = (0.01, 1e-40)
+    g = v.Vegas(ndim, nbins, 4242, precision=precision)
+    try:
+        g.set(v.VEGAS_OPT_EPT, ept)
+        w, bins = g.eval_events(v.VEGAS_GAUSS, params, 0, np.arange(ncall, dtype=np.int64))
+        g.iterate(ncall, 1, v.VEGAS_GAUSS, params)
+        sums = g.last_sums()
+    finally:
+        g.close()
+    tiny = (w != 0.0) & (np.abs(w) < 2.0**-120)
+    assert tiny.sum() > 100_000 and (np.abs(w) > 2.0**-100).sum() > 100
+    # exact sums as integers: w = mi 2^(e - 53) = mi 2^sh / 2^1200
+    m, e = np.frexp(w)
+    mi = (m * 2.0**53).astype(np.int64)
+    sh = e.astype(np.int64) - 53 + 1200
+    assert sh[w != 0].min() >= 0
+    s1, s2 = 0, 0
+    d = [0] * (ndim * nbins)
+    dmax = np.zeros(ndim * nbins)
+    for j in np.flatnonzero(w):
+        x = int(mi[j]) << int(sh[j])
+        xx = x * x  # over 2^2400
+        s1 += x
+        s2 += xx
+        for ax in range(ndim):
+            k = ax * nbins + int(bins[j, ax])
+            d[k] += xx
+            dmax[k] = max(dmax[k], abs(w[j]))
+    S1, S2 = float(Fraction(s1, 1 << 1200)), float(Fraction(s2, 1 << 2400))
+    assert abs(sums[0] - S1) <= 1e-15 * abs(S1)
+    assert abs(sums[1] - S2) <= 1e-15 * S2
+    dref = np.array([float(Fraction(x, 1 << 2400)) for x in d])
+    nz = dref != 0
+    assert np.array_equal(sums[2:] != 0, nz)
+    assert rel(sums[2:][nz], dref[nz]) < 1e-13
+    # bins whose every event came through the general route
+    assert np.count_nonzero(nz & (dmax < 2.0**-120)) >= 10
+
+
 def test_adjoint_matches_central_differences_on_gpu():
     """Frozen grid, one iteration, the same events: the adjoint estimate equals
     the central difference of the forward estimate (h = 1e-4 theta)."""
