@@ -46,7 +46,7 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FILL_TRAFFIC_BYTES = 80_384
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "2bf8b49e9a3b320f5dfa41a3aa24182557a72bb8bd9b95025c838aa777994115"
+FILL_SOURCES_SHA256 = "1d12e0c3fe11bc722eb085512457e689e0315a331646eb4ee89f46bc24f037e6"
 
 
 def _fill_traffic():

@@ -111,7 +111,6 @@ struct vegas_batch {
     unsigned long long* d_counter = nullptr;
   };
   std::vector<FillClass> cls;
-  double* logtab = nullptr;
   size_t reduce_smem = 0;
   int ept = 0;
   // graph cache
@@ -206,7 +205,6 @@ int upload_tables(vegas_batch* B) {
     r.tickets = x.tickets;
     r.alpha = B->alpha;
     r.inv_nbins = 1.0 / (double)B->N;
-    r.logtab = B->logtab;
     r.grid = x.grid;
     for (int yy = 0; yy < gy; ++yy)
       for (int xx = 0; xx < gx; ++xx) rt.push_back(make_int4(b, xx, yy, gx * gy));
@@ -367,8 +365,6 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     q[6] = off;  // tickets
     off = a256(off + gv_tickets_ints(x.nacc) * 4);
   }
-  const size_t o_log = off;
-  off = a256(off + 258 * 8);
   const size_t o_ig = off;
   off = a256(off + (size_t)n * 4);
   const size_t o_order = off;
@@ -396,13 +392,9 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     x.tileE = (int*)(base + q[8]);
     x.tickets = (int*)(base + q[6]);
   }
-  B->logtab = (double*)(base + o_log);
   B->d_ig = (int*)(base + o_ig);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(B->dmem, 0, off, B->stream) != cudaSuccess) st = VEGAS_ECUDA;
-  if (!st && cudaMemcpy(B->logtab, gv::host_log_table(), 258 * sizeof(double),
-                        cudaMemcpyHostToDevice) != cudaSuccess)
-    st = VEGAS_ECUDA;
   // uniform grids, constants, reset state
   for (int b = 0; b < n && !st; ++b) {
     Member& x = B->m[b];

@@ -147,7 +147,6 @@ struct vegas_ctx {
   double* params = nullptr;
   double* kconst = nullptr;
   double* sums = nullptr;
-  double* logtab = nullptr;
   int* tickets = nullptr;  // reduce tickets (zero between iterations)
   int nacc_max = 0;
   // histogram of the observable (hist_nh = 0: none); hist_valid: the last
@@ -462,7 +461,6 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
   r.tickets = c->tickets;
   r.alpha = c->alpha;
   r.inv_nbins = 1.0 / (double)c->nbins;
-  r.logtab = c->logtab;
   r.grid = c->grid;
   return r;
 }
@@ -879,28 +877,6 @@ const uint32_t kStateMagic = 0x47564547u;  // "GVEG"
 // ============================================================================
 // C ABI
 // ============================================================================
-namespace gv {
-// Table of the device log: R_j ~ 1/c_j at the centre of each 1/128-wide
-// interval of [1,2), L_j = -ln R_j, then ln 2 as a 42-bit head and a tail.
-const double* host_log_table() {
-  static double tab[258];
-  static std::once_flag once;
-  std::call_once(once, [] {
-    for (int j = 0; j < 128; ++j) {
-      const double cj = 1.0 + (j + 0.5) / 128.0;
-      const double R = 1.0 / cj;
-      tab[2 * j] = R;
-      tab[2 * j + 1] = (double)(-logl((long double)R));
-    }
-    const long double ln2 = logl(2.0L);
-    const double hi = std::ldexp(std::floor(std::ldexp((double)ln2, 42)), -42);
-    tab[256] = hi;
-    tab[257] = (double)(ln2 - (long double)hi);
-  });
-  return tab;
-}
-}  // namespace gv
-
 extern "C" {
 
 const char* vegas_strerror(int status) {
@@ -961,8 +937,6 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   off = align256(off + GV_MAXPARAMS * 8);
   const size_t o_k = off;
   off = align256(off + GV_NCONST * 8);
-  const size_t o_log = off;
-  off = align256(off + 258 * 8);
   const size_t o_sums = off;
   off = align256(off + (size_t)c->nacc_max * 8);
   const size_t o_tick = off;
@@ -981,16 +955,12 @@ int vegas_init(int ndim, int nbins, uint64_t seed, vegas_ctx** out) {
   c->params = (double*)(b + o_par);
   c->kconst = (double*)(b + o_k);
   c->sums = (double*)(b + o_sums);
-  c->logtab = (double*)(b + o_log);
   c->tickets = (int*)(b + o_tick);
   c->hist_acc = (double*)(b + o_hist);
   c->hist_out = c->hist_acc + 4 * (GV_HIST_MAX + 2);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(c->fixed, 0, off, c->stream) != cudaSuccess ||
       gv::launch_reset(c->st, c->stream) != cudaSuccess)
-    st = VEGAS_ECUDA;
-  if (!st && cudaMemcpyAsync(c->logtab, gv::host_log_table(), 258 * sizeof(double),
-                             cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     st = VEGAS_ECUDA;
   if (!st) {
     std::vector<double> e((size_t)ndim * (nbins + 1));

@@ -173,7 +173,6 @@ struct GvReduceArgs {
   int* tickets;                  // gv_tickets_ints(nacc) counters, one per 128-byte line
   // grid refinement
   double alpha, inv_nbins;
-  const double* logtab;          // table of the FP64 log (see gv_reduce.cu)
   double* grid;                  // grid pack (refined in place, one axis per CTA)
 };
 
@@ -497,7 +496,6 @@ cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int
 cudaError_t launch_consts(int integrand, const double* params, double* kconst, cudaStream_t s);
 cudaError_t launch_reset(GvState* st, cudaStream_t s);
 cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
-const double* host_log_table();  // 258 doubles, see gv_log_pos
 cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,
                              unsigned long long ev0, long long n, int d, uint32_t* out,
                              cudaStream_t s);

@@ -16,6 +16,7 @@
 // events per thread, batched or not).
 #pragma once
 #include "gv_common.cuh"
+#include "gv_math64.cuh"
 
 // Derived constants (filled by the setup kernel from the user parameters).
 // Gaussian
@@ -58,7 +59,9 @@ template <typename T>
 struct GvMath;
 
 // The FP32 form uses the MUFU-based intrinsics (ex2/lg2/rsqrt/rcp/sin/cos
-// with a few ulp of error); the FP64 form the correctly rounded library.
+// with a few ulp of error); the FP64 form the table-driven exp and log of
+// gv_math64.cuh (within an ulp, fewer FP64 operations than the library's) and
+// the library for the rest.
 template <>
 struct GvMath<float> {
   __device__ static __forceinline__ float exp(float x) { return __expf(x); }
@@ -73,8 +76,10 @@ struct GvMath<float> {
 
 template <>
 struct GvMath<double> {
-  __device__ static __forceinline__ double exp(double x) { return ::exp(x); }
-  __device__ static __forceinline__ double log(double x) { return ::log(x); }
+  __device__ static __forceinline__ double exp(double x) { return gv_exp64(x); }
+  __device__ static __forceinline__ double log(double x) {
+    return x > 0.0 && x < INFINITY ? gv_log_pos(x) : ::log(x);
+  }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   __device__ static __forceinline__ double div(double a, double b) { return a / b; }
   __device__ static __forceinline__ void sincospi(double x, double* s, double* c) {

@@ -170,46 +170,6 @@ __device__ __forceinline__ void gv_bar(int id, int nthr) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
 }
 
-// ---------------------------------------------------------------------------
-// Natural log of a positive double, table-driven (P. T. P. Tang,
-// "Table-driven implementation of the logarithm function in IEEE
-// floating-point arithmetic", ACM TOMS 16 (1990)): x = 2^k m, m in [1,2);
-// with R_j ~ 1/c_j for the 1/128-wide interval of m, r = m R_j - 1 (one fma,
-// one rounding, |r| < 2^-7) and ln x = k ln2 + L_j + log1p(r), L_j = -ln R_j,
-// log1p(r) by its Taylor series to r^7 (truncation below 2^-59 relative).
-// The table (R_j, L_j for j < 128, then ln2 split into a 42-bit head and a
-// tail) is built by the host from its libm when a context is created.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double gv_log1p_series(double r) {
-  double p = 1.0 / 7.0;
-  p = fma(p, r, -1.0 / 6.0);
-  p = fma(p, r, 1.0 / 5.0);
-  p = fma(p, r, -1.0 / 4.0);
-  p = fma(p, r, 1.0 / 3.0);
-  p = fma(p, r, -0.5);
-  p = fma(p, r, 1.0);
-  return p * r;
-}
-
-__device__ __forceinline__ double gv_log_pos(double x, const double* __restrict__ tab) {
-  // near 1 the reduction would cancel: r = x - 1 is exact there (Sterbenz)
-  if (fabs(x - 1.0) <= 0x1p-7) return gv_log1p_series(x - 1.0);
-  long long b = __double_as_longlong(x);
-  int k = 0;
-  if (b < (1ll << 52)) {  // subnormal: scale by 2^54
-    x *= 0x1p54;
-    b = __double_as_longlong(x);
-    k = -54;
-  }
-  k += (int)(b >> 52) - 1023;
-  const int j = (int)((b >> 45) & 127);
-  const double m = __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
-  const double R = __ldg(tab + 2 * j), L = __ldg(tab + 2 * j + 1);
-  const double p = gv_log1p_series(fma(m, R, -1.0));
-  const double kd = (double)k;
-  return fma(kd, __ldg(tab + 256), L) + fma(kd, __ldg(tab + 257), p);
-}
-
 // The iteration's finalisation, by the threads [0, nthr) of a group (local
 // thread index tid, barrier id bar): the iteration record, the stage's
 // combination and the per-iteration state.
@@ -301,10 +261,10 @@ __device__ __forceinline__ void pack_axis_tables(double* grid, const double* e_s
 
 // ((1 - rho)/(-ln rho))^alpha for 0 < rho < 1, with the common exponents
 // evaluated by roots rather than pow.
-__device__ __forceinline__ double compress(double rho, double alpha, const double* tab) {
+__device__ __forceinline__ double compress(double rho, double alpha) {
   if (rho <= 0.0) return 0.0;
   if (rho >= 1.0) return 1.0;
-  const double L = -gv_log_pos(rho, tab);
+  const double L = -gv_log_pos(rho);
   const double om = 1.0 - rho;
   if (alpha == 1.5) {
     const double y = rsqrt(L);
@@ -375,7 +335,7 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
       double rv = 0.0, sl = 0.0;
       const double s6 = r[i];
       if (s6 > 0.0) {
-        rv = compress(s6 * inv, a.alpha, a.logtab);
+        rv = compress(s6 * inv, a.alpha);
         if (rv > 0.0) sl = (e[i + 1] - e[i]) * __drcp_rn(rv);
       }
       r[i] = rv;
