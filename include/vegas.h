@@ -281,8 +281,9 @@ int vegas_get_ept(const vegas_ctx* ctx, int* ept);
 
 /* ---- batched integrations (many independent VEGAS runs per launch) ----
  * n integrations of uneven dimension, call count and integrand run as one
- * persistent fill launch per iteration over a work list of (integration,
- * tile) items taken largest-first from a device counter, then one reduce and
+ * persistent fill launch per iteration, dimension class (at most 4, 8, 16
+ * axes) and integrand over a work list of (integration, tile) items taken
+ * largest-first from a device counter, then one reduce and
  * one refine launch serving every integration; the itmx iterations are
  * captured in one CUDA graph (Section 2.1: many independent runs, here
  * sharing one device).  All integrations share nbins and seed.

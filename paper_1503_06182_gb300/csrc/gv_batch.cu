@@ -100,10 +100,10 @@ struct vegas_batch {
   GvReduceArgs* d_red = nullptr;
   int4* d_red_tasks = nullptr;
   int n_red_tasks = 0;
-  int* d_ig = nullptr;
-  // one work list per dimension class (members of at most 4, 8, 16 axes)
+  // one work list per dimension class (members of at most 4, 8, 16 axes) and
+  // integrand
   struct FillClass {
-    int maxd = 0, n = 0, ctas = 0;
+    int maxd = 0, ig = 0, n = 0, ctas = 0;
     long long total = 0;
     size_t smem = 0;
     int* d_order = nullptr;
@@ -126,14 +126,14 @@ namespace {
 // Dimension class of a member (the same classes as the single-context fill).
 int dim_class(int ig, int d) { return (d <= 4 && ig != VEGAS_EE3J) ? 4 : d <= 8 ? 8 : 16; }
 
-// The class' fill launch (its counter reset first) and its occupancy.
+// The list's fill launch (its counter reset first) and its occupancy.
 cudaError_t fill_class(vegas_batch* B, const vegas_batch::FillClass& c, int ept, int ctas) {
   cudaError_t e = cudaMemsetAsync(c.d_counter, 0, sizeof(unsigned long long), B->stream);
   if (e != cudaSuccess) return e;
   auto f = c.maxd == 4 ? (B->fp32 ? gv::fill_batch_f4 : gv::fill_batch_d4)
            : c.maxd == 8 ? (B->fp32 ? gv::fill_batch_f8 : gv::fill_batch_d8)
                          : (B->fp32 ? gv::fill_batch_f16 : gv::fill_batch_d16);
-  return f(ept, ctas, c.smem, B->stream, B->d_fill, B->d_ig, c.d_order, c.d_start, c.n, c.total,
+  return f(c.ig, ept, ctas, c.smem, B->stream, B->d_fill, c.d_order, c.d_start, c.n, c.total,
            c.d_counter);
 }
 
@@ -141,7 +141,7 @@ int class_occupancy(vegas_batch* B, const vegas_batch::FillClass& c, int ept) {
   auto f = c.maxd == 4 ? (B->fp32 ? gv::fill_batch_occ_f4 : gv::fill_batch_occ_d4)
            : c.maxd == 8 ? (B->fp32 ? gv::fill_batch_occ_f8 : gv::fill_batch_occ_d8)
                          : (B->fp32 ? gv::fill_batch_occ_f16 : gv::fill_batch_occ_d16);
-  return std::max(1, f(ept, c.smem));
+  return std::max(1, f(c.ig, ept, c.smem));
 }
 
 cudaError_t fill_batch(vegas_batch* B, int ept) {
@@ -365,14 +365,12 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     q[6] = off;  // tickets
     off = a256(off + gv_tickets_ints(x.nacc) * 4);
   }
-  const size_t o_ig = off;
-  off = a256(off + (size_t)n * 4);
   const size_t o_order = off;
   off = a256(off + (size_t)n * 4);
   const size_t o_start = off;
-  off = a256(off + (size_t)(n + 3) * 8);
-  const size_t o_ccount = off;  // three class counters, one per 128-byte line
-  off = a256(off + 3 * 128);
+  off = a256(off + (size_t)(n + 9) * 8);
+  const size_t o_ccount = off;  // up to nine list counters, one per 128-byte line
+  off = a256(off + 9 * 128);
   if (cudaMalloc(&B->dmem, off) != cudaSuccess) {
     cudaGetLastError();
     vegas_batch_free(B);
@@ -392,7 +390,6 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
     x.tileE = (int*)(base + q[8]);
     x.tickets = (int*)(base + q[6]);
   }
-  B->d_ig = (int*)(base + o_ig);
   int st = VEGAS_OK;
   if (cudaMemsetAsync(B->dmem, 0, off, B->stream) != cudaSuccess) st = VEGAS_ECUDA;
   // uniform grids, constants, reset state
@@ -408,46 +405,47 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
         gv::launch_reset(x.st, B->stream) != cudaSuccess)
       st = VEGAS_ECUDA;
   }
-  // work lists, one per dimension class: largest expected cost first
+  // work lists, one per dimension class and integrand: largest expected cost first
   if (!st) {
     std::vector<int> order;
     std::vector<long long> start;
-    std::vector<int> ig(n);
-    for (int b = 0; b < n; ++b) ig[b] = B->m[b].ig;
     int pos = 0, slot = 0;
     for (int maxd : {4, 8, 16}) {
-      std::vector<int> mem;
-      for (int b = 0; b < n; ++b)
-        if (dim_class(B->m[b].ig, B->m[b].d) == maxd) mem.push_back(b);
-      if (mem.empty()) continue;
-      std::stable_sort(mem.begin(), mem.end(), [&](int p, int q) {
-        return B->m[p].n_tiles * tile_cost(B->m[p].ig, B->m[p].d) >
-               B->m[q].n_tiles * tile_cost(B->m[q].ig, B->m[q].d);
-      });
-      vegas_batch::FillClass c;
-      c.maxd = maxd;
-      c.n = (int)mem.size();
-      c.d_order = (int*)(base + o_order) + pos;
-      c.d_start = (long long*)(base + o_start) + pos + slot;
-      c.d_counter = (unsigned long long*)(base + o_ccount + 128 * slot);
-      long long acc = 0;
-      start.push_back(0);
-      for (int b : mem) {
-        order.push_back(b);
-        acc += B->m[b].n_tiles;
-        start.push_back(acc);
-        c.smem = std::max(c.smem, GvFillSmem(B->m[b].d, nbins, B->fp32 ? 4 : 8, true, maxd > 4).total);
+      for (int ig : {VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J}) {
+        std::vector<int> mem;
+        for (int b = 0; b < n; ++b)
+          if (B->m[b].ig == ig && dim_class(B->m[b].ig, B->m[b].d) == maxd) mem.push_back(b);
+        if (mem.empty()) continue;
+        std::stable_sort(mem.begin(), mem.end(), [&](int p, int q) {
+          return B->m[p].n_tiles * tile_cost(B->m[p].ig, B->m[p].d) >
+                 B->m[q].n_tiles * tile_cost(B->m[q].ig, B->m[q].d);
+        });
+        vegas_batch::FillClass c;
+        c.maxd = maxd;
+        c.ig = ig;
+        c.n = (int)mem.size();
+        c.d_order = (int*)(base + o_order) + pos;
+        c.d_start = (long long*)(base + o_start) + pos + slot;
+        c.d_counter = (unsigned long long*)(base + o_ccount + 128 * slot);
+        long long acc = 0;
+        start.push_back(0);
+        for (int b : mem) {
+          order.push_back(b);
+          acc += B->m[b].n_tiles;
+          start.push_back(acc);
+          c.smem = std::max(c.smem,
+                            GvFillSmem(B->m[b].d, nbins, B->fp32 ? 4 : 8, true, maxd > 4).total);
+        }
+        c.total = acc;
+        B->cls.push_back(c);
+        pos += c.n;
+        ++slot;
       }
-      c.total = acc;
-      B->cls.push_back(c);
-      pos += c.n;
-      ++slot;
     }
     if (cudaMemcpy(base + o_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(base + o_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(B->d_ig, ig.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            cudaSuccess)
       st = VEGAS_ECUDA;
   }
   if (!st) {
