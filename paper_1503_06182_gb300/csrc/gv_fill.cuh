@@ -734,8 +734,23 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   }
 }
 
+// Minimum resident CTAs per SM in the fill's launch bound (0: none), i.e. its
+// register budget.  FP32 fills of at most 8 axes: 64 registers at any width
+// (the stratified fill included).  FP32 fills of up to 16 axes without
+// VEGAS+, 4 events per thread: three 256-thread CTAs, 80 registers (111 for
+// the 13-axis NLO-shaped weight unbounded).  FP64 fills: none (they would
+// spill).
+template <typename Real, int EPT, int MAXD, bool PLUS>
+struct GvFillBlocks {
+  static constexpr int B = GV_TILE / EPT;
+  static constexpr int value = sizeof(Real) != 4       ? 0
+                               : MAXD <= 8             ? 65536 / (64 * B)
+                               : (!PLUS && EPT == 4)   ? 3
+                                                       : 0;
+};
+
 template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
-__global__ void __launch_bounds__(GV_TILE / EPT, ((PLUS || EPT <= 8) && MAXD <= 8 && sizeof(Real) == 4) ? 65536 / (64 * (GV_TILE / EPT)) : 0)
+__global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, PLUS>::value))
     gv_fill_kernel(const GvFillArgs a) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
