@@ -11,8 +11,11 @@
 // ---------------------------------------------------------------------------
 // Persistent fill over the work list.
 // ---------------------------------------------------------------------------
+// At 4 events per thread the single-integration fill's register budget (64 or
+// 80 registers); at 8 the kernels would spill under it and keep their own.
 template <int IG, typename Real, int EPT, int MAXD>
-__global__ void __launch_bounds__(GV_TILE / EPT)
+__global__ void __launch_bounds__(GV_TILE / EPT,
+                                  (EPT == 4 ? GvFillBlocks<Real, EPT, MAXD, false>::value : 0))
     gv_fill_batch_kernel(const GvFillArgs* __restrict__ args, const int* __restrict__ order,
                          const long long* __restrict__ item_start, int n, long long total,
                          unsigned long long* counter) {
