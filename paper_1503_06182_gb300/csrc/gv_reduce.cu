@@ -620,12 +620,22 @@ __global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs
   extern __shared__ __align__(16) double sm[];
   __shared__ u192 s_part[8][32];
   __shared__ int s_emax[256], s_flags[4], s_won[GV_MAXD];
+  // the integration's arguments in shared memory, read where used (a copy in
+  // registers held ~40 of them for the whole task)
+  __shared__ GvReduceArgs s_a;
   const int4 t = tasks[blockIdx.x];
-  GvReduceArgs a = args[t.x];
-  a.k = k;
-  a.last = last;
-  a.inv_m1 = inv_m1;
-  gv_reduce_task(a, t.y, t.z, t.w, s_part, s_emax, s_flags, s_won, sm);
+  static_assert(sizeof(GvReduceArgs) % 4 == 0, "GvReduceArgs copy");
+  const unsigned* src = reinterpret_cast<const unsigned*>(args + t.x);
+  unsigned* dst = reinterpret_cast<unsigned*>(&s_a);
+  for (int i = threadIdx.x; i < (int)(sizeof(GvReduceArgs) / 4); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_a.k = k;
+    s_a.last = last;
+    s_a.inv_m1 = inv_m1;
+  }
+  __syncthreads();
+  gv_reduce_task(s_a, t.y, t.z, t.w, s_part, s_emax, s_flags, s_won, sm);
 }
 
 // ---------------------------------------------------------------------------
