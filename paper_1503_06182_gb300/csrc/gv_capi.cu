@@ -507,7 +507,10 @@ int autotune(vegas_ctx* c, Plan& p) {
   cudaEvent_t e0, e1;
   GV_TRY(cudaEventCreate(&e0));
   GV_TRY(cudaEventCreate(&e1));
-  float best = 1e30f;
+  // the fastest candidate, but 4 events per thread (the best for every forward
+  // fill measured) unless another is more than 2% faster: a few trial launches
+  // are noisy enough to flip a 10% difference now and then
+  float best = 1e30f, t4 = 1e30f;
   int best_ept = 4;
   for (int i = 0; i < nc; ++i) {
     const int ept = cands[i];
@@ -518,7 +521,7 @@ int autotune(vegas_ctx* c, Plan& p) {
       continue;
     }
     float best_i = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, c->stream);
       launch_fill_plan(c, p, ept);
       cudaEventRecord(e1, c->stream);
@@ -527,11 +530,13 @@ int autotune(vegas_ctx* c, Plan& p) {
       cudaEventElapsedTime(&ms, e0, e1);
       best_i = std::min(best_i, ms);
     }
+    if (ept == 4) t4 = best_i;
     if (best_i < best) {
       best = best_i;
       best_ept = ept;
     }
   }
+  if (best_ept != 4 && t4 < 1e30f && best > 0.98f * t4) best_ept = 4;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   GV_TRY(cudaGetLastError());

@@ -1,6 +1,6 @@
 """Batched form: many integrations of uneven dimension, call count and
-integrand advanced by one persistent fill launch per iteration (requires a
-GB300).
+integrand advanced by persistent fill launches, one per iteration, dimension
+class and integrand (requires a GB300).
 
 Bar: every member bit-identical to a single context with the same Philox
 batch word (any schedule, any events-per-thread, graph or not); FP64 members
@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 
 NBINS = 50
 SEED = 4321
-# (ndim, ncall, integrand, params): uneven sizes, ragged tails, every integrand,
-# both dimension classes of the single-context kernels
+# (ndim, ncall, integrand, params): uneven sizes, ragged tails, every integrand
+# in every dimension class it can take (4, 8, 16 axes): all eight work lists
 MEMBERS = [
     (2, 5_000, v.VEGAS_GAUSS, GAUSS_PARAMS),
     (4, 20_011, v.VEGAS_DY, DY_PARAMS),
@@ -26,6 +26,8 @@ MEMBERS = [
     (8, 3_001, v.VEGAS_GAUSS, GAUSS_PARAMS),
     (6, 1_500, v.VEGAS_DY, DY_PARAMS),
     (16, 2_500, v.VEGAS_GAUSS, GAUSS_PARAMS),
+    (12, 2_047, v.VEGAS_DY, DY_PARAMS),
+    (10, 3_333, v.VEGAS_EE3J, EE3J_PARAMS),
 ]
 STAGES = (3, 2)
 
