@@ -111,6 +111,14 @@ struct vegas_batch {
     unsigned long long* d_counter = nullptr;
   };
   std::vector<FillClass> cls;
+  // the lists' fill launches of one iteration run side by side: list
+  // launch_order[0] on the main stream, the others on side streams forked from
+  // it and joined before the reduce, so that a list's CTAs take the SMs the
+  // previous lists' last CTAs leave idle
+  std::vector<int> launch_order;  // largest estimated cost first
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
   size_t reduce_smem = 0;
   int ept = 0;
   // graph cache
@@ -127,13 +135,14 @@ namespace {
 int dim_class(int ig, int d) { return (d <= 4 && ig != VEGAS_EE3J) ? 4 : d <= 8 ? 8 : 16; }
 
 // The list's fill launch (its counter reset first) and its occupancy.
-cudaError_t fill_class(vegas_batch* B, const vegas_batch::FillClass& c, int ept, int ctas) {
-  cudaError_t e = cudaMemsetAsync(c.d_counter, 0, sizeof(unsigned long long), B->stream);
+cudaError_t fill_class(vegas_batch* B, const vegas_batch::FillClass& c, int ept, int ctas,
+                       cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c.d_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   auto f = c.maxd == 4 ? (B->fp32 ? gv::fill_batch_f4 : gv::fill_batch_d4)
            : c.maxd == 8 ? (B->fp32 ? gv::fill_batch_f8 : gv::fill_batch_d8)
                          : (B->fp32 ? gv::fill_batch_f16 : gv::fill_batch_d16);
-  return f(c.ig, ept, ctas, c.smem, B->stream, B->d_fill, c.d_order, c.d_start, c.n, c.total,
+  return f(c.ig, ept, ctas, c.smem, s, B->d_fill, c.d_order, c.d_start, c.n, c.total,
            c.d_counter);
 }
 
@@ -147,7 +156,8 @@ int class_occupancy(vegas_batch* B, const vegas_batch::FillClass& c, int ept) {
 cudaError_t fill_batch(vegas_batch* B, int ept) {
   if (ept != 4 && ept != 8) return cudaErrorInvalidValue;
   for (const auto& c : B->cls) {
-    const cudaError_t e = fill_class(B, c, ept, class_occupancy(B, c, ept) * B->sm_count);
+    const cudaError_t e =
+        fill_class(B, c, ept, class_occupancy(B, c, ept) * B->sm_count, B->stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -250,7 +260,20 @@ int ensure_per_iter(vegas_batch* B, int itmx) {
 
 int enqueue_iterations(vegas_batch* B, int itmx) {
   for (int k = 0; k < itmx; ++k) {
-    for (const auto& c : B->cls) GB_TRY(fill_class(B, c, B->ept, c.ctas));
+    const int nl = (int)B->launch_order.size();
+    if (nl > 1) GB_TRY(cudaEventRecord(B->fork, B->stream));
+    for (int i = 0; i < nl; ++i) {
+      const auto& c = B->cls[B->launch_order[i]];
+      if (i == 0) {
+        GB_TRY(fill_class(B, c, B->ept, c.ctas, B->stream));
+      } else {
+        cudaStream_t s = B->side[i - 1];
+        GB_TRY(cudaStreamWaitEvent(s, B->fork, 0));
+        GB_TRY(fill_class(B, c, B->ept, c.ctas, s));
+        GB_TRY(cudaEventRecord(B->join[i - 1], s));
+      }
+    }
+    for (int i = 1; i < nl; ++i) GB_TRY(cudaStreamWaitEvent(B->stream, B->join[i - 1], 0));
     GB_TRY(gv::launch_reduce_batch(B->d_red, B->d_red_tasks, B->n_red_tasks, k, k == itmx - 1,
                                    k > 0 ? 1.0 / (double)k : 0.0, B->reduce_smem, B->stream));
   }
@@ -451,6 +474,36 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
             cudaSuccess)
       st = VEGAS_ECUDA;
   }
+  // launch order of the lists (largest estimated cost first), side streams
+  // and the events that fork and join them
+  if (!st) {
+    std::vector<double> cost(B->cls.size(), 0.0);
+    for (size_t i = 0; i < B->cls.size(); ++i)
+      for (int b = 0; b < n; ++b)
+        if (B->m[b].ig == B->cls[i].ig && dim_class(B->m[b].ig, B->m[b].d) == B->cls[i].maxd)
+          cost[i] += (double)B->m[b].n_tiles * tile_cost(B->m[b].ig, B->m[b].d);
+    for (size_t i = 0; i < B->cls.size(); ++i) B->launch_order.push_back((int)i);
+    std::stable_sort(B->launch_order.begin(), B->launch_order.end(),
+                     [&](int p, int q) { return cost[p] > cost[q]; });
+    if (B->cls.size() > 1 &&
+        cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess)
+      st = VEGAS_ECUDA;
+    for (size_t i = 1; i < B->cls.size() && !st; ++i) {
+      cudaStream_t sd = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking) != cudaSuccess) {
+        st = VEGAS_ECUDA;
+        break;
+      }
+      B->side.push_back(sd);
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        st = VEGAS_ECUDA;
+        break;
+      }
+      B->join.push_back(ev);
+    }
+    if (st) cudaGetLastError();
+  }
   if (!st) {
     B->reduce_smem = gv::reduce_smem_bytes(nbins);
     st = ensure_per_iter(B, 16);
@@ -472,6 +525,9 @@ void vegas_batch_free(vegas_batch* B) {
   cudaFree(B->per_iter);
   cudaFree(B->dmem);
   if (B->pinned) cudaFreeHost(B->pinned);
+  for (cudaStream_t sd : B->side) cudaStreamDestroy(sd);
+  for (cudaEvent_t ev : B->join) cudaEventDestroy(ev);
+  if (B->fork) cudaEventDestroy(B->fork);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
 }
