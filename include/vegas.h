@@ -71,8 +71,10 @@ extern "C" {
 #define VEGAS_OPT_PRECISION 1 /* 0 = FP64 integrand (default), 1 = FP32 integrand; the sums are
                                  exact integer sums in both forms */
 #define VEGAS_OPT_ADAPT 2     /* 1 = refine the grid after every iteration (default), 0 = frozen */
-#define VEGAS_OPT_EPT 3       /* events per thread of the fill kernel: 0 = autotuned, or 1, 2, 4, 8
-                                 (8 only for ndim <= 8: VEGAS_EINVAL above) */
+#define VEGAS_OPT_EPT 3       /* events per thread of the fill kernel: 0 = autotuned (trial
+                                 launches per shape; 4 unless another candidate is more than 2%
+                                 faster), or 1, 2, 4, 8 (8 only for ndim <= 8: VEGAS_EINVAL
+                                 above).  Results do not depend on it. */
 #define VEGAS_OPT_NONFINITE 4 /* 0 = return VEGAS_ENONFINITE if any weight is not finite (default),
                                  1 = set such weights to 0 and count them silently */
 #define VEGAS_OPT_GRAPH 5     /* 1 = replay the iterations as one CUDA graph (default), 0 = plain launches */
