@@ -46,7 +46,7 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FILL_TRAFFIC_BYTES = 80_384
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "26858c08c290ecf4b577f819b94196a544c8608053137d0cb4e4bc856d49032f"
+FILL_SOURCES_SHA256 = "d2aaa5757c0a219f965c90d1e96b5eb96b1d1b014057b79110c2cda22077ca3c"
 
 
 def _fill_traffic():

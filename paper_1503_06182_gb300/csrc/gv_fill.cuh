@@ -7,9 +7,12 @@
 //           -> g(x) -> w = J g (J in FP64 in the FP64 form; FP32 mantissas
 //           with an integer exponent in the FP32 form); the bins stay in registers
 //           (d <= 4) or go to shared memory;
-//   tile scale: block max of |w| (order-free) -> E_t;
+//   tile scale: block max of |w| (order-free) -> E_t (in the FP32 form a
+//           32-bit max of exponents: each weight is kept as its FP32 product
+//           and Jacobian exponent, a 24-bit significand times a power of two);
 //   pass 2: w and the exact square w^2 rounded once to fixed point at the tile
-//           scale; sums in 128-bit integer registers (warp shuffle + block
+//           scale (FP32 form: from the 24-bit significand, gv_direct*);
+//           sums in 128-bit integer registers (warp shuffle + block
 //           reduction); per-bin sums of w^2, each bin with its own exponent F
 //           (an order-free shared atomicMax in pass 1), w^2 rounded once to
 //           2^(2F - 56) and added as three 22-bit limbs with 32-bit shared
