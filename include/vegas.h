@@ -193,18 +193,24 @@ int vegas_eval_events(vegas_ctx* ctx, int integrand_id, const double* params, in
 int vegas_rng_words(uint64_t seed, uint32_t iteration, uint32_t batch, int64_t first_event,
                     int64_t n, int ndim, uint32_t* out);
 
-/* No-allocation variant of vegas_rng_words (the paper has no counterpart:
- * it is for callers that cannot allocate device memory, e.g. while another
- * thread captures a CUDA graph in global mode, or when a caching allocator
- * holds the device's memory).  Same arguments, same words, but written
- * through a fixed buffer of VEGAS_NOALLOC_MAX_WORDS uint32 words (1 MiB)
- * inside the library; out is host memory owned by the caller.
- * n * ndim > VEGAS_NOALLOC_MAX_WORDS: VEGAS_EINVAL, nothing launched.
- * The first call on a device looks up the buffer's device address (a call
- * with n = 0 does only that); make it before any stream capture begins.
- * The buffer is shared by every caller on a device: calls that overlap on
- * one device race on it, so the caller must serialise them.  Nothing in the
- * buffer has to start at zero.  Blocking; runs on the legacy default stream. */
+/* No-allocation variant of vegas_rng_words (the paper has no counterpart).
+ * For callers that cannot allocate device memory: a process whose device
+ * memory a caching allocator holds (cudaMalloc from another library then
+ * fails although the cache has room), or latency-critical code that cannot
+ * take the device-wide synchronisation of cudaFree.  Same arguments, same
+ * words, but written through a fixed buffer of VEGAS_NOALLOC_MAX_WORDS uint32
+ * words (1 MiB) in the library's device image, held by every GPU that loads
+ * the library until the process exits; out is host memory owned by the
+ * caller.  n * ndim > VEGAS_NOALLOC_MAX_WORDS: VEGAS_EINVAL, nothing launched.
+ * The first call on a device, with that device current, does the set-up: it
+ * looks up the buffer's device address and loads the kernel (a call with
+ * n = 0 does only that); make it before any stream capture begins.  The
+ * address is kept for the life of the process: calls must not cross a
+ * cudaDeviceReset (or any release of the device's primary context).  The
+ * buffer is shared by every call on a device and keeps the last call's
+ * words: calls that overlap on one device race on it, so the caller must
+ * serialise them.  Nothing in the buffer has to start at zero.  Blocking;
+ * runs on the legacy default stream.  VEGAS_ECUDA: a CUDA call failed. */
 #define VEGAS_NOALLOC_MAX_WORDS (1 << 18)
 int vegas_rng_words_noalloc(uint64_t seed, uint32_t iteration, uint32_t batch,
                             int64_t first_event, int64_t n, int ndim, uint32_t* out);

@@ -44,6 +44,11 @@ cudaError_t launch_fill_ee3j_eval(int fp32, const GvFillArgs& a, uint32_t it, co
                                   long long n, double* w, int* bins, cudaStream_t s);
 cudaError_t launch_fill_dynlo_eval(int fp32, const GvFillArgs& a, uint32_t it, const long long* ev,
                                   long long n, double* w, int* bins, cudaStream_t s);
+// The last CUDA error behind a VEGAS_ECUDA status, per host thread.
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
 }  // namespace gv
 
 namespace {
@@ -57,10 +62,7 @@ namespace {
     }                                  \
   } while (0)
 
-cudaError_t& gv_last_cuda_error() {
-  static thread_local cudaError_t e = cudaSuccess;
-  return e;
-}
+cudaError_t& gv_last_cuda_error() { return gv::last_cuda_error(); }
 
 cudaError_t launch_fill_any(int ig, int fp32, int ept, const GvFillArgs& a, int n_tiles,
                             size_t smem, cudaStream_t s, bool pdl) {

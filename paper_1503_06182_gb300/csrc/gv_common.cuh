@@ -499,4 +499,6 @@ cudaError_t launch_grid_pack(int d, int N, double* grid, cudaStream_t s);
 cudaError_t launch_rng_words(unsigned long long seed, uint32_t it, uint32_t batch,
                              unsigned long long ev0, long long n, int d, uint32_t* out,
                              cudaStream_t s);
+// The CUDA error behind the last VEGAS_ECUDA status of this host thread.
+cudaError_t& last_cuda_error();
 }  // namespace gv

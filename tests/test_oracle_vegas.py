@@ -92,6 +92,43 @@ def test_refine_equal_share_property(oracle_mod):
         assert abs(m - share) < 1e-12 * r.sum()
 
 
+def test_refine_two_bins_hand_value(oracle_mod):
+    """N = 2, worked by hand: both bins smooth to (d_0 + d_1)/2, so rho = 1/2
+    for each, both compress to the same r, and the one inner edge sits where
+    the cumulative mass reaches R/2 = r: at the end of old bin 0, i.e. the
+    old edge.  Any sums, any edge: the grid is unchanged (a different end
+    rule of the smoothing would move it)."""
+    for e1, d in ((0.3, (5.0, 1.0)), (0.9, (1e-30, 7.0)), (0.125, (2.0, 0.0))):
+        e = np.array([[0.0, e1, 1.0]])
+        for alpha in (0.5, 1.0, 1.5):
+            assert np.array_equal(oracle_mod.refine(np.array([d]), e, alpha), e)
+
+
+def test_refine_three_bins_hand_values(oracle_mod):
+    """N = 3, worked by hand (values to 16 digits from the closed forms).
+
+    (a) d = (0, 0, 6), edges (0, 1/2, 3/4, 1), alpha = 1:
+        smoothed (d0+d1)/2, (d0+d1+d2)/3, (d1+d2)/2 = (0, 2, 3), total 5,
+        rho = (0, 2/5, 3/5), r = (0, (3/5)/ln(5/2), (2/5)/ln(5/3))
+          = (0, 0.6548140007623749, 0.7830460755884871),
+        R/3 = 0.4792866921169540.
+        Edge 1: bin 0 holds nothing, bin 1 holds r_1 > R/3, so
+          e'_1 = 1/2 + (R/3)/r_1 * (3/4 - 1/2) = 0.6829858141239111.
+        Edge 2: 2R/3 > r_1, so it lies in bin 2:
+          e'_2 = 3/4 + (2R/3 - r_1)/r_2 * (1 - 3/4) = 0.8469800478353867.
+    (b) d = (0, 6, 0), uniform edges, alpha = 3/2:
+        smoothed (3, 2, 3), total 8, rho = (3/8, 1/4, 3/8),
+        r_0 = r_2 = ((5/8)/ln(8/3))^(3/2) = 0.5086627218742808,
+        r_1 = ((3/4)/ln 4)^(3/2) = 0.3979318583048829,
+        R/3 = 0.4717524340178148 < r_0, so
+          e'_1 = (R/3)/r_0 * (1/3) = 0.3091455390319268, and by symmetry
+          e'_2 = 1 - e'_1 = 0.6908544609680732."""
+    a = oracle_mod.refine(np.array([[0.0, 0.0, 6.0]]), np.array([[0.0, 0.5, 0.75, 1.0]]), 1.0)
+    assert np.max(np.abs(a - [[0.0, 0.6829858141239111, 0.8469800478353867, 1.0]])) < 2e-16
+    b = oracle_mod.refine(np.array([[0.0, 6.0, 0.0]]), oracle_mod.uniform_edges(1, 3), 1.5)
+    assert np.max(np.abs(b - [[0.0, 0.3091455390319268, 0.6908544609680732, 1.0]])) < 2e-16
+
+
 def test_refine_concentrates_bins_on_peak(oracle_mod):
     d = np.zeros((1, 20))
     d[0, 9] = 1.0
