@@ -283,6 +283,7 @@ int ensure_pinned(vegas_ctx* c, size_t need) {
 struct Plan {
   int ig, fp32, mode, itmx, n_tiles, nacc, nch, ept, reduce_ctas, tiles_per_cta;
   int nhist;  // histogram bins with underflow and overflow (0: none)
+  int slot_major;  // slot-major partials and the single-level reduce (forward stages)
   int plus, s;     // VEGAS+: strata per axis
   long long nh;    // hypercubes
   long long cap;   // events the fill's grid can hold
@@ -311,6 +312,8 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   a.st = c->st;
   a.part = p.part;
   a.tileE = p.tileE;
+  a.slot_major = p.slot_major;
+  a.n_tiles = p.n_tiles;
   a.nhist = p.nhist;
   if (p.nhist) {
     const double invw = (double)c->hist_nh / (c->hist_hi - c->hist_lo);
@@ -576,6 +579,7 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   if (nt > 0x7fffffff) return VEGAS_EINVAL;
   p.n_tiles = (int)nt;
   p.nch = mode ? GV_MAXCH : 1;
+  p.slot_major = mode == 0 ? 1 : 0;
   p.nhist = (mode == 0 && c->hist_nh > 0) ? c->hist_nh + 2 : 0;
   p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins + 2 * p.nhist;
   p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist,
@@ -665,7 +669,10 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
-    GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
+    if (p.slot_major)
+      GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl));
+    else
+      GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
     if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
     if (p.plus) {
       // the hypercubes' statistics (sigma_k, the stage's combination), then

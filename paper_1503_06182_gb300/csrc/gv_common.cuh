@@ -111,8 +111,11 @@ struct GvFillArgs {
   const double* kconst;          // derived integrand constants
   const double* grid;            // grid pack
   GvState* st;
-  ulonglong2* part;              // [tile][nacc] 128-bit two's complement sums
+  ulonglong2* part;              // 128-bit two's complement sums: slot k of tile t at
+                                 // part[t nacc + k] (tile-major) or part[k n_tiles + t]
+                                 // (slot_major, read by the single-level reduce)
   int* tileE;                    // [tile][nch] scales
+  int slot_major = 0, n_tiles = 0;
   // histogram of the integrand's observable (forward fill only): nhist bins,
   // 0 = underflow, nhist - 1 = overflow (nhist = 0: no histogram); the bin of
   // a value v >= lo is 1 + trunc((v - lo) invw), in the integrand's precision
@@ -488,6 +491,8 @@ cudaError_t launch_fill_adjoint(int fp32, int ept, const GvFillArgs& a, int n_ti
 void reduce_grid(int n_tiles, int nacc, int* tiles_per_cta, int* gx, int* gy);
 size_t reduce_smem_bytes(int N);  // dynamic shared memory of the reduce kernels
 cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl);
+// the single-level reduce of slot-major partials (plain forward stages)
+cudaError_t launch_reduce_slots(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl);
 cudaError_t launch_hist(const GvHistArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_fill_hist(int ig, int fp32, const GvFillArgs& a, int n_tiles, size_t smem,
                              cudaStream_t s, bool pdl);

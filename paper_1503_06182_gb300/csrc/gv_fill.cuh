@@ -700,10 +700,12 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   const u128 t1 = gv_block_sum128<NW>(s1, red_128);
   const u128 t2 = gv_block_sum128<NW>(s2, red_128);
   gv_allow_next_grid();
-  ulonglong2* out = a.part + (size_t)tile * a.nacc;
+  // the tile's slots: slot k at out[k ks] (tile-major or slot-major partials)
+  const size_t ks = a.slot_major ? (size_t)a.n_tiles : (size_t)1;
+  ulonglong2* out = a.part + (a.slot_major ? (size_t)tile : (size_t)tile * a.nacc);
   if (tid == 0) {
     out[0] = make_ulonglong2(t1.lo, t1.hi);
-    out[1] = make_ulonglong2(t2.lo, t2.hi);
+    out[ks] = make_ulonglong2(t2.lo, t2.hi);
     a.tileE[tile] = E;
   }
   if (nbad) atomicAdd(&a.st->nonfinite_iter, nbad);
@@ -714,7 +716,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     u128 v = {l0, 0ull};
     v = add128(v, u128{l1 << 22, l1 >> 42});
     v = add128(v, u128{l2 << 44, l2 >> 20});
-    out[2 + k] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)ebin[k] << 32));
+    out[(2 + k) * ks] = make_ulonglong2(v.lo, v.hi | ((unsigned long long)(unsigned)ebin[k] << 32));
   }
   if constexpr (HIST) {
     for (int k = tid; k < hb; k += B) {
@@ -724,7 +726,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       u128 v = {l0, 0ull};
       v = add128(v, u128{l1 << 22, l1 >> 42});
       v = add128(v, u128{l2 << 44, l2 >> 20});
-      out[2 + dN + k] = make_ulonglong2(v.lo, v.hi | eh);
+      out[(2 + dN + k) * ks] = make_ulonglong2(v.lo, v.hi | eh);
       // w: M = m0 + m1 2^22 + m2 2^44 with m2 signed (|M| < 2^67) as a 96-bit
       // two's complement value in units of 2^(F_tb - GV_BIN_QBITS)
       const unsigned long long m0 = hh[3 * hb + k], m1 = hh[4 * hb + k];
@@ -732,7 +734,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       u128 t = {m0, 0ull};
       t = add128(t, u128{m1 << 22, m1 >> 42});
       t = add128(t, u128{(unsigned long long)m2 << 44, (unsigned long long)(m2 >> 20)});
-      out[2 + dN + hb + k] = make_ulonglong2(t.lo, (t.hi & 0xFFFFFFFFull) | eh);
+      out[(2 + dN + hb + k) * ks] = make_ulonglong2(t.lo, (t.hi & 0xFFFFFFFFull) | eh);
     }
   }
 }
@@ -774,8 +776,9 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, 
     // tile past this iteration's last event only leaves an empty partial
     const long long t0 = (long long)blockIdx.x * GV_TILE;
     if (t0 >= *a.plus->ncall) {
-      ulonglong2* out = a.part + (size_t)blockIdx.x * a.nacc;
-      for (int k = threadIdx.x; k < a.nacc; k += B) out[k] = make_ulonglong2(0ull, 0ull);
+      const size_t ks = a.slot_major ? (size_t)a.n_tiles : (size_t)1;
+      ulonglong2* out = a.part + (a.slot_major ? (size_t)blockIdx.x : (size_t)blockIdx.x * a.nacc);
+      for (int k = threadIdx.x; k < a.nacc; k += B) out[k * ks] = make_ulonglong2(0ull, 0ull);
       if (threadIdx.x == 0) a.tileE[blockIdx.x] = GV_EMPTY;
       return;
     }

@@ -612,6 +612,146 @@ __global__ void __launch_bounds__(256) gv_reduce_kernel(const GvReduceArgs a) {
                  s_won, sm);
 }
 
+// ---------------------------------------------------------------------------
+// Single-level reduce of a plain forward iteration (also with a histogram or
+// VEGAS+), for slot-major partials (slot k of tile t at part[k n_tiles + t]).
+// A group of GT threads (GT/32 warps; 256/GT groups per CTA) owns one slot and
+// reads it over every tile: the slot's largest exponent (group max), then the
+// partials aligned to it and added in 192-bit integers (group sum), rounded
+// once to FP64.  The alignment depends on the data alone, so the sums do not
+// depend on any launch shape.  Compared with the two-level reduce there is no
+// published per-range sum and no ticket between the levels: one L2 round trip
+// for the partials, then one fence and one ticket per slot.
+// Tickets: the group that completes the channel slots has its CTA finalise
+// the iteration; the group whose bin completes an axis has its CTA refine the
+// axis.  No CTA waits for another.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u192 warp_sum192(u192 v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    const u192 o = {shfl_xor_u64(v.l0, m), shfl_xor_u64(v.l1, m), shfl_xor_u64(v.l2, m)};
+    add192(v, o);
+  }
+  return v;
+}
+
+template <int GT>
+__global__ void __launch_bounds__(256) gv_reduce_slots_kernel(const GvReduceArgs a) {
+  constexpr int NG = 256 / GT;  // slots per CTA
+  constexpr int WPG = GT / 32;  // warps per slot
+  constexpr int G = GV_RED_TILES_PER_LOAD;
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int s_emax[8];
+  __shared__ u192 s_sum[8];
+  __shared__ int s_won[NG], s_nwon, s_fin;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int grp = tid / GT, u = tid - grp * GT;
+  const int k = blockIdx.x * NG + grp;
+  const bool live = k < a.nacc;
+  const bool bin = a.has_bins && k >= 2 * a.nch;
+  // the histogram's sums of w: the last nhist slots
+  const bool hw = bin && a.nhist > 0 && k >= a.nacc - a.nhist;
+  const int pw = hw ? 1 : (bin ? 2 : (k & 1) + 1);
+  const int empty = bin ? 0 : GV_EMPTY;
+  const int ch = k >> 1;
+  const int nt = a.n_tiles;
+  const ulonglong2* src = a.part + (size_t)k * nt;
+  if (tid == 0) {
+    s_nwon = 0;
+    s_fin = 0;
+  }
+  gv_wait_prior_grid();
+  __syncthreads();
+  // the slot's largest exponent over all tiles
+  const bool cached = nt <= G * GT;  // every partial of a thread fits in registers
+  ulonglong2 v[G];
+  int et[G];
+  int em = empty;
+  if (live) {
+    if (cached) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int t = u + g * GT;
+        v[g] = make_ulonglong2(0ull, 0ull);
+        et[g] = empty;
+        if (t < nt) {
+          v[g] = __ldcg(src + t);
+          et[g] = bin ? (int)(v[g].y >> 32) : __ldcg(a.tileE + (size_t)t * a.nch + ch);
+        }
+        em = max(em, et[g]);
+      }
+    } else {
+      for (int t = u; t < nt; t += GT)
+        em = max(em, bin ? (int)(__ldcg(src + t).y >> 32)
+                         : __ldcg(a.tileE + (size_t)t * a.nch + ch));
+    }
+  }
+  em = __reduce_max_sync(0xffffffffu, em);
+  if constexpr (WPG > 1) {
+    if (lane == 0) s_emax[wid] = em;
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < WPG; ++w) em = max(em, s_emax[grp * WPG + w]);
+  }
+  // the partials aligned to it, summed
+  u192 r = {0ull, 0ull, 0ull};
+  if (live && em != empty) {
+    if (cached) {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (et[g] != empty && (v[g].x | v[g].y)) add192(r, align_tile(v[g], et[g], em, bin, pw, hw));
+    } else {
+      for (int t = u; t < nt; t += GT) {
+        const ulonglong2 x = __ldcg(src + t);
+        const int e = bin ? (int)(x.y >> 32) : __ldcg(a.tileE + (size_t)t * a.nch + ch);
+        if (e != empty && (x.x | x.y)) add192(r, align_tile(x, e, em, bin, pw, hw));
+      }
+    }
+  }
+  r = warp_sum192(r);
+  if constexpr (WPG > 1) {
+    if (lane == 0) s_sum[wid] = r;
+    __syncthreads();
+    if (u == 0)
+#pragma unroll
+      for (int w = 1; w < WPG; ++w) add192(r, s_sum[grp * WPG + w]);
+  }
+  if (u == 0 && live) {
+    // the slot's sum over all events, rounded once to FP64
+    a.sums[k] = em == empty ? 0.0
+                            : u192_to_double(r, bin ? pw * (em - GV_BINE_OFF) - GV_BIN_FB
+                                                    : pw * em - GV_FB);
+    __threadfence();
+    if (k < 2 * a.nch) {
+      int* tk = a.tickets + gv_ticket_done(a.nacc);
+      if (atomicAdd(tk, 1) == 2 * a.nch - 1) {
+        *tk = 0;
+        s_fin = 1;
+      }
+    } else if (a.has_bins && a.refine_follows && k < 2 * a.nch + a.ndim * a.nbins) {
+      const int ax = (k - 2 * a.nch) / a.nbins;
+      int* tk = a.tickets + gv_ticket_axis(a.nacc, ax);
+      if (atomicAdd(tk, 1) == a.nbins - 1) {
+        *tk = 0;
+        s_won[atomicAdd(&s_nwon, 1)] = ax;
+      }
+    }
+  }
+  __syncthreads();
+  const int n_won = s_nwon, fin = s_fin;
+  if (n_won == 0 && !fin) return;
+  __threadfence();  // the other slots' sums, published before their tickets
+  gv_allow_next_grid();  // what is left is short: the next fill's CTAs may come in
+  // the finalisation on warp 7 (all warps if no axis was won), the won axes
+  // one after the other on the other warps
+  if (fin && (n_won == 0 || wid == 7)) {
+    const int nw = n_won == 0 ? 8 : 1, w0 = 8 - nw;
+    finalize_iteration(a, tid - 32 * w0, 32 * nw, 1);
+  } else if (n_won > 0) {
+    for (int i = 0; i < n_won; ++i) refine_axis(a, s_won[i], sm, tid, fin ? 224 : 256, 2, 0);
+  }
+}
+
 // Batched: one launch reduces many integrations; task i names the
 // integration and the block coordinates of CTA i.
 __global__ void __launch_bounds__(256) gv_reduce_batch_kernel(const GvReduceArgs* args,
@@ -823,6 +963,33 @@ cudaError_t launch_reduce(const GvReduceArgs& a, size_t smem, cudaStream_t s, bo
   cudaError_t e = allow_smem((const void*)gv_reduce_kernel, smem);
   if (e != cudaSuccess) return e;
   return gv_launch(gv_reduce_kernel, dim3(gx, gy), dim3(256), smem, s, pdl, a);
+}
+
+// Threads per slot of the single-level reduce: up to 4 tiles per thread
+// where that takes at most 256 threads, else 256.
+int reduce_slots_threads(int n_tiles) {
+  return n_tiles <= 128 ? 32 : (n_tiles <= 256 ? 64 : (n_tiles <= 512 ? 128 : 256));
+}
+
+cudaError_t launch_reduce_slots(const GvReduceArgs& a, size_t smem, cudaStream_t s, bool pdl) {
+  const int gt = reduce_slots_threads(a.n_tiles);
+  const int ng = 256 / gt;
+  const dim3 grid((a.nacc + ng - 1) / ng);
+  cudaError_t e = cudaSuccess;
+  switch (gt) {
+    case 32:
+      e = allow_smem((const void*)gv_reduce_slots_kernel<32>, smem);
+      return e ? e : gv_launch(gv_reduce_slots_kernel<32>, grid, dim3(256), smem, s, pdl, a);
+    case 64:
+      e = allow_smem((const void*)gv_reduce_slots_kernel<64>, smem);
+      return e ? e : gv_launch(gv_reduce_slots_kernel<64>, grid, dim3(256), smem, s, pdl, a);
+    case 128:
+      e = allow_smem((const void*)gv_reduce_slots_kernel<128>, smem);
+      return e ? e : gv_launch(gv_reduce_slots_kernel<128>, grid, dim3(256), smem, s, pdl, a);
+    default:
+      e = allow_smem((const void*)gv_reduce_slots_kernel<256>, smem);
+      return e ? e : gv_launch(gv_reduce_slots_kernel<256>, grid, dim3(256), smem, s, pdl, a);
+  }
 }
 
 cudaError_t launch_reduce_batch(const GvReduceArgs* args, const int4* tasks, int ntasks, int k,
