@@ -259,25 +259,61 @@ __device__ __forceinline__ void pack_axis_tables(double* grid, const double* e_s
   }
 }
 
+// 1/x and 1/sqrt(x) for positive normal x: the hardware approximations
+// (PTX rcp.approx.ftz.f64 and rsqrt.approx.ftz.f64, about 20 correct bits)
+// refined by two Newton-Raphson steps, y <- y + y (1 - x y) and
+// z <- z + z (1 - x z^2) / 2, each of which squares the relative error.
+// Measured against the correctly rounded results over six decades: the
+// reciprocal agrees bit for bit, the square root within 2.7e-16.  They
+// replace the library's correctly rounded routines, whose special-case
+// handling costs this chip's scarce FP64 pipe more instructions.
+__device__ __forceinline__ double gv_rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double gv_rsqrt_nr(double x) {
+  double z;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(z) : "d"(x));
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const double h = x * z;
+    const double e = fma(-h, z, 1.0);
+    z = fma(0.5 * z, e, z);
+  }
+  return z;
+}
+
 // ((1 - rho)/(-ln rho))^alpha for 0 < rho < 1, with the common exponents
-// evaluated by roots rather than pow.
+// evaluated by reciprocals and roots rather than pow.  In the refinement
+// rho <= 3/5 (a smoothed bin holds at most 3/5 of the smoothed total), so
+// 1 - rho >= 2/5 and -ln rho >= 0.51: both are positive normal numbers.
 __device__ __forceinline__ double compress(double rho, double alpha) {
   if (rho <= 0.0) return 0.0;
   if (rho >= 1.0) return 1.0;
   const double L = -gv_log_pos(rho);
   const double om = 1.0 - rho;
-  if (alpha == 1.5) {
-    const double y = rsqrt(L);
-    return om * sqrt(om) * (y * y * y);
+  if (alpha == 1.5) {  // om^(3/2) L^(-3/2) = (om^2 / sqrt(om)) (1/sqrt(L))^3
+    const double y = gv_rsqrt_nr(L), z = gv_rsqrt_nr(om);
+    return (om * om * z) * (y * y * y);
   }
-  if (alpha == 1.0) return om * __drcp_rn(L);
-  if (alpha == 0.5) return sqrt(om) * rsqrt(L);
+  if (alpha == 1.0) return om * gv_rcp_nr(L);
+  if (alpha == 0.5) return om * gv_rsqrt_nr(om) * gv_rsqrt_nr(L);
   if (alpha == 2.0) {
-    const double q = om * __drcp_rn(L);
+    const double q = om * gv_rcp_nr(L);
     return q * q;
   }
   if (alpha == 0.0) return 1.0;
   return pow(om * __drcp_rn(L), alpha);
+}
+
+// alpha values whose compressed values are at least (1/745)^2 > 1e-6 (the
+// reciprocal approximation then sees normal numbers only)
+__device__ __forceinline__ bool fast_alpha(double alpha) {
+  return alpha == 1.5 || alpha == 1.0 || alpha == 0.5 || alpha == 2.0 || alpha == 0.0;
 }
 
 // Shared memory of refine_axis: r[N], slope[N], C[N+1], e[N+1], ne[N+1].
@@ -301,7 +337,7 @@ __host__ __device__ inline size_t refine_axis_smem(int N) {
 __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, double* sm, int tid, int nthr, int bar,
                             int q) {
   const int N = a.nbins, lane = tid & 31, wid = tid >> 5;
-  __shared__ double s_inv[8], s_step[8];
+  __shared__ double s_inv[8], s_step[8], s_tree[8][32];
   double* r = sm;             // [N] 6 x smoothed sums, then compressed values
   double* slope = r + N;      // [N] bin sums, then slopes
   double* C = slope + N;      // [N+1]
@@ -319,24 +355,32 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
   gv_bar(bar, nthr);
   if (wid == 0) {
     // the total in an order fixed by N alone (whatever the group's size):
-    // 32 consecutive chunks in order, then a fixed butterfly
+    // 32 consecutive chunks in order, then a fixed pairwise tree in shared
+    // memory (shuffles of doubles cost more here)
     const int chunk = (N + 31) / 32;
     const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
     double part = 0.0;
     for (int i = i0; i < i1; ++i) part += r[i];
+    double* tr = s_tree[q];
+    tr[lane] = part;
+    __syncwarp();
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) part += __shfl_xor_sync(0xffffffffu, part, m);
-    if (lane == 0) s_inv[q] = part > 0.0 ? __drcp_rn(part) : 0.0;
+    for (int m = 16; m > 0; m >>= 1) {
+      if (lane < m) tr[lane] = tr[lane] + tr[lane + m];
+      __syncwarp();
+    }
+    if (lane == 0) s_inv[q] = tr[0] > 0.0 ? __drcp_rn(tr[0]) : 0.0;
   }
   gv_bar(bar, nthr);
   const double inv = s_inv[q];
+  const bool fast = fast_alpha(a.alpha);
   if (inv > 0.0) {
     for (int i = tid; i < N; i += nthr) {
       double rv = 0.0, sl = 0.0;
       const double s6 = r[i];
       if (s6 > 0.0) {
         rv = compress(s6 * inv, a.alpha);
-        if (rv > 0.0) sl = (e[i + 1] - e[i]) * __drcp_rn(rv);
+        if (rv > 0.0) sl = (e[i + 1] - e[i]) * (fast ? gv_rcp_nr(rv) : __drcp_rn(rv));
       }
       r[i] = rv;
       slope[i] = sl;
@@ -347,13 +391,19 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
       const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
       double local = 0.0;
       for (int i = i0; i < i1; ++i) local += r[i];
-      double incl = local;
+      // inclusive prefix sums of the 32 chunk sums (Hillis-Steele in shared
+      // memory), then each chunk's exclusive prefix
+      double* tr = s_tree[q];
+      tr[lane] = local;
+      __syncwarp();
 #pragma unroll
       for (int m = 1; m < 32; m <<= 1) {
-        const double o = __shfl_up_sync(0xffffffffu, incl, m);
-        if (lane >= m) incl += o;
+        const double v = lane >= m ? tr[lane] + tr[lane - m] : tr[lane];
+        __syncwarp();
+        tr[lane] = v;
+        __syncwarp();
       }
-      double run = incl - local;  // exclusive prefix of this lane's chunk
+      double run = lane > 0 ? tr[lane - 1] : 0.0;  // exclusive prefix of this lane's chunk
       if (lane == 0) C[0] = 0.0;
       for (int i = i0; i < i1; ++i) {
         run += r[i];
