@@ -33,11 +33,28 @@ METRIC = "VEGAS events/s (LO Drell-Yan, d=4, 100 bins, 10 iterations x 1e6 calls
 WORKLOAD = "drell_yan_lo_14tev_d4_n100_10x1e6calls"
 UNIT = "events/s"
 L2_FLUSH_BYTES = 256 << 20
-# FP32 floating-point operations per event of the FP32 Drell-Yan fill, counted
-# from the source: grid map 4 x (fma + fma) = 16; integrand 83 arithmetic
-# operations (fma counted as 2) + 8 transcendental calls (3 exp, 4 log, 1 sqrt)
-# counted as 1 each + 3 divisions counted as 1 each.
+# FP32 floating-point operations per event of the FP32 fills, counted from the
+# source (gv_integrands.cuh, gv_fill.cuh): an fma counts 2, an add, multiply,
+# division, square root or transcendental call (exp, log, sincos counted as
+# 2) counts 1; integer work (Philox, bins, exact sums) is not counted.
+#   Drell-Yan, d=4: grid map 4 x (fma + fma) = 16, integrand 83 arithmetic
+#     operations + 8 transcendental calls + 3 divisions: 110.
+#   3-jet, d=5: grid map 20; the cut test 4; an event inside the cuts adds
+#     the momenta, the Euler rotation (18 + 45), the invariants and |M|^2:
+#     144 in all, 24 for a cut event.  The cuts keep (1 - 3 y_cut)^2 / 2 =
+#     0.4705 of the unit square, so 0.4705 x 144 + 0.5295 x 24 = 80.5.
+#   NLO-shaped, d=13: Drell-Yan 110 + 9 more axes of grid map (36) and of
+#     exp(beta cos 2 pi x)/I0 (8 each: 72) + 1 = 219.
+#   Drell-Yan adjoint: forward 110 + reverse sweep 72 + 5 channel weights = 187.
 FLOPS_PER_EVENT_FP32 = 16 + 83 + 8 + 3
+FLOPS_EE3J_FP32 = 0.4705 * 144 + 0.5295 * 24
+FLOPS_DYNLO_FP32 = 110 + 36 + 72 + 1
+FLOPS_ADJOINT_FP32 = 110 + 72 + 5
+# FP64 operations per event of the plain FP64 Drell-Yan fill (the same
+# convention, with the table-driven exp (21 operations) and log (25), the
+# library square root (15) and divisions (15 each) counted by their FP64
+# operations): 83 + 3 x 21 + 25 + 15 + 3 x 15 + grid map 4 x 5 = 251.
+FP64_OPS_PER_EVENT_DY = 83 + 3 * 21 + 25 + 15 + 3 * 15 + 4 * 5
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) of one fill launch of this workload, from the ncu
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
@@ -47,6 +64,9 @@ FILL_TRAFFIC_BYTES = 80_384
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
 FILL_SOURCES_SHA256 = "d2aaa5757c0a219f965c90d1e96b5eb96b1d1b014057b79110c2cda22077ca3c"
+# HBM copy bandwidth measured by the driver on the GB300s (used when
+# MEASURED_PEAKS.json is absent: the profiling recipe's fallback)
+HBM_FALLBACK_GBS = 6800.0
 
 
 def _fill_traffic():
@@ -62,9 +82,29 @@ def _fill_traffic():
     return FILL_TRAFFIC_BYTES if h.hexdigest() == FILL_SOURCES_SHA256 else None
 
 
-def _fp32_peak_tflops():
+def _fp32_peak_derived_tflops():
     """Dense FP32 peak from unit counts and the maximum SM clock."""
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def _hbm_peak():
+    """(GB/s, source) of the HBM copy peak."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def measure_peaks(v, ms=60.0):
+    """The arithmetic pipes' rates on this GPU now (vegas_pipe_peak probes):
+    FFMA and DFMA in TFLOP/s, IMAD and MUFU (ex2) in T ops/s."""
+    return {"ffma_tflops": v.vegas_pipe_peak(v.VEGAS_PIPE_FFMA, ms) / 1e12,
+            "dfma_tflops": v.vegas_pipe_peak(v.VEGAS_PIPE_DFMA, ms) / 1e12,
+            "imad_tops": v.vegas_pipe_peak(v.VEGAS_PIPE_IMAD, ms) / 1e12,
+            "mufu_ex2_tops": v.vegas_pipe_peak(v.VEGAS_PIPE_MUFU, ms) / 1e12,
+            "how": "vegas_pipe_peak: 8 independent chains per thread, 8 x 256-thread CTAs "
+                   "per SM, about 60 ms each, CUDA events, this run's clock"}
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -240,7 +280,17 @@ def run_gpu(args):
     v.vegas_set_option(g32.h, v.VEGAS_OPT_TIMING, 0)
     fill_avg = kavg[0]
     achieved = FLOPS_PER_EVENT_FP32 * NCALL / (fill_avg * 1e-3) / 1e12
-    peak = _fp32_peak_tflops()
+    peaks = measure_peaks(v)
+    peak = peaks["ffma_tflops"]
+    hbm, hbm_src = _hbm_peak()
+    # the reduce (one launch per iteration): algorithmic bytes = the tile
+    # partials and tile scales read, the FP64 sums written, the refined grid
+    # pack (edges, widths, Jacobian factors in FP64 and FP32) rewritten
+    n_tiles = (NCALL + 1023) // 1024
+    nacc = 2 + NDIM * NBINS
+    grid_pack = 8 * (3 * NDIM * NBINS + NDIM) + 4 * (4 * NDIM * NBINS + NDIM)
+    red_bytes = n_tiles * nacc * 16 + n_tiles * 4 + nacc * 8 + grid_pack
+    red_gbs = red_bytes / (kavg[1] * 1e-3) / 1e9
 
     # plain FP64 path and equal-error comparison: one 10-iteration stage of each
     # form from the same grid and seed (the same events)
@@ -250,6 +300,13 @@ def run_gpu(args):
     k64 = max(3, min(K, 10))
     ms64, _ = timed_steps(g64, k64)
     value64 = world * ITMX * NCALL / (sum(ms64) / k64 * 1e-3)
+    v.vegas_set_option(g64.h, v.VEGAS_OPT_TIMING, 1)
+    v.vegas_kernel_time(g64.h, v.VEGAS_KERNEL_FILL, reset=True)
+    g64.iterate(NCALL, ITMX, DY, DY_PARAMS)
+    ms, n = v.vegas_kernel_time(g64.h, v.VEGAS_KERNEL_FILL)
+    v.vegas_set_option(g64.h, v.VEGAS_OPT_TIMING, 0)
+    fill64 = ms / max(n, 1)
+    ach64 = FP64_OPS_PER_EVENT_DY * NCALL / (fill64 * 1e-3) / 1e12
     sig = {}
     for prec in ("fp32", "fp64"):
         g = v.Vegas(NDIM, NBINS, 4321, precision=prec)
@@ -265,7 +322,7 @@ def run_gpu(args):
     ept = v.vegas_get_ept(g32.h)
     g32.close()
     g64.close()
-    form_rates = {} if args.no_forms else forms(v, stream, seed)
+    form_rates = {} if args.no_forms else forms(v, stream, seed, peaks)
 
     clocks = sampler.summary(t_wall0 - 0.1, t_wall2 + 0.1) if sampler else None
     if sampler:
@@ -284,7 +341,8 @@ def run_gpu(args):
                    "ndim": NDIM, "nbins": NBINS, "ncall_per_iteration": NCALL,
                    "itmx_per_step": ITMX,
                    "step": "one vegas_iterate stage of 10 iterations x 1e6 calls",
-                   "precision": "fp32 integrand, fp64 Jacobian, exact integer sums",
+                   "precision": "fp32 integrand; Jacobian as fp32 mantissas times integer "
+                                "exponents; exact integer sums rounded once to fp64",
                    "seed": 1234, "events_per_thread": ept,
                    "l2": "flushed between steps (256 MiB device write)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -300,9 +358,22 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": _fill_traffic(),
                      "kernel": "gv_fill_kernel<drell_yan, float>",
                      "kernel_avg_ms": fill_avg, "reduce_refine_avg_ms": kavg[1],
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "flops_per_event": FLOPS_PER_EVENT_FP32},
-        "fp64_path": {"value": value64, "unit": UNIT},
+                     "peak_source": "measured in this run: FFMA probe (vegas_pipe_peak)",
+                     "peak_derived": _fp32_peak_derived_tflops(),
+                     "frac_of_derived": achieved / _fp32_peak_derived_tflops(),
+                     "flops_per_event": FLOPS_PER_EVENT_FP32,
+                     "reduce": {"kernel": "gv_reduce_slots_kernel (sums, refinement, record)",
+                                "bound": "latency", "algorithmic_bytes": red_bytes,
+                                "achieved_gbs": red_gbs, "peak_gbs": hbm,
+                                "peak_source": hbm_src, "frac": red_gbs / hbm}},
+        "peaks_measured": peaks,
+        "fp64_path": {"value": value64, "unit": UNIT,
+                      "roofline": {"bound": "fp64", "kernel": "gv_fill_kernel<drell_yan, double>",
+                                   "kernel_avg_ms": fill64, "fp64_ops_per_event":
+                                       FP64_OPS_PER_EVENT_DY, "achieved": ach64,
+                                   "peak": peaks["dfma_tflops"], "unit": "TFLOP/s",
+                                   "frac": ach64 / peaks["dfma_tflops"],
+                                   "peak_source": "measured in this run: DFMA probe"}},
         "forms": form_rates,
         "equal_error": {"sigma_fp32": sig["fp32"][1], "sigma_fp64": sig["fp64"][1],
                         "integral_fp32": sig["fp32"][0], "integral_fp64": sig["fp64"][0],
@@ -311,12 +382,14 @@ def run_gpu(args):
     }
     if cpu:
         out["cpu_baseline"] = cpu
+        if not args.no_forms:
+            out["cpu_baselines"] = cpu_baselines()
     print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def forms(v, stream, seed):
+def forms(v, stream, seed, peaks):
     """The other workloads, each a warm-up stage then one timed stage on the
     bench stream (device time between CUDA events; L2 not flushed inside a
     stage, as in a real run): 3-jet 10 x 1e7 FP32; Drell-Yan adjoint 10 x 1e8
@@ -324,11 +397,17 @@ def forms(v, stream, seed):
     the plain FP64 Gauss case 5 x 1e5; the NLO-shaped 13-axis case 10 x 1e6
     FP32; Drell-Yan 10 x 1e6 FP32 filling a 60-bin m_ll histogram; Drell-Yan
     10 x 1e6 FP32 with VEGAS+ stratification, with its integration efficiency
-    1/(sigma^2 t) against plain VEGAS on the same workload."""
+    1/(sigma^2 t) against plain VEGAS on the same workload.  Each FP32 form
+    also reports its fill kernel's FP32 roofline fraction (a separate stage
+    with per-kernel timing) and its difference from the FP64 form on the same
+    events (the FP64 path matches the oracle to 1e-12)."""
+    import numpy as np
     import torch
 
     from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, DYNLO, DYNLO_PARAMS, EE3J,
                                                   EE3J_PARAMS, GAUSS, GAUSS_PARAMS, batch_spec)
+
+    ffma = peaks["ffma_tflops"]
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -339,29 +418,73 @@ def forms(v, stream, seed):
         stream.synchronize()
         return a.elapsed_time(b), out
 
+    def fill_ms(g, fn):
+        """Average fill-kernel time of one more stage, with per-kernel events."""
+        v.vegas_set_option(g.h, v.VEGAS_OPT_TIMING, 1)
+        v.vegas_kernel_time(g.h, v.VEGAS_KERNEL_FILL, reset=True)
+        fn()
+        ms, n = v.vegas_kernel_time(g.h, v.VEGAS_KERNEL_FILL)
+        v.vegas_set_option(g.h, v.VEGAS_OPT_TIMING, 0)
+        return ms / max(n, 1)
+
+    def vs64(I, e, I64, e64):
+        return {"integral_fp64": I64, "error_fp64": e64,
+                "rel_diff_integral": abs(I - I64) / abs(I64),
+                "diff_in_sigma": abs(I - I64) / e64 if e64 > 0 else None,
+                "rel_diff_error": abs(e - e64) / e64 if e64 > 0 else None}
+
     res = {}
-    for name, (iid, params, d, n, ncall, itmx, prec, hist) in {
-            "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32", None),
-            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64", None),
+    for name, (iid, params, d, n, ncall, itmx, prec, hist, flops) in {
+            "ee3j_d5_n100_10x1e7_fp32": (EE3J, EE3J_PARAMS, 5, 100, 10_000_000, 10, "fp32", None,
+                                         FLOPS_EE3J_FP32),
+            "gauss_d4_n50_5x1e5_fp64": (GAUSS, GAUSS_PARAMS, 4, 50, 100_000, 5, "fp64", None,
+                                        None),
             "dy_nlo_shaped_d13_n50_10x1e6_fp32": (DYNLO, DYNLO_PARAMS, 13, 50, 1_000_000, 10,
-                                                  "fp32", None),
+                                                  "fp32", None, FLOPS_DYNLO_FP32),
             "dy_mll_hist60_d4_n100_10x1e6_fp32": (DY, DY_PARAMS, 4, 100, 1_000_000, 10, "fp32",
-                                                  (60, 60.0, 120.0))}.items():
-        g = v.Vegas(d, n, seed, precision=prec)
-        v.vegas_set_stream(g.h, stream.cuda_stream)
-        if hist:
-            g.hist_set(*hist)
-        try:
-            g.iterate(ncall, itmx, iid, params)  # warm-up stage (adapts, tunes, captures)
-            ms, (I, e, c, _, _) = timed(lambda: g.iterate(ncall, itmx, iid, params))
-        finally:
-            g.close()
-        res[name] = {"value": ncall * itmx / (ms * 1e-3), "unit": UNIT, "integral": I,
-                     "error": e, "chi2_dof": c}
+                                                  (60, 60.0, 120.0), FLOPS_PER_EVENT_FP32)}.items():
+        out = {}
+        edges = None
+        for p in ((prec, "fp64") if prec == "fp32" else (prec,)):
+            g = v.Vegas(d, n, seed, precision=p)
+            v.vegas_set_stream(g.h, stream.cuda_stream)
+            if hist:
+                g.hist_set(*hist)
+            try:
+                g.iterate(ncall, itmx, iid, params)  # warm-up stage (adapts, tunes, captures)
+                if edges is None:
+                    edges = g.grid
+                else:  # the FP64 form from the FP32 form's grid: the same events follow
+                    g.grid = edges
+                st = g.state()
+                ms, (I, e, c, _, _) = timed(lambda: g.iterate(ncall, itmx, iid, params))
+                hv = g.hist()[0] if hist else None
+                fm = None
+                if p == prec and flops:
+                    g.restore(st)
+                    fm = fill_ms(g, lambda: g.iterate(ncall, itmx, iid, params))
+            finally:
+                g.close()
+            out[p] = (ms, I, e, c, fm, hv)
+        ms, I, e, c, fm, hv = out[prec]
+        r = {"value": ncall * itmx / (ms * 1e-3), "unit": UNIT, "integral": I, "error": e,
+             "chi2_dof": c}
+        if fm:
+            ach = flops * ncall / (fm * 1e-3) / 1e12
+            r["fill_roofline"] = {"fill_avg_ms": fm, "flops_per_event": flops,
+                                  "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma}
+        if "fp64" in out and prec == "fp32":
+            r["fp32_vs_fp64"] = vs64(I, e, out["fp64"][1], out["fp64"][2])
+            if hist:
+                h32, h64 = hv, out["fp64"][5]
+                nz = h64 != 0
+                r["fp32_vs_fp64"]["hist_max_rel_diff_bin"] = float(
+                    np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
+        res[name] = r
     # VEGAS+ against plain VEGAS: the same workload, events/s and efficiency
     plus = {}
-    for strat in (0, 1):
-        g = v.Vegas(NDIM, NBINS, seed, precision="fp32")
+    for strat, prec in ((0, "fp32"), (1, "fp32"), (1, "fp64")):
+        g = v.Vegas(NDIM, NBINS, seed, precision=prec)
         v.vegas_set_stream(g.h, stream.cuda_stream)
         g.set(v.VEGAS_OPT_STRAT, strat)
         try:
@@ -369,41 +492,107 @@ def forms(v, stream, seed):
             ms, (I, e, c, _, _) = timed(lambda: g.iterate(NCALL, 10, DY, DY_PARAMS))
         finally:
             g.close()
-        plus[strat] = (ms, I, e, c)
-    ms, I, e, c = plus[1]
+        plus[(strat, prec)] = (ms, I, e, c)
+    ms, I, e, c = plus[(1, "fp32")]
+    p0 = plus[(0, "fp32")]
     res["dy_vegasplus_d4_n100_10x1e6_fp32"] = {
         "value": NCALL * 10 / (ms * 1e-3), "unit": UNIT, "integral": I, "error": e, "chi2_dof": c,
         "events_note": "target 1e6 calls per iteration; VEGAS+ runs up to 1e6 + 2 nh",
-        "error_plain_vegas": plus[0][2], "ms_plain_vegas": plus[0][0],
-        "efficiency_ratio_over_plain": (plus[0][2] ** 2 * plus[0][0]) / (e ** 2 * ms)}
+        "error_plain_vegas": p0[2], "ms_plain_vegas": p0[0],
+        "efficiency_ratio_over_plain": (p0[2] ** 2 * p0[0]) / (e ** 2 * ms),
+        "fp32_vs_fp64": vs64(I, e, plus[(1, "fp64")][1], plus[(1, "fp64")][2])}
     # gradient: frozen grid adapted by a forward warm-up, then the adjoint stage
-    g = v.Vegas(NDIM, NBINS, seed, precision="fp32")
-    v.vegas_set_stream(g.h, stream.cuda_stream)
-    try:
-        g.iterate(NCALL, 5, DY, DY_PARAMS)
-        g.set(v.VEGAS_OPT_ADAPT, 0)
-        # warm-up stage of the timed size: events per thread are tuned per size
-        g.adjoint(100_000_000, 10, DY_PARAMS)
-        ms, (grad, gerr, _, _, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
-    finally:
-        g.close()
-    res["dy_adjoint_d4_n100_10x1e8_fp32"] = {"value": 1e9 / (ms * 1e-3), "unit": UNIT,
-                                              "grad": list(grad), "grad_err": list(gerr)}
+    adj = {}
+    edges = None
+    for prec in ("fp32", "fp64"):
+        g = v.Vegas(NDIM, NBINS, seed, precision=prec)
+        v.vegas_set_stream(g.h, stream.cuda_stream)
+        try:
+            g.iterate(NCALL, 5, DY, DY_PARAMS)
+            if edges is None:
+                edges = g.grid
+            else:  # the FP64 gradient on the FP32 form's frozen grid: the same events
+                g.grid = edges
+            g.set(v.VEGAS_OPT_ADAPT, 0)
+            st = g.state()
+            # warm-up stage of the timed size: events per thread are tuned per size
+            g.adjoint(100_000_000, 10, DY_PARAMS)
+            g.restore(st)
+            ms, (grad, gerr, I, e, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
+            fm = None
+            if prec == "fp32":
+                g.restore(st)
+                fm = fill_ms(g, lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
+        finally:
+            g.close()
+        adj[prec] = (ms, np.asarray(grad), np.asarray(gerr), I, e, fm)
+    ms, grad, gerr, I, e, fm = adj["fp32"]
+    g64, ge64 = adj["fp64"][1], adj["fp64"][2]
+    ach = FLOPS_ADJOINT_FP32 * 1e8 / (fm * 1e-3) / 1e12
+    res["dy_adjoint_d4_n100_10x1e8_fp32"] = {
+        "value": 1e9 / (ms * 1e-3), "unit": UNIT, "grad": list(grad), "grad_err": list(gerr),
+        "fill_roofline": {"fill_avg_ms": fm, "flops_per_event": FLOPS_ADJOINT_FP32,
+                          "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma},
+        "fp32_vs_fp64": {"grad_fp64": list(g64), "max_diff_over_abs_plus_sigma":
+                         float(np.max(np.abs(grad - g64) / (np.abs(g64) + ge64))),
+                         "integral_rel_diff": abs(I - adj["fp64"][3]) / abs(adj["fp64"][3])}}
     # batched: 64 integrations of uneven dimension, calls and integrand
     spec = batch_spec(64, seed)
     members = [(m.ndim, m.ncall, m.integrand, m.params) for m in spec]
-    B = v.VegasBatch(members, NBINS, seed, precision="fp32")
-    v.vegas_batch_set_stream(B.h, stream.cuda_stream)
-    try:
-        B.iterate(1)  # tunes events per thread
-        B.iterate(10)  # captures the 10-iteration graph
-        ms, _ = timed(lambda: B.iterate(10))
-    finally:
-        B.close()
+    bat = {}
+    for prec in ("fp32", "fp64"):
+        B = v.VegasBatch(members, NBINS, seed, precision=prec)
+        v.vegas_batch_set_stream(B.h, stream.cuda_stream)
+        try:
+            B.iterate(1)  # tunes events per thread
+            B.iterate(10)  # captures the 10-iteration graph
+            ms, out = timed(lambda: B.iterate(10))
+        finally:
+            B.close()
+        bat[prec] = (ms, out)
     tot = sum(m.ncall for m in spec) * 10
-    res["batch64_10it_fp32"] = {"value": tot / (ms * 1e-3), "unit": UNIT,
-                                "events_per_iteration": tot // 10}
+    (ms, o32), o64 = bat["fp32"], bat["fp64"][1]
+    # events-weighted FP32 flops of the members' integrands (the Gaussian:
+    # grid map 4 d + d (sub, fma) + exp and scale 3)
+    fl = {GAUSS: lambda d: 4 * d + 3 * d + 3, DY: lambda d: FLOPS_PER_EVENT_FP32 + 4 * (d - 4),
+          EE3J: lambda d: FLOPS_EE3J_FP32 + 4 * (d - 5)}
+    flops_b = sum(fl[m.integrand](m.ndim) * m.ncall for m in spec) / sum(m.ncall for m in spec)
+    ach = flops_b * tot / (ms * 1e-3) / 1e12
+    res["batch64_10it_fp32"] = {
+        "value": tot / (ms * 1e-3), "unit": UNIT, "events_per_iteration": tot // 10,
+        "stage_roofline": {"flops_per_event": flops_b, "achieved_tflops": ach,
+                           "frac_of_measured_ffma": ach / ffma,
+                           "note": "whole stage (fills, reduce, refinement) over the FFMA peak"},
+        "fp32_vs_fp64": {"max_rel_diff_integral": float(np.max(np.abs(o32[0] - o64[0]) /
+                                                                np.abs(o64[0]))),
+                         "max_diff_in_sigma": float(np.max(np.abs(o32[0] - o64[0]) / o64[1]))}}
+    res["paper_shaped"] = paper_shaped(v, stream, seed, timed)
     return res
+
+
+def paper_shaped(v, stream, seed, timed):
+    """The paper's run shape (Section 3.2): a warm-up stage of 4 x 1,000 and a
+    production stage of 10 x 10,000 events, here on the 10- and 13-axis
+    Gaussian (the process of the paper is not available).  Latency-bound on
+    a GPU: reported, not targeted."""
+    from paper_1503_06182_gb300.workloads import GAUSS, GAUSS_PARAMS
+
+    out = {}
+    for d in (10, 13):
+        for prec in ("fp64", "fp32"):
+            g = v.Vegas(d, 50, seed, precision=prec)
+            v.vegas_set_stream(g.h, stream.cuda_stream)
+            try:
+                g.iterate(1000, 4, GAUSS, GAUSS_PARAMS)  # tunes and captures
+                g.iterate(10_000, 10, GAUSS, GAUSS_PARAMS)
+                ms_w, _ = timed(lambda: g.iterate(1000, 4, GAUSS, GAUSS_PARAMS))
+                ms_p, (I, e, c, _, _) = timed(lambda: g.iterate(10_000, 10, GAUSS, GAUSS_PARAMS))
+            finally:
+                g.close()
+            out[f"gauss_d{d}_n50_4x1e3+10x1e4_{prec}"] = {
+                "ms_warmup": ms_w, "ms_production": ms_p,
+                "events_per_s": 104_000 / ((ms_w + ms_p) * 1e-3), "integral": I, "error": e}
+    return out
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -430,6 +619,64 @@ def cpu_baseline(args):
     rate, n_it, dt, cores = _oracle_rate(args.cpu_seconds)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_it} iterations x 1e6 events of the same workload (FP64), {dt:.1f} s"}
+
+
+def cpu_baselines():
+    """The oracle (FP64, OpenMP over this host's cores) on every configuration,
+    each on a bounded sample of its workload; events/s is the sample's rate.
+    Also the per-core rate of the Gaussian configuration (one thread) and the
+    paper-shaped runs.  A few seconds of CPU work in all."""
+    import oracle
+    from paper_1503_06182_gb300.workloads import (DY, DY_PARAMS, EE3J, EE3J_PARAMS, GAUSS,
+                                                  GAUSS_PARAMS, SEED, batch_spec)
+
+    oracle.build()
+    cores = oracle.get_threads()
+    out = {}
+
+    def rate(name, events, fn, sample, reps=1, **extra):
+        dt = float("inf")
+        for _ in range(reps):  # the fastest of reps runs (short samples)
+            t0 = time.perf_counter()
+            fn()
+            dt = min(dt, time.perf_counter() - t0)
+        if reps > 1:
+            sample += f" (fastest of {reps})"
+        out[name] = {"value": events / dt, "unit": UNIT, "cores": extra.pop("cores", cores),
+                     "kind": "oracle", "sample": f"{sample}, {dt:.3f} s", **extra}
+
+    rate("gauss_d4_n50_5x1e5", 5 * 100_000,
+         lambda: oracle.iterate(4, 50, SEED, 100_000, 5, GAUSS, GAUSS_PARAMS),
+         "the whole 5 x 1e5 stage", reps=5)
+    oracle.set_threads(1)
+    try:
+        rate("gauss_d4_n50_1e5_one_core", 100_000,
+             lambda: oracle.iterate(4, 50, SEED, 100_000, 1, GAUSS, GAUSS_PARAMS),
+             "one 1e5-event iteration on one thread", reps=5, cores=1)
+    finally:
+        oracle.set_threads(cores)
+    r = oracle.iterate(5, 100, SEED, 1_000_000, 1, EE3J, EE3J_PARAMS)
+    rate("ee3j_d5_n100_10x1e7", 10_000_000,
+         lambda: oracle.iterate(5, 100, SEED, 10_000_000, 1, EE3J, EE3J_PARAMS, edges=r.edges,
+                                iteration=1), "one 1e7-event iteration of the 10 x 1e7 stage")
+    r = oracle.iterate(NDIM, NBINS, SEED, 1_000_000, 3, DY, DY_PARAMS)
+    rate("dy_adjoint_d4_n100_10x1e8", 10_000_000,
+         lambda: oracle.adjoint(NDIM, NBINS, SEED, 10_000_000, 1, DY_PARAMS, edges=r.edges,
+                                iteration=3),
+         "one 1e7-event gradient iteration; the workload is 10 x 1e8, so its rate is this "
+         "sample's scaled linearly", scaled=True)
+    spec = batch_spec(64, SEED)
+    rate("batch64_1iteration", sum(m.ncall for m in spec),
+         lambda: [oracle.iterate(m.ndim, NBINS, SEED, m.ncall, 1, m.integrand, m.params,
+                                 batch=m.index) for m in spec],
+         "one iteration of each of the 64 integrations, one after the other")
+    for d in (10, 13):
+        rate(f"gauss_d{d}_n50_4x1e3+10x1e4", 104_000,
+             lambda: oracle.iterate(d, 50, SEED, 10_000, 10, GAUSS, GAUSS_PARAMS,
+                                    edges=oracle.iterate(d, 50, SEED, 1000, 4, GAUSS,
+                                                         GAUSS_PARAMS).edges, iteration=4),
+             "the paper's run shape: 4 x 1,000 warm-up + 10 x 10,000 production events", reps=5)
+    return out
 
 
 def run_reference(args):

@@ -215,6 +215,25 @@ int vegas_rng_words(uint64_t seed, uint32_t iteration, uint32_t batch, int64_t f
 int vegas_rng_words_noalloc(uint64_t seed, uint32_t iteration, uint32_t batch,
                             int64_t first_event, int64_t n, int ndim, uint32_t* out);
 
+/* Measurement helper (no counterpart in the paper): the rate of one
+ * arithmetic pipe of the current GPU at its present clock, the denominator of
+ * the per-event kernels' rooflines (they are bound by plain arithmetic, not by
+ * a dense contraction or by HBM).  A probe kernel runs 8 independent chains of
+ * one instruction per thread, 8 resident 256-thread CTAs per SM, for about
+ * `ms` milliseconds (0 < ms <= 10000; the round count is calibrated first):
+ *   VEGAS_PIPE_FFMA  FP32 fused multiply-add, 2 flops each;
+ *   VEGAS_PIPE_DFMA  FP64 fused multiply-add, 2 flops each;
+ *   VEGAS_PIPE_IMAD  32-bit integer multiply-add, 1 op each;
+ *   VEGAS_PIPE_MUFU  FP32 base-2 exponential approximation, 1 op each.
+ * *ops_per_s receives flops (or ops) per second.  Uses the legacy default
+ * stream and allocates a small output buffer.  VEGAS_EINVAL for an unknown
+ * pipe or duration, VEGAS_ECUDA if a CUDA call failed. */
+#define VEGAS_PIPE_FFMA 0
+#define VEGAS_PIPE_DFMA 1
+#define VEGAS_PIPE_IMAD 2
+#define VEGAS_PIPE_MUFU 3
+int vegas_pipe_peak(int pipe, double ms, double* ops_per_s);
+
 /* FP64 sums of the last iteration: (sum w, sum w^2, d[ndim*nbins]), with
  * d[a*nbins + i] = sum of w^2 over the events in bin i of axis a. */
 int vegas_last_sums(const vegas_ctx* ctx, double* sums);

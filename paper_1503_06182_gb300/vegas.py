@@ -29,6 +29,7 @@ VEGAS_MAX_PARAMS = 16
 VEGAS_TILE = 1024
 VEGAS_NOALLOC_MAX_WORDS = 1 << 18
 VEGAS_HIST_MAX_BINS = 1000
+VEGAS_PIPE_FFMA, VEGAS_PIPE_DFMA, VEGAS_PIPE_IMAD, VEGAS_PIPE_MUFU = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -99,6 +100,7 @@ def lib():
             "vegas_rng_words_noalloc": ([C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int64,
                                          C.c_int, _u32p], C.c_int),
             "vegas_last_sums": ([_vp, _dp], C.c_int),
+            "vegas_pipe_peak": ([C.c_int, C.c_double, C.POINTER(C.c_double)], C.c_int),
             "vegas_hist_set": ([_vp, C.c_int, C.c_double, C.c_double], C.c_int),
             "vegas_strat_get": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), _vp, _vp], C.c_int),
             "vegas_strat_set": ([_vp, C.c_int64, _vp], C.c_int),
@@ -276,6 +278,13 @@ def vegas_rng_words_noalloc(seed: int, iteration: int, batch: int, first_event: 
                              f"buffer of {VEGAS_NOALLOC_MAX_WORDS} words")
     _check(st, "vegas_rng_words_noalloc")
     return out
+
+
+def vegas_pipe_peak(pipe: int, ms: float = 50.0) -> float:
+    """Measured rate of one arithmetic pipe (VEGAS_PIPE_*), flops or ops per second."""
+    r = C.c_double()
+    _check(lib().vegas_pipe_peak(int(pipe), float(ms), C.byref(r)), "vegas_pipe_peak")
+    return r.value
 
 
 def vegas_last_sums(h, ndim: int, nbins: int) -> np.ndarray:
