@@ -284,6 +284,7 @@ struct Plan {
   int ig, fp32, mode, itmx, n_tiles, nacc, nch, ept, reduce_ctas, tiles_per_cta;
   int nhist;  // histogram bins with underflow and overflow (0: none)
   int slot_major;  // slot-major partials and the single-level reduce (forward stages)
+  int hoist;       // the fill makes its Philox words before it waits (gv_fill_hoistable)
   int plus, s;     // VEGAS+: strata per axis
   long long nh;    // hypercubes
   long long cap;   // events the fill's grid can hold
@@ -298,8 +299,9 @@ struct Plan {
   GvSlot* cpart;
 };
 
-GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
+GvFillArgs fill_args(const vegas_ctx* c, const Plan& p, int k = 0) {
   GvFillArgs a;
+  a.kst = k;
   a.ndim = c->ndim;
   a.nbins = c->nbins;
   a.nch = p.nch;
@@ -313,6 +315,7 @@ GvFillArgs fill_args(const vegas_ctx* c, const Plan& p) {
   a.part = p.part;
   a.tileE = p.tileE;
   a.slot_major = p.slot_major;
+  a.hoist = p.hoist;
   a.n_tiles = p.n_tiles;
   a.nhist = p.nhist;
   if (p.nhist) {
@@ -485,8 +488,9 @@ int ensure_consts(vegas_ctx* c, int ig, const double* params, int np) {
   return VEGAS_OK;
 }
 
-cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pdl = false) {
-  const GvFillArgs a = fill_args(c, p);
+cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pdl = false,
+                             int k = 0) {
+  const GvFillArgs a = fill_args(c, p, k);
   if (p.mode) return gv::launch_fill_adjoint(p.fp32, ept, a, p.n_tiles, p.smem, c->stream, pdl);
   if (p.nhist) return gv::launch_fill_hist(p.ig, p.fp32, a, p.n_tiles, p.smem, c->stream, pdl);
   if (p.plus) return gv::launch_fill_plus(p.ig, p.fp32, a, p.n_tiles, p.smem, c->stream, pdl);
@@ -582,9 +586,17 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.slot_major = mode == 0 ? 1 : 0;
   p.nhist = (mode == 0 && c->hist_nh > 0) ? c->hist_nh + 2 : 0;
   p.nacc = mode ? 2 * GV_MAXCH : 2 + c->ndim * c->nbins + 2 * p.nhist;
-  p.smem = GvFillSmem(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist,
-                      p.plus != 0)
-               .total;
+  {
+    const GvFillSmem plain(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist,
+                           p.plus != 0, false);
+    const GvFillSmem words(c->ndim, c->nbins, c->fp32 ? 4 : 8, mode == 0, c->ndim > 4, p.nhist,
+                           p.plus != 0, true);
+    p.hoist = gv_fill_hoistable(mode == 0, p.plus != 0, c->ndim) &&
+                      words.total <= GV_WORDS_SMEM_MAX
+                  ? 1
+                  : 0;
+    p.smem = (p.hoist ? words : plain).total;
+  }
   int gx = 0, gy = 0;
   gv::reduce_grid(p.n_tiles, p.nacc, &p.tiles_per_cta, &gx, &gy);
   p.reduce_ctas = gx * gy;
@@ -667,7 +679,7 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
   const bool pdl = c->pdl && !ev;
   for (int k = 0; k < p.itmx; ++k) {
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
-    GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0));
+    GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0, k));
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
     if (p.slot_major)
       GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl));
@@ -1291,6 +1303,7 @@ int vegas_state_set(vegas_ctx* c, const void* buf, size_t bytes) {
   GvState hs;
   GV_TRY(cudaMemcpy(&hs, c->st, sizeof hs, cudaMemcpyDeviceToHost));
   hs.it = h.it;
+  hs.it0 = h.it;
   GV_TRY(cudaMemcpy(c->st, &hs, sizeof hs, cudaMemcpyHostToDevice));
   clear_graphs(c);
   c->plus_valid = false;  // a VEGAS+ allocation is not part of a checkpoint

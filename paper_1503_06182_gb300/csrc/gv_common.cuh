@@ -60,6 +60,11 @@ struct GvState {
   int pad;
   double integral, error, chi2;
   double grad[GV_NGRAD], grad_err[GV_NGRAD];
+  // the counter at the start of the running stage: the counter of its
+  // iteration k is it0 + k.  Written only by the last iteration of a stage
+  // (and with `it` by the host), so the fill of iteration k > 0 may read it
+  // while the previous iteration's kernels still run.
+  unsigned long long it0;
 };
 
 // Grid pack of one integration (device memory, rewritten by every refine):
@@ -116,6 +121,8 @@ struct GvFillArgs {
                                  // (slot_major, read by the single-level reduce)
   int* tileE;                    // [tile][nch] scales
   int slot_major = 0, n_tiles = 0;
+  int kst = 0;                   // the iteration's index in its stage (counter it0 + kst)
+  int hoist = 0;                 // 1: the forward fill makes its words before it waits
   // histogram of the integrand's observable (forward fill only): nhist bins,
   // 0 = underflow, nhist - 1 = overflow (nhist = 0: no histogram); the bin of
   // a value v >= lo is 1 + trunc((v - lo) invw), in the integrand's precision

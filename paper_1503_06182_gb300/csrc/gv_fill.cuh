@@ -267,16 +267,29 @@ struct GvPair<double> {
 //   hh   [7][nhist] u32   histogram: w^2 limbs [3], w limbs [3] (the third
 //                         signed), the tile's bin exponents (with a histogram)
 //   po   [GV_PLUS_WIN] i32 hypercube offsets relative to the tile (VEGAS+)
+//   wd   [ceil(d/4)][GV_TILE] uint4  the tile's Philox words, generated before
+//                         the kernel waits for its predecessor (see below)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// The forward fill generates its tile's Philox words before it waits for the
+// previous kernel (the words depend only on the seed, the counter and the
+// event), where the launch overlaps the previous iteration's reduce and
+// refinement; not with VEGAS+ (stratified words), nor beyond 8 axes, nor
+// where the words' shared memory would take the layout past GV_WORDS_SMEM_MAX
+// (the host sets GvFillArgs::hoist accordingly).
+#define GV_WORDS_SMEM_MAX (200 * 1024)
+__host__ __device__ inline bool gv_fill_hoistable(bool forward, bool plus, int d) {
+  return forward && !plus && d <= 8;
+}
 
 // A tile of GV_TILE events meets at most GV_TILE/2 + 1 hypercubes (each has
 // at least 2 events): the window holds their offsets and the next one.
 #define GV_PLUS_WIN (GV_TILE / 2 + 4)
 
 struct GvFillSmem {
-  size_t hist, jac, ew, bins, hh, po, total;
+  size_t hist, jac, ew, bins, hh, po, wd, total;
   __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem,
-                                 int nhist = 0, bool plus = false) {
+                                 int nhist = 0, bool plus = false, bool words = false) {
     const size_t dN = (size_t)d * N;
     hist = 0;
     jac = gv_align16(hist + (forward ? dN * 16 : 0));
@@ -284,7 +297,8 @@ struct GvFillSmem {
     bins = gv_align16(ew + dN * 16);
     hh = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
     po = gv_align16(hh + (forward ? (size_t)nhist * 7 * 4 : 0));
-    total = gv_align16(po + (plus ? (size_t)GV_PLUS_WIN * 4 : 0));
+    wd = gv_align16(po + (plus ? (size_t)GV_PLUS_WIN * 4 : 0));
+    total = gv_align16(wd + (words ? (size_t)((d + 3) / 4) * GV_TILE * 16 : 0));
   }
 };
 
@@ -475,7 +489,8 @@ __device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
 template <int IG, typename Real, int EPT, int MAXD, bool HIST = false, bool PLUS = false>
 __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile,
                                              unsigned char* smem, unsigned long long* red_u64,
-                                             u128* red_128, uint32_t it) {
+                                             u128* red_128, uint32_t it,
+                                             const uint4* s_words = nullptr) {
   constexpr int B = GV_TILE / EPT;
   constexpr int NW = B / 32;
   using Pair = typename GvPair<Real>::T;
@@ -532,7 +547,20 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     hbin[k] = 0;
     if (ev < ncall) {
       uint32_t r[MAXD];
-      gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
+      if (s_words) {  // generated before the wait (by this thread: same local index)
+#pragma unroll
+        for (int j = 0; j < (MAXD + 3) / 4; ++j) {
+          if (4 * j < d) {
+            const uint4 o = s_words[j * GV_TILE + local];
+            if (4 * j + 0 < MAXD) r[4 * j + 0] = o.x;
+            if (4 * j + 1 < MAXD) r[4 * j + 1] = o.y;
+            if (4 * j + 2 < MAXD) r[4 * j + 2] = o.z;
+            if (4 * j + 3 < MAXD) r[4 * j + 3] = o.w;
+          }
+        }
+      } else {
+        gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
+      }
       long long hc = 0;
       if constexpr (PLUS) {
         hc = h0 + gv_plus_cube(s_off, local);
@@ -739,6 +767,26 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   }
 }
 
+// The Philox words of a tile's events at counter `it` into shared memory
+// (layout [ceil(d/4)][GV_TILE]); each thread makes the words of the events it
+// will evaluate (local index tid + k B), so no barrier is needed before use.
+template <int MAXD>
+__device__ __forceinline__ void gv_tile_words(const GvFillArgs& a, uint32_t it, long long tile,
+                                              uint4* s_words, int B) {
+  const int d = a.ndim;
+  const long long t0 = tile * GV_TILE;
+  for (int local = threadIdx.x; local < GV_TILE; local += B) {
+    uint32_t r[MAXD];
+    gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)(t0 + local), d, r);
+#pragma unroll
+    for (int j = 0; j < (MAXD + 3) / 4; ++j)
+      if (4 * j < d)
+        s_words[j * GV_TILE + local] =
+            make_uint4(r[4 * j], 4 * j + 1 < MAXD ? r[4 * j + 1] : 0u,
+                       4 * j + 2 < MAXD ? r[4 * j + 2] : 0u, 4 * j + 3 < MAXD ? r[4 * j + 3] : 0u);
+  }
+}
+
 // Minimum resident CTAs per SM in the fill's launch bound (0: none), i.e. its
 // register budget.  FP32 fills of at most 8 axes: 64 registers at any width
 // (the stratified fill included).  FP32 fills of up to 16 axes without
@@ -763,12 +811,22 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, 
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
-  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0, PLUS);
+  const bool hoist = !PLUS && MAXD <= 8 && a.hoist;  // set by the host (gv_fill_hoistable)
+  const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0, PLUS, hoist);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
   for (int k = threadIdx.x; k < 4 * d * N; k += B) hist[k] = 0u;
   if constexpr (HIST) {
     unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);
     for (int k = threadIdx.x; k < 7 * a.nhist; k += B) hh[k] = 0u;
+  }
+  // the tile's words at the counter this iteration should have (the stage's
+  // first counter, which no running kernel writes, plus the iteration index),
+  // made while the previous iteration's reduce and refinement finish
+  uint4* s_words = reinterpret_cast<uint4*>(smem + lay.wd);
+  uint32_t itg = 0u;
+  if (hoist) {
+    itg = (uint32_t)(a.st->it0 + (unsigned long long)a.kst);
+    gv_tile_words<MAXD>(a, itg, blockIdx.x, s_words, B);
   }
   gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
   if constexpr (PLUS) {
@@ -802,8 +860,10 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, 
     }
   }
   const uint32_t it = (uint32_t)a.st->it;
+  if (hoist && it != itg) gv_tile_words<MAXD>(a, it, blockIdx.x, s_words, B);  // (not expected)
   __syncthreads();
-  gv_fill_tile<IG, Real, EPT, MAXD, HIST, PLUS>(a, blockIdx.x, smem, red_u64, red_128, it);
+  gv_fill_tile<IG, Real, EPT, MAXD, HIST, PLUS>(a, blockIdx.x, smem, red_u64, red_128, it,
+                                                hoist ? s_words : nullptr);
 }
 
 // Single-event diagnostics (no shared memory): weight and bins of the given

@@ -205,6 +205,7 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
   }
   if (tid == 0) {
     st->it = st->it + 1ull;
+    if (a.last) st->it0 = st->it;  // the next stage's first counter
     if (a.last && a.host_st) {
       // the state the host reads after the stage: this thread wrote all of it
       a.host_st->it = st->it;
