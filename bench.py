@@ -60,10 +60,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 80_384
+FILL_TRAFFIC_BYTES = 82_944
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "d2aaa5757c0a219f965c90d1e96b5eb96b1d1b014057b79110c2cda22077ca3c"
+FILL_SOURCES_SHA256 = "b3f77f4bf15475a9fdff658f70dec529ef87a84cb622883be74dfdc9936e7f41"
 # HBM copy bandwidth measured by the driver on the GB300s (used when
 # MEASURED_PEAKS.json is absent: the profiling recipe's fallback)
 HBM_FALLBACK_GBS = 6800.0
@@ -389,7 +389,7 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def forms(v, stream, seed, peaks):
+def forms(v, stream, seed, peaks, only=None):
     """The other workloads, each a warm-up stage then one timed stage on the
     bench stream (device time between CUDA events; L2 not flushed inside a
     stage, as in a real run): 3-jet 10 x 1e7 FP32; Drell-Yan adjoint 10 x 1e8
@@ -408,6 +408,9 @@ def forms(v, stream, seed, peaks):
                                                   EE3J_PARAMS, GAUSS, GAUSS_PARAMS, batch_spec)
 
     ffma = peaks["ffma_tflops"]
+
+    def want(name):
+        return only is None or name in only
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,6 +446,8 @@ def forms(v, stream, seed, peaks):
                                                   "fp32", None, FLOPS_DYNLO_FP32),
             "dy_mll_hist60_d4_n100_10x1e6_fp32": (DY, DY_PARAMS, 4, 100, 1_000_000, 10, "fp32",
                                                   (60, 60.0, 120.0), FLOPS_PER_EVENT_FP32)}.items():
+        if not want(name):
+            continue
         out = {}
         edges = None
         for p in ((prec, "fp64") if prec == "fp32" else (prec,)):
@@ -481,93 +486,109 @@ def forms(v, stream, seed, peaks):
                 r["fp32_vs_fp64"]["hist_max_rel_diff_bin"] = float(
                     np.max(np.abs(h32[nz] - h64[nz]) / np.abs(h64[nz])))
         res[name] = r
-    # VEGAS+ against plain VEGAS: the same workload, events/s and efficiency
-    plus = {}
-    for strat, prec in ((0, "fp32"), (1, "fp32"), (1, "fp64")):
-        g = v.Vegas(NDIM, NBINS, seed, precision=prec)
-        v.vegas_set_stream(g.h, stream.cuda_stream)
-        g.set(v.VEGAS_OPT_STRAT, strat)
-        try:
-            g.iterate(NCALL, 10, DY, DY_PARAMS)  # warm-up stage: grid and allocation adapt
-            ms, (I, e, c, _, _) = timed(lambda: g.iterate(NCALL, 10, DY, DY_PARAMS))
-        finally:
-            g.close()
-        plus[(strat, prec)] = (ms, I, e, c)
-    ms, I, e, c = plus[(1, "fp32")]
-    p0 = plus[(0, "fp32")]
-    res["dy_vegasplus_d4_n100_10x1e6_fp32"] = {
-        "value": NCALL * 10 / (ms * 1e-3), "unit": UNIT, "integral": I, "error": e, "chi2_dof": c,
-        "events_note": "target 1e6 calls per iteration; VEGAS+ runs up to 1e6 + 2 nh",
-        "error_plain_vegas": p0[2], "ms_plain_vegas": p0[0],
-        "efficiency_ratio_over_plain": (p0[2] ** 2 * p0[0]) / (e ** 2 * ms),
-        "fp32_vs_fp64": vs64(I, e, plus[(1, "fp64")][1], plus[(1, "fp64")][2])}
-    # gradient: frozen grid adapted by a forward warm-up, then the adjoint stage
-    adj = {}
-    edges = None
-    for prec in ("fp32", "fp64"):
-        g = v.Vegas(NDIM, NBINS, seed, precision=prec)
-        v.vegas_set_stream(g.h, stream.cuda_stream)
-        try:
-            g.iterate(NCALL, 5, DY, DY_PARAMS)
-            if edges is None:
-                edges = g.grid
-            else:  # the FP64 gradient on the FP32 form's frozen grid: the same events
-                g.grid = edges
-            g.set(v.VEGAS_OPT_ADAPT, 0)
-            st = g.state()
-            # warm-up stage of the timed size: events per thread are tuned per size
-            g.adjoint(100_000_000, 10, DY_PARAMS)
-            g.restore(st)
-            ms, (grad, gerr, I, e, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
-            fm = None
-            if prec == "fp32":
+    if want("dy_vegasplus_d4_n100_10x1e6_fp32"):
+        # VEGAS+ against plain VEGAS: the same workload, events/s and efficiency
+        plus = {}
+        for strat, prec in ((0, "fp32"), (1, "fp32"), (1, "fp64")):
+            g = v.Vegas(NDIM, NBINS, seed, precision=prec)
+            v.vegas_set_stream(g.h, stream.cuda_stream)
+            g.set(v.VEGAS_OPT_STRAT, strat)
+            try:
+                g.iterate(NCALL, 10, DY, DY_PARAMS)  # warm-up stage: grid and allocation adapt
+                ms, (I, e, c, _, _) = timed(lambda: g.iterate(NCALL, 10, DY, DY_PARAMS))
+            finally:
+                g.close()
+            plus[(strat, prec)] = (ms, I, e, c)
+        ms, I, e, c = plus[(1, "fp32")]
+        p0 = plus[(0, "fp32")]
+        res["dy_vegasplus_d4_n100_10x1e6_fp32"] = {
+            "value": NCALL * 10 / (ms * 1e-3), "unit": UNIT, "integral": I, "error": e, "chi2_dof": c,
+            "events_note": "target 1e6 calls per iteration; VEGAS+ runs up to 1e6 + 2 nh",
+            "error_plain_vegas": p0[2], "ms_plain_vegas": p0[0],
+            "efficiency_ratio_over_plain": (p0[2] ** 2 * p0[0]) / (e ** 2 * ms),
+            "fp32_vs_fp64": vs64(I, e, plus[(1, "fp64")][1], plus[(1, "fp64")][2])}
+    if want("dy_adjoint_d4_n100_10x1e8_fp32"):
+        # gradient: frozen grid adapted by a forward warm-up, then the adjoint stage
+        adj = {}
+        edges = None
+        for prec in ("fp32", "fp64"):
+            g = v.Vegas(NDIM, NBINS, seed, precision=prec)
+            v.vegas_set_stream(g.h, stream.cuda_stream)
+            try:
+                g.iterate(NCALL, 5, DY, DY_PARAMS)
+                if edges is None:
+                    edges = g.grid
+                else:  # the FP64 gradient on the FP32 form's frozen grid: the same events
+                    g.grid = edges
+                g.set(v.VEGAS_OPT_ADAPT, 0)
+                st = g.state()
+                # warm-up stage of the timed size: events per thread are tuned per size
+                g.adjoint(100_000_000, 10, DY_PARAMS)
                 g.restore(st)
-                fm = fill_ms(g, lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
-        finally:
-            g.close()
-        adj[prec] = (ms, np.asarray(grad), np.asarray(gerr), I, e, fm)
-    ms, grad, gerr, I, e, fm = adj["fp32"]
-    g64, ge64 = adj["fp64"][1], adj["fp64"][2]
-    ach = FLOPS_ADJOINT_FP32 * 1e8 / (fm * 1e-3) / 1e12
-    res["dy_adjoint_d4_n100_10x1e8_fp32"] = {
-        "value": 1e9 / (ms * 1e-3), "unit": UNIT, "grad": list(grad), "grad_err": list(gerr),
-        "fill_roofline": {"fill_avg_ms": fm, "flops_per_event": FLOPS_ADJOINT_FP32,
-                          "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma},
-        "fp32_vs_fp64": {"grad_fp64": list(g64), "max_diff_over_abs_plus_sigma":
-                         float(np.max(np.abs(grad - g64) / (np.abs(g64) + ge64))),
-                         "integral_rel_diff": abs(I - adj["fp64"][3]) / abs(adj["fp64"][3])}}
-    # batched: 64 integrations of uneven dimension, calls and integrand
-    spec = batch_spec(64, seed)
-    members = [(m.ndim, m.ncall, m.integrand, m.params) for m in spec]
-    bat = {}
-    for prec in ("fp32", "fp64"):
-        B = v.VegasBatch(members, NBINS, seed, precision=prec)
-        v.vegas_batch_set_stream(B.h, stream.cuda_stream)
-        try:
-            B.iterate(1)  # tunes events per thread
-            B.iterate(10)  # captures the 10-iteration graph
-            ms, out = timed(lambda: B.iterate(10))
-        finally:
-            B.close()
-        bat[prec] = (ms, out)
-    tot = sum(m.ncall for m in spec) * 10
-    (ms, o32), o64 = bat["fp32"], bat["fp64"][1]
-    # events-weighted FP32 flops of the members' integrands (the Gaussian:
-    # grid map 4 d + d (sub, fma) + exp and scale 3)
-    fl = {GAUSS: lambda d: 4 * d + 3 * d + 3, DY: lambda d: FLOPS_PER_EVENT_FP32 + 4 * (d - 4),
-          EE3J: lambda d: FLOPS_EE3J_FP32 + 4 * (d - 5)}
-    flops_b = sum(fl[m.integrand](m.ndim) * m.ncall for m in spec) / sum(m.ncall for m in spec)
-    ach = flops_b * tot / (ms * 1e-3) / 1e12
-    res["batch64_10it_fp32"] = {
-        "value": tot / (ms * 1e-3), "unit": UNIT, "events_per_iteration": tot // 10,
-        "stage_roofline": {"flops_per_event": flops_b, "achieved_tflops": ach,
-                           "frac_of_measured_ffma": ach / ffma,
-                           "note": "whole stage (fills, reduce, refinement) over the FFMA peak"},
-        "fp32_vs_fp64": {"max_rel_diff_integral": float(np.max(np.abs(o32[0] - o64[0]) /
-                                                                np.abs(o64[0]))),
-                         "max_diff_in_sigma": float(np.max(np.abs(o32[0] - o64[0]) / o64[1]))}}
-    res["paper_shaped"] = paper_shaped(v, stream, seed, timed)
+                ms, (grad, gerr, I, e, _) = timed(lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
+                fm = None
+                if prec == "fp32":
+                    g.restore(st)
+                    fm = fill_ms(g, lambda: g.adjoint(100_000_000, 10, DY_PARAMS))
+            finally:
+                g.close()
+            adj[prec] = (ms, np.asarray(grad), np.asarray(gerr), I, e, fm)
+        ms, grad, gerr, I, e, fm = adj["fp32"]
+        g64, ge64 = adj["fp64"][1], adj["fp64"][2]
+        ach = FLOPS_ADJOINT_FP32 * 1e8 / (fm * 1e-3) / 1e12
+        res["dy_adjoint_d4_n100_10x1e8_fp32"] = {
+            "value": 1e9 / (ms * 1e-3), "unit": UNIT, "grad": list(grad), "grad_err": list(gerr),
+            "fill_roofline": {"fill_avg_ms": fm, "flops_per_event": FLOPS_ADJOINT_FP32,
+                              "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma},
+            "fp32_vs_fp64": {"grad_fp64": list(g64), "max_diff_over_abs_plus_sigma":
+                             float(np.max(np.abs(grad - g64) / (np.abs(g64) + ge64))),
+                             "integral_rel_diff": abs(I - adj["fp64"][3]) / abs(adj["fp64"][3])}}
+    if want("batch64_10it_fp32"):
+        # batched: 64 integrations of uneven dimension, calls and integrand
+        spec = batch_spec(64, seed)
+        members = [(m.ndim, m.ncall, m.integrand, m.params) for m in spec]
+        bat = {}
+        for prec in ("fp32", "fp64"):
+            B = v.VegasBatch(members, NBINS, seed, precision=prec)
+            v.vegas_batch_set_stream(B.h, stream.cuda_stream)
+            try:
+                B.iterate(1)  # tunes events per thread
+                B.iterate(10)  # captures the 10-iteration graph
+                ms, out = timed(lambda: B.iterate(10))
+            finally:
+                B.close()
+            bat[prec] = (ms, out)
+        tot = sum(m.ncall for m in spec) * 10
+        (ms, o32), o64 = bat["fp32"], bat["fp64"][1]
+        # events-weighted FP32 flops of the members' integrands (the Gaussian:
+        # grid map 4 d + d (sub, fma) + exp and scale 3)
+        fl = {GAUSS: lambda d: 4 * d + 3 * d + 3, DY: lambda d: FLOPS_PER_EVENT_FP32 + 4 * (d - 4),
+              EE3J: lambda d: FLOPS_EE3J_FP32 + 4 * (d - 5)}
+        flops_b = sum(fl[m.integrand](m.ndim) * m.ncall for m in spec) / sum(m.ncall for m in spec)
+        ach = flops_b * tot / (ms * 1e-3) / 1e12
+        res["batch64_10it_fp32"] = {
+            "value": tot / (ms * 1e-3), "unit": UNIT, "events_per_iteration": tot // 10,
+            "stage_roofline": {"flops_per_event": flops_b, "achieved_tflops": ach,
+                               "frac_of_measured_ffma": ach / ffma,
+                               "note": "whole stage (fills, reduce, refinement) over the FFMA peak"},
+            "fp32_vs_fp64": {"max_rel_diff_integral": float(np.max(np.abs(o32[0] - o64[0]) /
+                                                                    np.abs(o64[0]))),
+                             "max_diff_in_sigma": float(np.max(np.abs(o32[0] - o64[0]) / o64[1]))}}
+    if want("paper_shaped"):
+        res["paper_shaped"] = paper_shaped(v, stream, seed, timed)
     return res
+
+
+def run_only(names):
+    """Only the named forms (for a profiler's launch list of one workload)."""
+    import torch
+
+    from paper_1503_06182_gb300 import vegas as v
+    from paper_1503_06182_gb300.workloads import SEED
+
+    stream = torch.cuda.Stream()
+    peaks = {"ffma_tflops": v.vegas_pipe_peak(v.VEGAS_PIPE_FFMA, 20.0) / 1e12}
+    print(json.dumps({"forms": forms(v, stream, SEED, peaks, only=set(names))}))
 
 
 def paper_shaped(v, stream, seed, timed):
@@ -770,11 +791,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ept", type=int, default=0, choices=(0, 1, 2, 4, 8),
                     help="events per thread of the fill kernel (0: autotuned)")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated names of forms to run alone (profiling); prints "
+                         "their results instead of the benchmark line")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the extra workloads reported under 'forms'")
     ap.add_argument("--oracle-scaling", action="store_true",
                     help="print the oracle's thread-scaling table (CPU only) and exit")
     args = ap.parse_args()
+    if args.only:
+        run_only(args.only.split(","))
+        return
     if args.oracle_scaling:
         print(json.dumps({"oracle_scaling": oracle_scaling()}))
         return
