@@ -430,11 +430,17 @@ def forms(v, stream, seed, peaks, only=None):
         v.vegas_set_option(g.h, v.VEGAS_OPT_TIMING, 0)
         return ms / max(n, 1)
 
-    def vs64(I, e, I64, e64):
-        return {"integral_fp64": I64, "error_fp64": e64,
-                "rel_diff_integral": abs(I - I64) / abs(I64),
-                "diff_in_sigma": abs(I - I64) / e64 if e64 > 0 else None,
-                "rel_diff_error": abs(e - e64) / e64 if e64 > 0 else None}
+    def vs64(I, e, I64, e64, ms=None, ms64=None, events=None):
+        r = {"integral_fp64": I64, "error_fp64": e64,
+             "rel_diff_integral": abs(I - I64) / abs(I64),
+             "diff_in_sigma": abs(I - I64) / e64 if e64 > 0 else None,
+             "rel_diff_error": abs(e - e64) / e64 if e64 > 0 else None}
+        if ms and ms64 and events:
+            # events/s of the FP64 form, and the integration efficiency
+            # 1/(sigma^2 t) of the FP32 form over the FP64 form's
+            r["value_fp64"] = events / (ms64 * 1e-3)
+            r["efficiency_ratio_fp32_over_fp64"] = (e64 ** 2 * ms64) / (e ** 2 * ms) if e > 0 else None
+        return r
 
     res = {}
     for name, (iid, params, d, n, ncall, itmx, prec, hist, flops) in {
@@ -479,7 +485,8 @@ def forms(v, stream, seed, peaks, only=None):
             r["fill_roofline"] = {"fill_avg_ms": fm, "flops_per_event": flops,
                                   "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma}
         if "fp64" in out and prec == "fp32":
-            r["fp32_vs_fp64"] = vs64(I, e, out["fp64"][1], out["fp64"][2])
+            r["fp32_vs_fp64"] = vs64(I, e, out["fp64"][1], out["fp64"][2], ms, out["fp64"][0],
+                                     ncall * itmx)
             if hist:
                 h32, h64 = hv, out["fp64"][5]
                 nz = h64 != 0
@@ -506,7 +513,8 @@ def forms(v, stream, seed, peaks, only=None):
             "events_note": "target 1e6 calls per iteration; VEGAS+ runs up to 1e6 + 2 nh",
             "error_plain_vegas": p0[2], "ms_plain_vegas": p0[0],
             "efficiency_ratio_over_plain": (p0[2] ** 2 * p0[0]) / (e ** 2 * ms),
-            "fp32_vs_fp64": vs64(I, e, plus[(1, "fp64")][1], plus[(1, "fp64")][2])}
+            "fp32_vs_fp64": vs64(I, e, plus[(1, "fp64")][1], plus[(1, "fp64")][2], ms,
+                                 plus[(1, "fp64")][0], NCALL * 10)}
     if want("dy_adjoint_d4_n100_10x1e8_fp32"):
         # gradient: frozen grid adapted by a forward warm-up, then the adjoint stage
         adj = {}
@@ -540,7 +548,8 @@ def forms(v, stream, seed, peaks, only=None):
             "value": 1e9 / (ms * 1e-3), "unit": UNIT, "grad": list(grad), "grad_err": list(gerr),
             "fill_roofline": {"fill_avg_ms": fm, "flops_per_event": FLOPS_ADJOINT_FP32,
                               "achieved_tflops": ach, "frac_of_measured_ffma": ach / ffma},
-            "fp32_vs_fp64": {"grad_fp64": list(g64), "max_diff_over_abs_plus_sigma":
+            "fp32_vs_fp64": {"grad_fp64": list(g64), "value_fp64": 1e9 / (adj["fp64"][0] * 1e-3),
+                             "max_diff_over_abs_plus_sigma":
                              float(np.max(np.abs(grad - g64) / (np.abs(g64) + ge64))),
                              "integral_rel_diff": abs(I - adj["fp64"][3]) / abs(adj["fp64"][3])}}
     if want("batch64_10it_fp32"):
@@ -571,7 +580,8 @@ def forms(v, stream, seed, peaks, only=None):
             "stage_roofline": {"flops_per_event": flops_b, "achieved_tflops": ach,
                                "frac_of_measured_ffma": ach / ffma,
                                "note": "whole stage (fills, reduce, refinement) over the FFMA peak"},
-            "fp32_vs_fp64": {"max_rel_diff_integral": float(np.max(np.abs(o32[0] - o64[0]) /
+            "fp32_vs_fp64": {"value_fp64": tot / (bat["fp64"][0] * 1e-3),
+                             "max_rel_diff_integral": float(np.max(np.abs(o32[0] - o64[0]) /
                                                                     np.abs(o64[0]))),
                              "max_diff_in_sigma": float(np.max(np.abs(o32[0] - o64[0]) / o64[1]))}}
     if want("paper_shaped"):

@@ -1,11 +1,12 @@
 """GPU path vs the oracle at the sizes the benchmark runs (requires a GB300).
 
 The Drell-Yan workload of the benchmark (d = 4, N = 100, 10 iterations x 1e6
-calls; 977 tiles, which the reduce splits into 16 tile ranges of 64 tiles)
-and the other workloads at their full sizes: the Gaussian (5 x 1e5), the
-3-jet form (1e7 calls per iteration: 9,766 tiles, 64 tile ranges), the
-Drell-Yan gradient (1e8 calls per iteration) and the batch of 64
-integrations.  Sections 2.1 and 2.2: the same events give the same result
+calls; 977 tiles, which the single-level reduce reads with one 256-thread
+group per slot, four tiles per thread, from registers) and the other
+workloads at their full sizes: the Gaussian (5 x 1e5), the 3-jet form (1e7
+calls per iteration: 9,766 tiles, 38 per thread, read in two passes), the
+Drell-Yan gradient (1e8 calls per iteration, the two-level reduce) and the
+batch of 64 integrations.  Sections 2.1 and 2.2: the same events give the same result
 whatever the split of the work.
 
 Bar (FP64 form): each iteration, run by the oracle from the GPU's grid and
@@ -166,8 +167,9 @@ def test_gauss_workload_fp64_matches_oracle():
 
 
 def test_ee3j_1e7_calls_fp64_matches_oracle():
-    """3-jet form, d = 5, N = 100, 1e7 calls per iteration (64 tile ranges in
-    the reduce), two iterations from the GPU's grids."""
+    """3-jet form, d = 5, N = 100, 1e7 calls per iteration (the reduce's
+    two-pass path: more tiles than a group holds in registers), two
+    iterations from the GPU's grids."""
     ndim, nbins, ncall = 5, 100, 10_000_000
     grids, per, sums = chain(ndim, nbins, ncall, 2, v.VEGAS_EE3J, EE3J_PARAMS)
     check_iterations_fp64(ndim, nbins, ncall, v.VEGAS_EE3J, EE3J_PARAMS, grids, per, sums)
@@ -259,3 +261,20 @@ def test_batch64_workload_matches_oracle_and_single_contexts():
             assert np.array_equal(g.grid, bgrids[b]), b
         finally:
             g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_paper_shaped_gauss13_iterations_match_oracle(precision):
+    """The paper's run shape on the 13-axis Gaussian (Section 3.2: 1e4 events per
+    production iteration): each iteration against the oracle from the GPU's grid
+    and counter.  At so few events per iteration VEGAS itself is unreliable in 13
+    dimensions (single iterations scatter by factors of several), so the FP32 and
+    FP64 chains part; each step still agrees."""
+    ndim, nbins, ncall = 13, 50, 10_000
+    grids, per, sums = chain(ndim, nbins, ncall, 6, v.VEGAS_GAUSS, GAUSS_PARAMS,
+                             precision=precision)
+    if precision == "fp64":
+        check_iterations_fp64(ndim, nbins, ncall, v.VEGAS_GAUSS, GAUSS_PARAMS, grids, per, sums)
+    else:
+        check_iterations_fp32("gauss d13 N50 1e4", ndim, nbins, ncall, v.VEGAS_GAUSS,
+                              GAUSS_PARAMS, grids, per)
