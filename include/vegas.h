@@ -85,6 +85,8 @@ extern "C" {
 #define VEGAS_OPT_STRAT 9     /* 1 = VEGAS+ adaptive stratified sampling (see vegas_strat_get),
                                  0 = plain VEGAS (default) */
 #define VEGAS_OPT_BETA 10     /* VEGAS+ damping of the allocation: 0, 0.25, 0.5, 0.75 (default), 1 */
+#define VEGAS_OPT_BATCH_GRID 11 /* batches only: each work list's persistent grid in eighths of
+                                   its resident CTAs, 1..8; 0 = tuned (default) */
 
 /* ---- kernel ids for vegas_kernel_time ---- */
 #define VEGAS_KERNEL_FILL 0   /* per-event kernel */
@@ -326,8 +328,12 @@ int vegas_batch_create(int n, const int* ndim, const int64_t* ncall, const int* 
                        int precision, vegas_batch** out);
 void vegas_batch_free(vegas_batch* b);
 /* Keys: VEGAS_OPT_ALPHA, VEGAS_OPT_ADAPT, VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH
- * as for a context; VEGAS_OPT_EPT 0 (autotune), 4 or 8.  The precision is
- * fixed at creation (VEGAS_EINVAL otherwise). */
+ * as for a context; VEGAS_OPT_EPT 0 (autotune), 4 or 8.  The first stage
+ * tunes the launch shape by timing one iteration's fills, side by side as in
+ * a stage: events per thread (4 or 8, unless VEGAS_OPT_EPT fixes them) and
+ * each work list's persistent grid (all, 3/4 or 1/2 of its resident CTAs,
+ * unless VEGAS_OPT_BATCH_GRID fixes it); results do not depend on the choice.  The precision is fixed at creation
+ * (VEGAS_EINVAL otherwise). */
 int vegas_batch_set_option(vegas_batch* b, int key, double value);
 int vegas_batch_set_stream(vegas_batch* b, void* stream);
 /* itmx iterations of every integration; integral/error/chi2_dof: n values;

@@ -86,6 +86,7 @@ struct vegas_batch {
   int n = 0, N = 0;
   uint64_t seed = 0;
   int fp32 = 1, adapt = 1, ept_opt = 0, nonfinite_policy = 0, use_graph = 1;
+  int grid_opt = 0;  // eighths of the resident CTAs per list (0: tuned)
   double alpha = 1.5;
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
@@ -121,6 +122,7 @@ struct vegas_batch {
   cudaEvent_t fork = nullptr;
   size_t reduce_smem = 0;
   int ept = 0;
+  int cta_eighths = 8;  // each list's persistent grid: this many eighths of its resident CTAs
   // graph cache
   std::string graph_key;
   cudaGraphExec_t graph = nullptr;
@@ -153,14 +155,33 @@ int class_occupancy(vegas_batch* B, const vegas_batch::FillClass& c, int ept) {
   return std::max(1, f(c.ig, ept, c.smem));
 }
 
-cudaError_t fill_batch(vegas_batch* B, int ept) {
-  if (ept != 4 && ept != 8) return cudaErrorInvalidValue;
-  for (const auto& c : B->cls) {
-    const cudaError_t e =
-        fill_class(B, c, ept, class_occupancy(B, c, ept) * B->sm_count, B->stream);
-    if (e != cudaSuccess) return e;
+// A list's persistent grid: eighths/8 of its resident CTAs on every SM.
+int class_ctas(vegas_batch* B, const vegas_batch::FillClass& c, int ept, int eighths) {
+  return std::max(1, class_occupancy(B, c, ept) * B->sm_count * eighths / 8);
+}
+
+// All lists' fill launches of one iteration, side by side (as in a stage):
+// list launch_order[0] on the main stream, the others on side streams forked
+// from it and joined back.
+cudaError_t fill_lists(vegas_batch* B, int ept, const std::vector<int>& ctas) {
+  const int nl = (int)B->launch_order.size();
+  cudaError_t e = cudaSuccess;
+  if (nl > 1) e = cudaEventRecord(B->fork, B->stream);
+  for (int i = 0; i < nl && e == cudaSuccess; ++i) {
+    const int li = B->launch_order[i];
+    const auto& c = B->cls[li];
+    if (i == 0) {
+      e = fill_class(B, c, ept, ctas[li], B->stream);
+    } else {
+      cudaStream_t s = B->side[i - 1];
+      e = cudaStreamWaitEvent(s, B->fork, 0);
+      if (e == cudaSuccess) e = fill_class(B, c, ept, ctas[li], s);
+      if (e == cudaSuccess) e = cudaEventRecord(B->join[i - 1], s);
+    }
   }
-  return cudaSuccess;
+  for (int i = 1; i < nl && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(B->stream, B->join[i - 1], 0);
+  return e;
 }
 
 int reset_all(vegas_batch* B) {
@@ -259,63 +280,68 @@ int ensure_per_iter(vegas_batch* B, int itmx) {
 }
 
 int enqueue_iterations(vegas_batch* B, int itmx) {
+  std::vector<int> ctas;
+  for (const auto& c : B->cls) ctas.push_back(c.ctas);
   for (int k = 0; k < itmx; ++k) {
-    const int nl = (int)B->launch_order.size();
-    if (nl > 1) GB_TRY(cudaEventRecord(B->fork, B->stream));
-    for (int i = 0; i < nl; ++i) {
-      const auto& c = B->cls[B->launch_order[i]];
-      if (i == 0) {
-        GB_TRY(fill_class(B, c, B->ept, c.ctas, B->stream));
-      } else {
-        cudaStream_t s = B->side[i - 1];
-        GB_TRY(cudaStreamWaitEvent(s, B->fork, 0));
-        GB_TRY(fill_class(B, c, B->ept, c.ctas, s));
-        GB_TRY(cudaEventRecord(B->join[i - 1], s));
-      }
-    }
-    for (int i = 1; i < nl; ++i) GB_TRY(cudaStreamWaitEvent(B->stream, B->join[i - 1], 0));
+    GB_TRY(fill_lists(B, B->ept, ctas));
     GB_TRY(gv::launch_reduce_batch(B->d_red, B->d_red_tasks, B->n_red_tasks, k, k == itmx - 1,
                                    k > 0 ? 1.0 / (double)k : 0.0, B->reduce_smem, B->stream));
   }
   return VEGAS_OK;
 }
 
-// Choose events per thread by timing fills per candidate (between resets): 8
-// only if it beats 4 by more than 2% (the trials are noisy).
+// Choose the launch shape by timing one iteration's fills, side by side as
+// in a stage (fastest of three, between resets): events per thread 4 or 8
+// (256- or 128-thread CTAs) and each list's persistent grid, all, 3/4 or 1/2
+// of its resident CTAs (fewer CTAs per list leave room for the lists that
+// run beside it).  4 events per thread and full grids are kept unless
+// another shape is more than 2% faster (the trials are noisy).  Results do
+// not depend on the choice.
 int autotune_batch(vegas_batch* B) {
-  if (B->ept_opt) {
-    B->ept = B->ept_opt;
-  } else {
-    cudaEvent_t e0, e1;
-    GB_TRY(cudaEventCreate(&e0));
-    GB_TRY(cudaEventCreate(&e1));
-    float best = 1e30f, t4 = 1e30f;
-    int best_ept = 4;
-    for (int ept : {4, 8}) {
+  const int fixed_ept = B->ept_opt;
+  cudaEvent_t e0, e1;
+  GB_TRY(cudaEventCreate(&e0));
+  GB_TRY(cudaEventCreate(&e1));
+  const int def_ept = fixed_ept ? fixed_ept : 4;
+  const int def_eighths = B->grid_opt ? B->grid_opt : 8;
+  float best = 1e30f, t_def = 1e30f;
+  int best_ept = def_ept, best_eighths = def_eighths;
+  for (int ept : {4, 8}) {
+    if (fixed_ept && ept != fixed_ept) continue;
+    for (int eighths : {8, 6, 4}) {
+      if (B->grid_opt) eighths = B->grid_opt;
+      std::vector<int> ctas;
+      for (const auto& c : B->cls) ctas.push_back(class_ctas(B, c, ept, eighths));
       float t = 1e30f;
       for (int rep = 0; rep < 3; ++rep) {
         GB_TRY(cudaEventRecord(e0, B->stream));
-        GB_TRY(fill_batch(B, ept));
+        GB_TRY(fill_lists(B, ept, ctas));
         GB_TRY(cudaEventRecord(e1, B->stream));
         GB_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         t = std::min(t, ms);
       }
-      if (ept == 4) t4 = t;
+      if (ept == def_ept && eighths == def_eighths) t_def = t;
       if (t < best) {
         best = t;
         best_ept = ept;
+        best_eighths = eighths;
       }
+      if (B->grid_opt) break;
     }
-    if (best_ept != 4 && best > 0.98f * t4) best_ept = 4;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    B->ept = best_ept;
-    int st = reset_all(B);
-    if (st) return st;
   }
-  for (auto& c : B->cls) c.ctas = class_occupancy(B, c, B->ept) * B->sm_count;
+  if ((best_ept != def_ept || best_eighths != def_eighths) && best > 0.98f * t_def) {
+    best_ept = def_ept;
+    best_eighths = def_eighths;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->ept = best_ept;
+  B->cta_eighths = best_eighths;
+  int st = reset_all(B);
+  if (st) return st;
+  for (auto& c : B->cls) c.ctas = class_ctas(B, c, B->ept, B->cta_eighths);
   return VEGAS_OK;
 }
 
@@ -550,6 +576,11 @@ int vegas_batch_set_option(vegas_batch* B, int key, double v) {
       B->ept_opt = (int)v;
       B->ept = 0;
       break;
+    case VEGAS_OPT_BATCH_GRID:
+      if (!(v >= 0.0 && v <= 8.0) || v != std::floor(v)) return VEGAS_EINVAL;
+      B->grid_opt = (int)v;
+      B->ept = 0;
+      break;
     case VEGAS_OPT_NONFINITE:
       if (v != 0.0 && v != 1.0) return VEGAS_EINVAL;
       B->nonfinite_policy = (int)v;
@@ -596,7 +627,7 @@ int vegas_batch_iterate(vegas_batch* B, int itmx, double* integral, double* erro
   const bool graph_ok = B->use_graph && B->stream != nullptr;
   if (graph_ok) {
     const std::string key = std::to_string(itmx) + ":" + std::to_string(B->ept) + ":" +
-                            std::to_string(B->adapt);
+                            std::to_string(B->cta_eighths) + ":" + std::to_string(B->adapt);
     if (!B->graph || B->graph_key != key) {
       if (B->graph) {
         cudaGraphExecDestroy(B->graph);

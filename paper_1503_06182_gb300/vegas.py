@@ -22,7 +22,7 @@ VEGAS_ENONFINITE, VEGAS_EDEVICE, VEGAS_ESTATE = -5, -6, -7
 VEGAS_GAUSS, VEGAS_DY, VEGAS_EE3J, VEGAS_DY_NLO = 0, 1, 2, 3
 VEGAS_OPT_ALPHA, VEGAS_OPT_PRECISION, VEGAS_OPT_ADAPT, VEGAS_OPT_EPT = 0, 1, 2, 3
 VEGAS_OPT_NONFINITE, VEGAS_OPT_GRAPH, VEGAS_OPT_TIMING, VEGAS_OPT_BATCH_ID = 4, 5, 6, 7
-VEGAS_OPT_PDL, VEGAS_OPT_STRAT, VEGAS_OPT_BETA = 8, 9, 10
+VEGAS_OPT_PDL, VEGAS_OPT_STRAT, VEGAS_OPT_BETA, VEGAS_OPT_BATCH_GRID = 8, 9, 10, 11
 VEGAS_KERNEL_FILL, VEGAS_KERNEL_REDUCE, VEGAS_KERNEL_REFINE = 0, 1, 2
 VEGAS_NGRAD = 5
 VEGAS_MAX_PARAMS = 16

@@ -75,7 +75,8 @@ def test_batch_bit_identical_to_single_contexts(precision):
 
 def test_batch_launch_shapes_bit_identical():
     base, bgrids = run_batch(ept=4)
-    for opts in ({"ept": 8}, {"ept": 4, "graph": 0}):
+    for opts in ({"ept": 8}, {"ept": 4, "graph": 0}, {"ept": 4, "batch_grid": 4},
+                 {"ept": 8, "batch_grid": 3}):
         out, grids = run_batch(**opts)
         for s in range(len(STAGES)):
             for a, b in zip(out[s], base[s]):
