@@ -168,6 +168,11 @@ struct vegas_ctx {
   long long plus_tab_C = 0;  // the C of the ab table on the device (0: none)
   GvPlusArgs pa;  // device arrays of the allocation (pointers only)
   GvPlusFill* plus_fill = nullptr;  // the stratified fill's data (device)
+  // VEGAS+: the hypercube statistics, allocation and layout of an iteration
+  // run on this stream beside the reduce (forked after the fill, joined
+  // before the next fill)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -220,9 +225,8 @@ size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhis
   b += align256((size_t)n_tiles * nch * 4);
   b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
   b += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
-  // VEGAS+: per event J g (8 B), its hypercube (4 B), the segment sums (16 B)
-  if (plus_f) b += align256((size_t)ncall * 8) + align256((size_t)ncall * 4) +
-                   align256((size_t)ncall * 16);
+  // VEGAS+: segment sums (16 B) per range and per hypercube (nh <= ncall / 4)
+  if (plus_f) b += align256((size_t)(ncall / GV_PLUS_SEG + 1) * 16) + align256((size_t)(ncall / 4 + 1) * 16);
   return b;
 }
 
@@ -288,9 +292,8 @@ struct Plan {
   int plus, s;     // VEGAS+: strata per axis
   long long nh;    // hypercubes
   long long cap;   // events the fill's grid can hold
-  double* F;       // per-event J g (VEGAS+)
-  int* hc;         // per-event hypercube (VEGAS+)
-  double2* seg;    // segment sums (VEGAS+)
+  double2* seg_h;  // each hypercube's first segment sums (VEGAS+)
+  double2* seg_r;  // each range's continuing segment sums (VEGAS+)
   int64_t ncall;
   size_t smem;
   ulonglong2* part;
@@ -338,9 +341,8 @@ GvPlusArgs plus_args(const vegas_ctx* c, const Plan& p, int k) {
   a.k = k < 0 ? 0 : k;
   a.last = k == p.itmx - 1;
   a.inv_m1 = k > 0 ? 1.0 / (double)k : 0.0;
-  a.F = p.F;
-  a.hc = p.hc;
-  a.seg = p.seg;
+  a.seg_h = p.seg_h;
+  a.seg_r = p.seg_r;
   a.cap = p.cap;
   a.per_iter = p.per_iter;
   a.st = c->st;
@@ -364,6 +366,8 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   off = align256(off + (size_t)nh * 4);
   const size_t o_ab = off;
   off = align256(off + (size_t)nh * 16);
+  const size_t o_ab32 = off;
+  off = align256(off + (size_t)nh * 8);
   const size_t o_t = off;
   off = align256(off + (size_t)n_tiles * 4);
   const size_t o_var = off;
@@ -374,6 +378,13 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   off = align256(off + (size_t)nb * 16);
   const size_t o_np = off;
   off = align256(off + (size_t)nb * 8);
+  const long long ng = (nb + 31) / 32;
+  const size_t o_gs = off;
+  off = align256(off + (size_t)ng * 8);
+  const size_t o_gp = off;
+  off = align256(off + (size_t)ng * 16);
+  const size_t o_gc = off;
+  off = align256(off + (size_t)(2 * ng + 1) * 4);
   const size_t o_sc = off;
   off = align256(off + 64);
   const size_t o_pf = off;
@@ -392,15 +403,18 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   a.off = (long long*)(b + o_off);
   a.n = (int*)(b + o_n);
   a.ab = (double2*)(b + o_ab);
+  a.ab32 = (float2*)(b + o_ab32);
   a.tile_h0 = (int*)(b + o_t);
   a.var = (double*)(b + o_var);
   a.dw = (double*)(b + o_dw);
   a.part = (double*)(b + o_part);
   a.npart = (long long*)(b + o_np);
-  // 64 bytes: the event count, three scalars, two tickets
+  a.gsum = (long long*)(b + o_gs);
+  a.gpart = (double2*)(b + o_gp);
+  a.gctr = (int*)(b + o_gc);
+  // 64 bytes: the event count, three scalars
   a.ncall_dev = (long long*)(b + o_sc);
   a.scal = (double*)(b + o_sc + 8);
-  a.tickets = (int*)(b + o_sc + 32);
   c->plus_fill = (GvPlusFill*)(b + o_pf);
   a.inv = (const double*)(b + o_tab);
   a.abtab = (const double2*)(b + o_tab + (size_t)GV_PLUS_NTAB * 8);
@@ -568,9 +582,8 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.plus = (mode == 0 && c->strat) ? 1 : 0;
   p.s = 0;
   p.nh = 0;
-  p.F = nullptr;
-  p.hc = nullptr;
-  p.seg = nullptr;
+  p.seg_h = nullptr;
+  p.seg_r = nullptr;
   int64_t cap = ncall;
   if (p.plus) {
     if (c->hist_nh > 0 || ncall < 8 || ncall > ((int64_t)1 << 30)) return VEGAS_EINVAL;
@@ -613,11 +626,9 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.cpart = (GvSlot*)w;
   if (p.plus) {
     w += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
-    p.F = (double*)w;
-    w += align256((size_t)cap * 8);
-    p.hc = (int*)w;
-    w += align256((size_t)cap * 4);
-    p.seg = (double2*)w;
+    p.seg_r = (double2*)w;
+    w += align256((size_t)(cap / GV_PLUS_SEG + 1) * 16);
+    p.seg_h = (double2*)w;
   }
   p.ept = c->ept_opt;
   return VEGAS_OK;
@@ -655,10 +666,11 @@ int ensure_allocation(vegas_ctx* c, const Plan& p) {
   f.magic = ~0ull / (unsigned long long)p.s;
   f.off = c->pa.off;
   f.ab = c->pa.ab;
+  f.ab32 = c->pa.ab32;
   f.tile_h0 = c->pa.tile_h0;
   f.ncall = c->pa.ncall_dev;
-  f.F = p.F;
-  f.hc = p.hc;
+  f.seg_h = p.seg_h;
+  f.seg_r = p.seg_r;
   // a pageable copy is staged before cudaMemcpyAsync returns
   GV_TRY(cudaMemcpyAsync(c->plus_fill, &f, sizeof f, cudaMemcpyHostToDevice, c->stream));
   if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;
@@ -671,6 +683,18 @@ int ensure_allocation(vegas_ctx* c, const Plan& p) {
   return VEGAS_OK;
 }
 
+// The side stream and its fork/join events (made once per context).
+int ensure_side(vegas_ctx* c) {
+  if (c->side) return VEGAS_OK;
+  int least = 0, greatest = 0;
+  GV_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  c->pa.prio = greatest;
+  GV_TRY(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest));
+  GV_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  GV_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  return VEGAS_OK;
+}
+
 int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool capture) {
   const unsigned flags = capture ? cudaEventRecordExternal : 0u;
   const size_t rsmem = gv::reduce_smem_bytes(c->nbins);
@@ -680,22 +704,32 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
   for (int k = 0; k < p.itmx; ++k) {
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0, k));
+    if (p.plus) {
+      // fork: the hypercube statistics need the fill's segments only
+      GV_TRY(cudaEventRecord(c->ev_fork, c->stream));
+      GV_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
+    // (VEGAS+: a plain launch, so that its CTAs do not hold the SMs while
+    // they wait for the fill; the more urgent statistics beside it go first)
     if (p.slot_major)
-      GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl));
+      GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl && !p.plus));
     else
       GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
     if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
     if (p.plus) {
-      // the hypercubes' statistics (sigma_k, the stage's combination), then
-      // the next iteration's allocation and its layout
+      // beside the reduce: the hypercubes' statistics from the fill's
+      // segments (sigma_k; the stage's combination with the reduce's I_k),
+      // then the next iteration's allocation and its layout; joined before
+      // the next fill
       const GvPlusArgs a = plus_args(c, p, k);
-      GV_TRY(gv::launch_plus_seg(a, c->stream, pdl));
-      GV_TRY(gv::launch_plus_stats(a, c->stream, pdl));
+      GV_TRY(gv::launch_plus_stats(a, c->side, false));
       if (c->adapt) {
-        GV_TRY(gv::launch_plus_alloc(a, c->stream, pdl));
-        GV_TRY(gv::launch_plus_layout(a, c->stream, pdl));
+        GV_TRY(gv::launch_plus_alloc(a, c->side, pdl));
+        GV_TRY(gv::launch_plus_layout(a, c->side, pdl));
       }
+      GV_TRY(cudaEventRecord(c->ev_join, c->side));
+      GV_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
@@ -741,6 +775,8 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   if (st) return st;
   if (p.plus) {
     st = ensure_allocation(c, p);
+    if (st) return st;
+    st = ensure_side(c);
     if (st) return st;
   }
   if (p.nhist || p.plus) {
@@ -804,7 +840,7 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
       return st;
     }
     GV_TRY(ce);
-    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     GV_TRY(ie);
     c->graphs.push_back(g);
@@ -1012,6 +1048,9 @@ void vegas_free(vegas_ctx* c) {
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->hres) cudaFreeHost(c->hres);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;
 }
 
@@ -1118,16 +1157,20 @@ int vegas_strat_set(vegas_ctx* c, int64_t ncall, const int32_t* counts) {
   if (st) return st;
   st = upload_abtab(c, ncall, nh);
   if (st) return st;
-  // the counts, the per-CTA exclusive bases and the total; then the layout
-  const int64_t nb = (nh + 255) / 256;
-  std::vector<long long> base((size_t)nb);
+  // the counts, their sums per CTA of 256 hypercubes and per group of 32
+  // CTAs, and the total; then the layout
+  const int64_t nb = (nh + 255) / 256, ng = (nb + 31) / 32;
+  std::vector<long long> agg((size_t)nb, 0), gsum((size_t)ng, 0);
   long long run = 0;
   for (int64_t b = 0; b < nb; ++b) {
-    base[(size_t)b] = run;
-    for (int64_t h = b * 256; h < std::min(nh, (b + 1) * 256); ++h) run += counts[h];
+    for (int64_t h = b * 256; h < std::min(nh, (b + 1) * 256); ++h) agg[(size_t)b] += counts[h];
+    gsum[(size_t)(b / 32)] += agg[(size_t)b];
+    run += agg[(size_t)b];
   }
   GV_TRY(cudaMemcpyAsync(c->pa.n, counts, (size_t)nh * 4, cudaMemcpyHostToDevice, c->stream));
-  GV_TRY(cudaMemcpyAsync(c->pa.npart, base.data(), (size_t)nb * 8, cudaMemcpyHostToDevice,
+  GV_TRY(cudaMemcpyAsync(c->pa.npart, agg.data(), (size_t)nb * 8, cudaMemcpyHostToDevice,
+                         c->stream));
+  GV_TRY(cudaMemcpyAsync(c->pa.gsum, gsum.data(), (size_t)ng * 8, cudaMemcpyHostToDevice,
                          c->stream));
   GV_TRY(cudaMemcpyAsync(c->pa.ncall_dev, &run, 8, cudaMemcpyHostToDevice, c->stream));
   GvPlusArgs a = c->pa;

@@ -57,7 +57,10 @@ struct GvState {
   unsigned long long nonfinite_iter;  // non-finite weights of the running iteration
   unsigned long long nonfinite;       // non-finite weights of the stage
   int status;                         // device error word (0 = ok)
-  int pad;
+  // VEGAS+: arrivals at the end of a stage's last iteration of the reduce
+  // (I_k) and of the hypercube statistics (sigma_k), which run side by side;
+  // the second to arrive combines the stage and resets it
+  int join;
   double integral, error, chi2;
   double grad[GV_NGRAD], grad_err[GV_NGRAD];
   // the counter at the start of the running stage: the counter of its
@@ -93,7 +96,11 @@ struct GvGridLayout {
 // VEGAS+ data of the stratified fill: s strata per axis, nh = s^d
 // hypercubes; event e lies in the h with off[h] <= e < off[h+1]; tile t's
 // first hypercube is tile_h0[t]; ab[h] = (C/(nh n_h), sqrt(1/(nh n_h)));
-// *ncall events in all; F[e] receives J g of event e.
+// *ncall events in all.  Each GV_PLUS_SEG-event range r of the fill sums
+// J g and (J g)^2 over its run of each hypercube, in event order (its
+// segments): a hypercube's first segment goes to seg_h[h], and a segment that
+// continues a hypercube begun in an earlier range (only a range's first can)
+// to seg_r[r].
 struct GvPlusFill {
   int s;
   float inv_s;
@@ -101,10 +108,11 @@ struct GvPlusFill {
   unsigned long long magic;  // floor((2^64 - 1) / s)
   const long long* off;
   const double2* ab;
+  const float2* ab32;  // ab rounded to FP32 (the FP32 form)
   const int* tile_h0;
   const long long* ncall;
-  double* F;
-  int* hc;  // [events] the hypercube of each event
+  double2* seg_h;
+  double2* seg_r;
 };
 
 // Arguments of the fill kernels (forward and adjoint).
@@ -252,6 +260,28 @@ inline cudaError_t gv_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, si
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = pdl ? attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// The same with a scheduling priority (cudaDeviceGetStreamPriorityRange's
+// scale: lower is more urgent): among launches whose CTAs wait for room on
+// the SMs, the more urgent are placed first (a graph keeps it per node when
+// instantiated with cudaGraphInstantiateFlagUseNodePriority).
+template <typename... KArgs, typename... Args>
+inline cudaError_t gv_launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, bool pdl, int prio, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -451,7 +481,7 @@ struct GvHistArgs {
 };
 
 #define GV_PLUS_NTAB 4096  // per-count tables of the VEGAS+ kernels (larger counts: computed)
-#define GV_PLUS_SEG 8      // events per lane in the VEGAS+ segment sums
+#define GV_PLUS_SEG 4      // consecutive events per thread of the stratified fill (one range)
 
 // VEGAS+ after an iteration (see gv_plus.cu): per-hypercube statistics, the
 // next allocation, its layout.
@@ -464,30 +494,34 @@ struct GvPlusArgs {
   int k = 0, last = 0;       // iteration in the stage
   double inv_m1 = 0.0;       // 1 / (k) for chi2/dof at the last iteration
   double inv_nh2 = 0.0;      // 1 / nh^2
-  const double* F = nullptr; // [events] J g per event
-  const int* hc = nullptr;   // [events] hypercube per event
-  double2* seg = nullptr;    // [events] per GV_PLUS_SEG-event range: the sums of its
-                             // hypercube segments (sum F, sum F^2), in order
+  // the fill's segment sums (sum F, sum F^2): each hypercube's first, and
+  // per GV_PLUS_SEG-event range the one that continues an earlier hypercube
+  const double2* seg_h = nullptr;  // [nh]
+  const double2* seg_r = nullptr;  // [ranges]
   long long cap = 0;         // events the buffers hold
   long long* off = nullptr;  // [nh + 1] first event of each hypercube, then the count
   int* n = nullptr;          // [nh] events per hypercube
   double2* ab = nullptr;     // [nh] (C/(nh n_h), sqrt(1/(nh n_h)))
+  float2* ab32 = nullptr;    // [nh] the same rounded to FP32
   int* tile_h0 = nullptr;    // [n_tiles] hypercube of each tile's first event
   double* var = nullptr;     // [nh] sample variance of J g in each hypercube
   double* dw = nullptr;      // [nh] allocation weights v^(beta/2)
   double* part = nullptr;    // [CTAs][2] per-CTA sums of v/n and of the weights
-  long long* npart = nullptr;  // [CTAs] per-CTA sums of n, then their exclusive scan
+  // per CTA of kT = 256 hypercubes, per group of 32 CTAs
+  long long* npart = nullptr;  // [CTAs] the CTA's events of the next allocation
+  long long* gsum = nullptr;   // [groups] the group's events
+  double2* gpart = nullptr;    // [groups] the group's sums of v/n and of the weights
+  int* gctr = nullptr;         // [2 groups + 1] arrival counters (zero between uses)
   long long* ncall_dev = nullptr;  // events of the allocation
   double* scal = nullptr;    // [2] sigma_k^2, the weights' sum D
   const double* inv = nullptr;    // [GV_PLUS_NTAB] 1/n (entry 0 unused)
   const double2* abtab = nullptr; // [GV_PLUS_NTAB] ab for n_h = n (C and nh of the allocation)
-  int* tickets = nullptr;    // [2] last-CTA tickets (zero between uses)
+  int prio = 0;              // launch priority (the most urgent of the device)
   double* per_iter = nullptr;  // [itmx][2]
   GvState* st = nullptr;
 };
 
 namespace gv {
-cudaError_t launch_plus_seg(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl);

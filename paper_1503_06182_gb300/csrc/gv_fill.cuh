@@ -19,9 +19,14 @@
 //           atomics (32-bit shared atomics run several times faster than
 //           64-bit ones here, and 10 bits of headroom cover the 1024 events of
 //           a tile).
-// With VEGAS+ (PLUS), each event first finds its hypercube and takes
-// stratified words; the estimate's weight is F C/(nh n_h) and the bins'
-// quantity F sqrt(1/(nh n_h)), F = J g, which is also stored per event.
+// With VEGAS+ (PLUS), each thread takes GV_PLUS_SEG consecutive events (one
+// range): a binary search finds its first event's hypercube, the next events
+// step across hypercube boundaries (every hypercube holds at least 2 events),
+// and each event takes stratified words from its hypercube's digits.  The
+// estimate's weight is F C/(nh n_h) and the bins' quantity F sqrt(1/(nh n_h)),
+// F = J g.  The thread also sums F and F^2 over the run of each hypercube in
+// its range, in event order (the range's segments), which the hypercube
+// statistics add up after the iteration.
 // With a histogram of the observable (HIST), every event with w != 0 also
 // adds w and w^2 to its observable's bin, in the same limb scheme: a per-bin
 // exponent from pass 1, then w^2 as three unsigned 22-bit limbs and w as two
@@ -304,7 +309,8 @@ struct GvFillSmem {
 
 // VEGAS+: the hypercube of the tile's local event `local` (the last window
 // entry at or below it), and the stratified words of hypercube h:
-// r' = floor((c_a 2^32 + r_a) / s) with c_a the base-s digits of h.
+// r' = floor((c_a 2^32 + r_a) / s) with c_a the base-s digits of h (the
+// next two functions).
 __device__ __forceinline__ int gv_plus_cube(const int* s_off, int local) {
   int lo = 0, hi = GV_PLUS_WIN;
   while (hi - lo > 1) {
@@ -317,23 +323,46 @@ __device__ __forceinline__ int gv_plus_cube(const int* s_off, int local) {
   return lo;
 }
 
+// A range's segment of window hypercube j (sums s1, s2): the hypercube's
+// first segment if it begins in the range (at or after local event r0),
+// else the range's continuation of it.
+__device__ __forceinline__ void gv_plus_put_segment(const GvPlusFill* pf, const int* s_off,
+                                                    long long h0, int j, long long tile0, int r0,
+                                                    double s1, double s2) {
+  if (s_off[j] >= r0)
+    pf->seg_h[h0 + j] = make_double2(s1, s2);
+  else
+    pf->seg_r[(tile0 + r0) / GV_PLUS_SEG] = make_double2(s1, s2);
+}
+
+// The base-s digits c_a of hypercube h (h < 2^22 is exact in FP32: h / s
+// from a float estimate, corrected to the floor).
 template <int MAXD>
-__device__ __forceinline__ void gv_plus_words(unsigned h, int d, unsigned s, float inv_s,
-                                              unsigned long long magic, uint32_t (&r)[MAXD]) {
+__device__ __forceinline__ void gv_plus_digits(unsigned h, int d, unsigned s, float inv_s,
+                                               unsigned (&c)[MAXD]) {
 #pragma unroll
   for (int ax = 0; ax < MAXD; ++ax) {
     if (ax < d) {
-      // h / s from a float estimate (h < 2^22 is exact in FP32), corrected to the floor
       unsigned q = (unsigned)((float)h * inv_s);
       if (q * s > h)
         --q;
       else if ((q + 1u) * s <= h)
         ++q;
-      const unsigned c = h - q * s;
+      c[ax] = h - q * s;
       h = q;
-      // floor(X / s), X = c 2^32 + r < 2^54: the product with floor((2^64-1)/s)
-      // is the quotient or one less
-      const unsigned long long X = ((unsigned long long)c << 32) | r[ax];
+    }
+  }
+}
+
+// The stratified words floor(X / s), X = c_a 2^32 + r_a < 2^54: the product
+// with floor((2^64-1)/s) is the quotient or one less.
+template <int MAXD>
+__device__ __forceinline__ void gv_plus_strat(const unsigned (&c)[MAXD], int d, unsigned s,
+                                              unsigned long long magic, uint32_t (&r)[MAXD]) {
+#pragma unroll
+  for (int ax = 0; ax < MAXD; ++ax) {
+    if (ax < d) {
+      const unsigned long long X = ((unsigned long long)c[ax] << 32) | r[ax];
       unsigned long long t = __umul64hi(X, magic);
       if ((t + 1ull) * s <= X) ++t;
       r[ax] = (uint32_t)t;
@@ -479,6 +508,19 @@ __device__ __forceinline__ bool gv_finite_bits(unsigned long long absbits) {
   return absbits < 0x7FF0000000000000ull;
 }
 
+// The scale exponent of the weight u 2^e (gv_scale_exp of the double) and
+// whether that double is finite.
+__device__ __forceinline__ int gv_direct_scale(unsigned u, int e, bool& fin) {
+  const GvDirect dd = gv_direct(u, e);
+  if (dd.direct) {
+    fin = true;
+    return dd.e2 + 24;
+  }
+  const unsigned long long ab = gv_abs_bits(gv_weight_bits(u, e));
+  fin = gv_finite_bits(ab);
+  return gv_scale_exp(ab);
+}
+
 // ---------------------------------------------------------------------------
 // Forward fill of one tile: channel 0 = w, with per-bin sums of w^2.  The grid
 // of the integration must be staged and the histogram zeroed (both followed
@@ -522,23 +564,34 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   GvConst<Real, GvTraits<IG>::NK> K;
   K.load(a.kconst);
 
-  // FP32 form without VEGAS+: each weight is kept as its FP32 product and
-  // Jacobian exponent and summed through gv_direct
-  constexpr bool DIRECT = sizeof(Real) == 4 && !PLUS;
+  // FP32 form: each weight is kept as its FP32 product and Jacobian exponent
+  // and summed through gv_direct (VEGAS+: the estimate's weight in wp, the
+  // bins' quantity in wq)
+  constexpr bool DIRECT = sizeof(Real) == 4;
   const long long tile0 = tile * GV_TILE;
   [[maybe_unused]] double w[EPT];
-  [[maybe_unused]] unsigned wp[EPT];
+  [[maybe_unused]] unsigned wp[EPT], wq[EPT];
   [[maybe_unused]] int wj[EPT];
   GvBinStore<MAXD> bs[EPT];
   unsigned long long mx = 0ull;
   int mE = GV_EMPTY;  // the direct form's largest weight scale
   unsigned long long nbad = 0ull;
+  // VEGAS+: this thread's range (events tile0 + tid EPT ..), the window index
+  // of its current hypercube, that hypercube's digits and factors, and the
+  // running segment sums
+  static_assert(!PLUS || EPT == GV_PLUS_SEG, "a stratified fill thread holds one range");
+  [[maybe_unused]] int jc = PLUS ? gv_plus_cube(s_off, tid * EPT) : 0;
+  [[maybe_unused]] int jcur = -1;  // the open segment's window index
+  [[maybe_unused]] double sg1 = 0.0, sg2 = 0.0;
+  constexpr bool KEEP_DIGITS = MAXD <= 4;  // registers to spare only for few axes
+  [[maybe_unused]] unsigned cdig[MAXD];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int local = k * B + tid;
+    const int local = PLUS ? tid * EPT + k : k * B + tid;
     const long long ev = tile0 + local;
     if constexpr (DIRECT) {
       wp[k] = 0u;
+      wq[k] = 0u;
       wj[k] = 0;
     } else {
       w[k] = 0.0;
@@ -561,10 +614,19 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       } else {
         gv_event_words<MAXD>(a.seed, it, a.batch, (unsigned long long)ev, d, r);
       }
-      long long hc = 0;
       if constexpr (PLUS) {
-        hc = h0 + gv_plus_cube(s_off, local);
-        gv_plus_words<MAXD>((unsigned)hc, d, (unsigned)pf->s, pf->inv_s, pf->magic, r);
+        while (jc + 1 < GV_PLUS_WIN && s_off[jc + 1] <= local) ++jc;
+        if (jc != jcur) {  // a new hypercube: close the previous segment
+          if (jcur >= 0) gv_plus_put_segment(pf, s_off, h0, jcur, tile0, tid * EPT, sg1, sg2);
+          jcur = jc;
+          sg1 = 0.0;
+          sg2 = 0.0;
+          if (KEEP_DIGITS)
+            gv_plus_digits<MAXD>((unsigned)(h0 + jc), d, (unsigned)pf->s, pf->inv_s, cdig);
+        }
+        if (!KEEP_DIGITS)
+          gv_plus_digits<MAXD>((unsigned)(h0 + jc), d, (unsigned)pf->s, pf->inv_s, cdig);
+        gv_plus_strat<MAXD>(cdig, d, (unsigned)pf->s, pf->magic, r);
       }
       Real x[MAXD];
       int bin[MAXD];
@@ -576,22 +638,34 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       if constexpr (DIRECT) {
         const unsigned u = __float_as_uint(__fmul_rn(J.m, g));
         if ((u & 0x7FFFFFFFu) != 0u) {
-          const GvDirect dd = gv_direct(u, J.e);
-          bool fin = true;
-          int Ev;
-          if (dd.direct) {
-            Ev = dd.e2 + 24;  // gv_scale_exp of the double
-          } else {
-            const unsigned long long ab = gv_abs_bits(gv_weight_bits(u, J.e));
-            fin = gv_finite_bits(ab);
-            Ev = gv_scale_exp(ab);
+          // VEGAS+: the estimate's weight u a_h and the bins' quantity u b_h,
+          // FP32 products with the hypercube's factors rounded to FP32
+          unsigned uw = u, uq = u;
+          if constexpr (PLUS) {
+            const float2 f = pf->ab32[h0 + jc];
+            uw = __float_as_uint(__fmul_rn(__uint_as_float(u), f.x));
+            uq = __float_as_uint(__fmul_rn(__uint_as_float(u), f.y));
           }
-          if (fin) {
-            wp[k] = u;
+          bool fin, finq = true;
+          const int Ev = gv_direct_scale(uw, J.e, fin);
+          int Eq = Ev;
+          if constexpr (PLUS) Eq = gv_direct_scale(uq, J.e, finq);
+          if (fin && finq) {
+            if constexpr (PLUS) {
+              // F = u 2^e, widened exactly, into the segment (a rounded
+              // product, then the sum, as the statistics define them: the
+              // variance cancels where a hypercube's values are nearly equal)
+              double Fv = gv_weight_bits(u, J.e);
+              Fv = gv_finite_bits(gv_abs_bits(Fv)) ? Fv : 0.0;
+              sg1 += Fv;
+              sg2 += Fv * Fv;
+              wq[k] = uq;
+            }
+            wp[k] = uw;
             wj[k] = J.e;
-            if (Ev != GV_EMPTY) {
-              mE = max(mE, Ev);
-              const int F = Ev + GV_BINE_OFF;
+            if (Ev != GV_EMPTY) mE = max(mE, Ev);
+            if (Eq != GV_EMPTY) {
+              const int F = Eq + GV_BINE_OFF;
 #pragma unroll
               for (int ax = 0; ax < MAXD; ++ax)
                 if (ax < d) atomicMax(ebin + ax * N + bin[ax], F);
@@ -606,11 +680,14 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       double wv = gv_weight(J, g);
       [[maybe_unused]] double qk = 0.0;
       if constexpr (PLUS) {
-        // F = J g: stored for the hypercube statistics (0 if not finite); the
-        // estimate's weight F C/(nh n_h), the bins' F sqrt(1/(nh n_h))
-        pf->F[ev] = gv_finite_bits(gv_abs_bits(wv)) ? wv : 0.0;
-        pf->hc[ev] = (int)hc;
-        const double2 f = pf->ab[hc];
+        // F = J g into the segment (0 if not finite); the estimate's weight
+        // F C/(nh n_h), the bins' F sqrt(1/(nh n_h))
+        // (a rounded product, then the sum, as the statistics define them: the
+        // variance cancels where a hypercube's values are nearly equal)
+        const double Fv = gv_finite_bits(gv_abs_bits(wv)) ? wv : 0.0;
+        sg1 += Fv;
+        sg2 += Fv * Fv;
+        const double2 f = pf->ab[h0 + jc];
         qk = wv * f.y;
         wv = wv * f.x;
       }
@@ -637,6 +714,10 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       }
     }
   }
+  if constexpr (PLUS) {
+    // the range's last segment and its first hypercube
+    if (jcur >= 0) gv_plus_put_segment(pf, s_off, h0, jcur, tile0, tid * EPT, sg1, sg2);
+  }
   // the tile's scale (the barrier also orders ebin)
   int E;
   if constexpr (DIRECT)
@@ -650,11 +731,11 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     for (int k = 0; k < EPT; ++k) {
       bool any;
       if constexpr (DIRECT)
-        any = (wp[k] & 0x7FFFFFFFu) != 0u;
+        any = (wp[k] & 0x7FFFFFFFu) != 0u || (PLUS && (wq[k] & 0x7FFFFFFFu) != 0u);
       else
         any = gv_abs_bits(w[k]) != 0ull || (PLUS && gv_abs_bits(qv[k]) != 0ull);
       if (any) {
-        const int local = k * B + tid;
+        const int local = PLUS ? tid * EPT + k : k * B + tid;
         // bins: w^2 (VEGAS+: q^2) at its bin's scale, a 56-bit value, as three
         // 22-bit limbs, from P = floor(m^2 2^-42) of its 53-bit significand m
         // and c = 2 e2 + 98 + 2 GV_BINE_OFF
@@ -677,8 +758,21 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
             if (dw.m != 0ull) {
               s1 = add128(s1, gv_fixed_tile(dw, E));
               s2 = add128(s2, gv_square_tile(dw, P, E));
-            } else {
+            } else if (!PLUS) {
               continue;  // below the FP64 range: zero
+            }
+          }
+          if constexpr (PLUS) {
+            // the bins' terms from the bins' quantity
+            const GvDirect dq = gv_direct(wq[k], wj[k]);
+            if (dq.direct) {
+              P = ((unsigned long long)dq.m * dq.m) << 16;
+              c = 2 * (dq.e2 - 29) + 98 + 2 * GV_BINE_OFF;
+            } else {
+              const GvDecoded q = gv_decode(gv_weight_bits(wq[k], wj[k]));
+              if (q.m == 0ull) continue;  // below the FP64 range: zero
+              P = gv_square_hi(q.m);
+              c = 2 * q.e2 + 98 + 2 * GV_BINE_OFF;
             }
           }
         } else {
@@ -789,7 +883,9 @@ __device__ __forceinline__ void gv_tile_words(const GvFillArgs& a, uint32_t it, 
 
 // Minimum resident CTAs per SM in the fill's launch bound (0: none), i.e. its
 // register budget.  FP32 fills of at most 8 axes: 64 registers at any width
-// (the stratified fill included).  FP32 fills of up to 16 axes without
+// (the stratified fill of at most 4 axes included; the stratified fill of up
+// to 8 axes, which keeps its range's segment sums, takes 80 with three
+// 256-thread CTAs: at 64 it spilled ~250 bytes).  FP32 fills of up to 16 axes without
 // VEGAS+, 4 events per thread: three 256-thread CTAs, 80 registers (111 for
 // the 13-axis NLO-shaped weight unbounded).  FP64 fills: none (they would
 // spill).
@@ -797,6 +893,7 @@ template <typename Real, int EPT, int MAXD, bool PLUS>
 struct GvFillBlocks {
   static constexpr int B = GV_TILE / EPT;
   static constexpr int value = sizeof(Real) != 4       ? 0
+                               : (PLUS && MAXD == 8)   ? 3
                                : MAXD <= 8             ? 65536 / (64 * B)
                                : (!PLUS && EPT == 4)   ? 3
                                                        : 0;

@@ -1,22 +1,25 @@
 // gv_plus.cu -- VEGAS+ (adaptive stratified sampling on the VEGAS map;
 // Lepage, J. Comput. Phys. 439 (2021) 110386, a later form of the VEGAS
-// method cited in Section 2.1) after each iteration:
-//   seg:    each lane sums J g and its square over GV_PLUS_SEG consecutive
-//           events, in event order, split where the hypercube changes (every
-//           lane does the same number of steps: the FP64 pipe, which this chip
-//           has little of, does no work for idle lanes);
+// method cited in Section 2.1) after each iteration.  The stratified fill has
+// left the sums of J g and its square over each GV_PLUS_SEG-event range's run
+// of each hypercube (its segments, in event order): a hypercube's first
+// segment at its index, a range's continuation of an earlier one at the
+// range's.
 //   stats:  one thread per hypercube adds its segments in range order, then
 //           forms its sample variance v_h, v_h/n_h and the allocation weight
 //           v_h^(beta/2) (divisions by n and n - 1 as products with tabulated
 //           reciprocals: FP64 division is a long sequence on the FP64 pipe);
 //           the CTA that completes the grid (ticket) forms
-//           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights, writes
-//           sigma_k and, at the last iteration, combines the stage;
+//           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights and
+//           writes sigma_k; at the stage's last iteration, of this CTA and the
+//           reduce (which runs beside these kernels) the second to arrive
+//           combines the stage;
 //   alloc:  n_h = max(2, floor(C d_h / D)) (floor(C/nh) if D = 0 or for the
 //           uniform start), per-CTA event counts; the completing CTA scans
 //           them (exact integers);
-//   layout: the offsets of the hypercubes, (C/(nh n_h), sqrt(1/(nh n_h))) and
-//           each tile's first hypercube for the next fill.
+//   layout: the offsets of the hypercubes, (C/(nh n_h), sqrt(1/(nh n_h))) (in
+//           FP64 and rounded to FP32, for the two forms' fills) and each
+//           tile's first hypercube for the next fill.
 // Every sum over hypercubes has a shape fixed by nh alone, every count is an
 // integer, and no CTA waits for another: the last one to arrive does the rest.
 #include "gv_combine.cuh"
@@ -24,6 +27,12 @@
 namespace {
 
 constexpr int kT = 256;  // threads per CTA, one hypercube each
+// 8 CTAs per SM (at most 32 registers): 1216 resident CTAs on 152 SMs hold a
+// million-event iteration's 234,256 hypercubes (916 CTAs) in one wave; at 6
+// (38 registers) its last four CTAs ran as a second wave, a whole CTA
+// lifetime later
+constexpr int kMinBlocks = 8;
+constexpr int kG = 32;  // CTAs per group of the two-level completion counters
 
 // v^(j/8) (beta = j/4) from correctly rounded operations only: v = t 2^(8q)
 // with t in [1/2, 128) rounded to FP32, three FP32 square roots, j - 1 FP32
@@ -68,20 +77,27 @@ __device__ __forceinline__ double plus_weight(double v, int j) {
   return __longlong_as_double(db + ((long long)(q * j) << 52));
 }
 
-// Sum over the CTA in a fixed order, with few FP64 instructions (this chip's
-// FP64 pipe is narrow): warp 0's lane l adds the values of threads 8l..8l+7
-// in order, then a butterfly over the warp.  The result is valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* s) {
+// Two sums over the CTA in a fixed order, with few FP64 instructions (this
+// chip's FP64 pipe is narrow) and one latency chain for both: warp 0's lane l
+// adds the values of threads 8l..8l+7 in order, then a butterfly over the
+// warp.  The result is valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* s) {
   s[threadIdx.x] = v;
   __syncthreads();
-  double r = 0.0;
+  double2 r = make_double2(0.0, 0.0);
   if (threadIdx.x < 32) {
-    const double* q = s + 8 * threadIdx.x;
+    const double2* q = s + 8 * threadIdx.x;
     r = q[0];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) r += q[i];
+    for (int i = 1; i < 8; ++i) {
+      r.x += q[i].x;
+      r.y += q[i].y;
+    }
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) r += __shfl_xor_sync(0xffffffffu, r, m);
+    for (int m = 16; m > 0; m >>= 1) {
+      r.x += __shfl_xor_sync(0xffffffffu, r.x, m);
+      r.y += __shfl_xor_sync(0xffffffffu, r.y, m);
+    }
   }
   __syncthreads();
   return r;
@@ -117,63 +133,77 @@ __device__ __noinline__ void plus_recips(double n, double* inv_n, double* inv_m1
   *inv_m1 = 1.0 / (n - 1.0);
 }
 
-// The completing CTA: the sum of nb per-CTA values in CTA order, each thread
+// Per-CTA values a completing CTA's thread holds in registers (up to kT kR
+// CTAs: all loads in flight at once; more are read in a loop).
+constexpr int kR = 4;
+
+// The completing CTA: the sums of nb per-CTA pairs in CTA order, each thread
 // taking a contiguous run, then the fixed tree.
-__device__ __forceinline__ double sum_parts(const double* part, int stride, int nb, double* s) {
+__device__ __forceinline__ double2 sum_parts2(const double2* part, int nb, double2* s) {
   const int chunk = (nb + kT - 1) / kT;
   const int i0 = threadIdx.x * chunk, i1 = min(nb, i0 + chunk);
-  double v = 0.0;
-  for (int i = i0; i < i1; ++i) v += __ldcg(part + (size_t)i * stride);
-  return block_sum(v, s);
+  double2 v = make_double2(0.0, 0.0);
+  if (chunk <= kR) {
+    double2 p[kR];
+#pragma unroll
+    for (int q = 0; q < kR; ++q) p[q] = i0 + q < i1 ? __ldcg(part + i0 + q) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kR; ++q) {
+      if (i0 + q < i1) {
+        v.x += p[q].x;
+        v.y += p[q].y;
+      }
+    }
+  } else {
+    for (int i = i0; i < i1; ++i) {
+      const double2 p = __ldcg(part + i);
+      v.x += p.x;
+      v.y += p.y;
+    }
+  }
+  return block_sum2(v, s);
+}
+
+// floor(x / D) with x / D rounded to nearest, as the allocation rule states
+// it, for x >= 0 and D > 0 with 1/D rounded to nearest given.  y = x (1/D)
+// lies within 3 units in the last place of the rounded quotient q, so when
+// no integer lies within 8 units of y, floor(q) = floor(y), read from y's
+// bits on the integer pipes; otherwise (equal weights put shares on
+// integers) the true division decides.
+__device__ __forceinline__ long long floor_quotient(double x, double D, double rD) {
+  const double y = x * rD;
+  const long long b = __double_as_longlong(y);
+  const int E = (int)(b >> 52) - 1023;  // y in [2^E, 2^(E+1)) (y >= 0)
+  if (E < 0) {
+    // below 1 (and 8 units clear of it): floor 0
+    if (b < __double_as_longlong(1.0) - 8) return 0;
+  } else if (E < 52) {
+    const unsigned long long M = ((unsigned long long)b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 52 - E;
+    const unsigned long long F = M & ((1ull << sh) - 1ull);  // fraction, in units of y
+    if (F > 8ull && (1ull << sh) - F > 8ull) return (long long)(M >> sh);
+  }
+  return (long long)floor(x / D);
 }
 
 }  // namespace
 
-// Range r = events [r K, r K + K) (K = GV_PLUS_SEG): its segments, one per
-// hypercube it meets, at seg[r K + j] for the j-th hypercube from hc[r K].
-__global__ void __launch_bounds__(kT) gv_plus_seg_kernel(const GvPlusArgs a) {
-  gv_wait_prior_grid();  // the fill's J g values and hypercubes
-  const long long ncall = __ldcg(a.ncall_dev);
-  const long long r = (long long)blockIdx.x * kT + threadIdx.x;
-  const long long e0 = r * GV_PLUS_SEG;
-  gv_allow_next_grid();
-  if (e0 >= ncall) return;
-  const long long e1 = e0 + GV_PLUS_SEG < ncall ? e0 + GV_PLUS_SEG : ncall;
-  int hp = a.hc[e0];
-  long long j = e0;
-  double s1 = 0.0, s2 = 0.0;
-  for (long long e = e0; e < e1; ++e) {
-    const int h = a.hc[e];
-    if (h != hp) {
-      a.seg[j++] = make_double2(s1, s2);
-      s1 = 0.0;
-      s2 = 0.0;
-      hp = h;
-    }
-    const double f = a.F[e];
-    s1 += f;
-    s2 += f * f;
-  }
-  a.seg[j] = make_double2(s1, s2);
-}
-
-__global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
-  __shared__ double s_red[kT];
+__global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_stats_kernel(const GvPlusArgs a) {
+  __shared__ double2 s_red[kT];
   __shared__ int s_last;
-  gv_wait_prior_grid();  // the segments and the reduce's I_k
+  gv_wait_prior_grid();  // the fill's segments and the reduce's I_k
   const long long h = (long long)blockIdx.x * kT + threadIdx.x;
   double vn = 0.0, dd = 0.0;
   if (h < a.nh) {
     const long long o = a.off[h];
     const int m = a.n[h];
-    // the hypercube's segments, range by range: in its first range it is the
-    // (h - hc[first event])-th segment; every later range starts inside it
+    // the hypercube's segments in event order: its first, then the
+    // continuations of every later range it reaches
+    double2 sg = a.seg_h[h];
     const long long r0 = o / GV_PLUS_SEG, r1 = (o + m - 1) / GV_PLUS_SEG;
-    const long long b0 = r0 * GV_PLUS_SEG;
-    double2 sg = a.seg[b0 + (h - a.hc[b0])];
     double s1 = sg.x, s2 = sg.y;
     for (long long r = r0 + 1; r <= r1; ++r) {
-      sg = a.seg[r * GV_PLUS_SEG];
+      sg = a.seg_r[r];
       s1 += sg.x;
       s2 += sg.y;
     }
@@ -193,132 +223,181 @@ __global__ void __launch_bounds__(kT) gv_plus_stats_kernel(const GvPlusArgs a) {
     a.dw[h] = dd;
   }
   gv_allow_next_grid();
-  vn = block_sum(vn, s_red);
-  dd = block_sum(dd, s_red);
+  const double2 sums = block_sum2(make_double2(vn, dd), s_red);
+  // two-level completion: the last CTA of each group of kG adds the group's
+  // sums (in CTA order, a fixed tree); the last group adds the groups'
+  const int b = blockIdx.x, nb = gridDim.x;
+  const int g = b / kG, ng = (nb + kG - 1) / kG, gsize = min(kG, nb - g * kG);
   if (threadIdx.x == 0) {
-    a.part[2 * (size_t)blockIdx.x] = vn;
-    a.part[2 * (size_t)blockIdx.x + 1] = dd;
+    reinterpret_cast<double2*>(a.part)[b] = sums;
     __threadfence();
-    s_last = atomicAdd(a.tickets, 1) == (int)gridDim.x - 1;
+    s_last = atomicAdd(a.gctr + g, 1) == gsize - 1;
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();  // the other CTAs' sums, published before their tickets
-  const int nb = gridDim.x;
-  const double V = sum_parts(a.part, 2, nb, s_red);
-  const double D = sum_parts(a.part + 1, 2, nb, s_red);
-  if (threadIdx.x == 0) {
-    a.tickets[0] = 0;
-    const double var_k = V * a.inv_nh2;
-    a.scal[0] = var_k;
-    a.scal[1] = D;
-    a.per_iter[2 * a.k + 1] = var_k > 0.0 ? sqrt(var_k) : 0.0;
-    __threadfence_block();
+  if (threadIdx.x < 32) {
+    __threadfence();  // the group's sums, published before their arrivals
+    double2 v = threadIdx.x < gsize ? __ldcg(reinterpret_cast<const double2*>(a.part) + g * kG + threadIdx.x)
+                                    : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+    }
+    if (threadIdx.x == 0) {
+      a.gpart[g] = v;
+      a.gctr[g] = 0;
+      __threadfence();
+      s_last = atomicAdd(a.gctr + ng, 1) == ng - 1;
+    }
   }
   __syncthreads();
-  if (a.last && threadIdx.x < 32)
+  if (!s_last) return;
+  __threadfence();  // the groups' sums, published before their arrivals
+  const double2 VD = sum_parts2(a.gpart, ng, s_red);
+  if (threadIdx.x == 0) {
+    a.gctr[ng] = 0;
+    const double var_k = VD.x * a.inv_nh2;
+    const double D = VD.y;
+    a.scal[0] = var_k;
+    a.scal[1] = D;
+    a.scal[2] = D > 0.0 ? 1.0 / D : 0.0;
+    a.per_iter[2 * a.k + 1] = var_k > 0.0 ? sqrt(var_k) : 0.0;
+    // the stage's last iteration: the reduce runs beside this kernel, and the
+    // second of the two to arrive combines the stage
+    s_last = 0;
+    if (a.last) {
+      __threadfence();  // sigma_k before the arrival
+      s_last = atomicAdd(&a.st->join, 1) == 1;
+    }
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();  // the reduce's I_k, published before its arrival
     combine_stage_warp(a.per_iter, 2, a.k + 1, a.inv_m1, a.st, false);
+    if (threadIdx.x == 0) a.st->join = 0;
+  }
 }
 
-__global__ void __launch_bounds__(kT) gv_plus_alloc_kernel(const GvPlusArgs a) {
+// The next allocation's count of hypercube h (h < nh): n_h = max(2,
+// floor(C d_h / D)), or floor(C / nh) everywhere for the uniform start or
+// when every weight is zero.
+__device__ __forceinline__ long long plus_count(const GvPlusArgs& a, long long h, double D,
+                                                double rD) {
+  long long k;
+  if (D > 0.0) {
+    // floor of the rounded quotient C d_h / D, as the rule states it: shares
+    // land on integers exactly (one hypercube, equal weights), where
+    // floor(x (1/D)) would fall an ulp short and one event lower
+    k = floor_quotient((double)a.ncall * __ldcg(a.dw + h), D, rD);
+  } else {
+    k = a.ncall / a.nh;
+  }
+  return k > 2 ? k : 2;
+}
+
+// Hypercube h's layout from its count m and first event o: its offset, its
+// factors (C/(nh m), sqrt(1/(nh m))) in FP64 and FP32, the tiles whose first
+// event lies in it, and after the last hypercube the total and the tiles
+// past it.
+__device__ __forceinline__ void plus_layout_one(const GvPlusArgs& a, long long h, long long m,
+                                                long long o) {
+  a.off[h] = o;
+  double2 f;
+  if (m < GV_PLUS_NTAB) {
+    f = __ldg(a.abtab + m);
+  } else {
+    const double nhd = (double)a.nh * (double)m;
+    f = make_double2((double)a.ncall / nhd, sqrt(1.0 / nhd));
+  }
+  a.ab[h] = f;
+  a.ab32[h] = make_float2(__double2float_rn(f.x), __double2float_rn(f.y));
+  for (long long t = (o + GV_TILE - 1) / GV_TILE; t * GV_TILE < o + m && t < a.n_tiles; ++t)
+    a.tile_h0[t] = (int)h;
+  if (h == a.nh - 1) {
+    a.off[a.nh] = o + m;
+    *a.ncall_dev = o + m;
+    // tiles past the last event start in the last hypercube (they hold no event)
+    for (long long t = (o + m + GV_TILE - 1) / GV_TILE; t < a.n_tiles; ++t) a.tile_h0[t] = (int)h;
+  }
+}
+
+// Counts of the next allocation: per CTA their sum (agg); the last CTA of each
+// group of kG CTAs (a counter per group, so arrivals spread over many
+// addresses) adds its group's (gsum).  Nothing waits; the layout reads them
+// after this kernel.
+__global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_alloc_kernel(const GvPlusArgs a) {
   __shared__ long long s_scan[kT / 32];
   __shared__ int s_last;
   gv_wait_prior_grid();  // the weights and their sum
   const double D = a.uniform ? 0.0 : __ldcg(a.scal + 1);
-  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
+  const double rD = a.uniform ? 0.0 : __ldcg(a.scal + 2);
+  const int b = blockIdx.x, nb = gridDim.x;
+  const long long h = (long long)b * kT + threadIdx.x;
   long long m = 0;
   if (h < a.nh) {
-    long long k;
-    if (D > 0.0) {
-      // a true division, as the rule states it: shares land on integers
-      // exactly (one hypercube, equal weights), where a product with 1/D
-      // would fall an ulp short and floor one event lower
-      const double x = (double)a.ncall * __ldcg(a.dw + h) / D;
-      k = (long long)floor(x);
-    } else {
-      k = a.ncall / a.nh;
-    }
-    m = k > 2 ? k : 2;
+    m = plus_count(a, h, D, rD);
     a.n[h] = (int)m;
   }
   gv_allow_next_grid();
   long long tot;
   block_exscan(m, s_scan, &tot);
+  const int g = b / kG, gsize = min(kG, nb - g * kG);
+  int* ctr = a.gctr + ((nb + kG - 1) / kG) + 1 + g;
   if (threadIdx.x == 0) {
-    a.npart[blockIdx.x] = tot;
+    a.npart[b] = tot;
     __threadfence();
-    s_last = atomicAdd(a.tickets + 1, 1) == (int)gridDim.x - 1;
+    s_last = atomicAdd(ctr, 1) == gsize - 1;
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // exclusive scan of the per-CTA counts, in place
-  const int nb = gridDim.x;
-  const int chunk = (nb + kT - 1) / kT;
-  const int i0 = threadIdx.x * chunk, i1 = min(nb, i0 + chunk);
-  long long run = 0;
-  for (int i = i0; i < i1; ++i) run += __ldcg(a.npart + i);
-  long long all;
-  long long base = block_exscan(run, s_scan, &all);
-  for (int i = i0; i < i1; ++i) {
-    const long long v = __ldcg(a.npart + i);
-    a.npart[i] = base;
-    base += v;
-  }
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();  // the group's counts, published before their arrivals
+  long long v = threadIdx.x < gsize ? __ldcg(a.npart + g * kG + threadIdx.x) : 0ll;
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) v += __shfl_xor_sync(0xffffffffu, v, k);
   if (threadIdx.x == 0) {
-    a.tickets[1] = 0;
-    *a.ncall_dev = all;
+    a.gsum[g] = v;
+    *ctr = 0;
   }
 }
 
-__global__ void __launch_bounds__(kT) gv_plus_layout_kernel(const GvPlusArgs a) {
+// The layout: CTA b's first event is the sum of the groups before its group
+// (gsum) and of the CTAs before it in its group (agg), then each hypercube's
+// by the CTA's scan.
+__global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_layout_kernel(const GvPlusArgs a) {
   __shared__ long long s_scan[kT / 32];
-  gv_wait_prior_grid();  // the counts and the per-CTA bases
-  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
+  gv_wait_prior_grid();  // the counts and their per-CTA and per-group sums
+  const int b = blockIdx.x, g = b / kG;
+  const long long h = (long long)b * kT + threadIdx.x;
   const long long m = h < a.nh ? (long long)a.n[h] : 0ll;
-  long long tot;
-  const long long o = __ldcg(a.npart + blockIdx.x) + block_exscan(m, s_scan, &tot);
-  if (h < a.nh) {
-    a.off[h] = o;
-    if (m < GV_PLUS_NTAB) {
-      a.ab[h] = __ldg(a.abtab + m);
-    } else {
-      const double nhd = (double)a.nh * (double)m;
-      a.ab[h] = make_double2((double)a.ncall / nhd, sqrt(1.0 / nhd));
-    }
-    // the tiles whose first event lies in this hypercube
-    for (long long t = (o + GV_TILE - 1) / GV_TILE; t * GV_TILE < o + m; ++t)
-      a.tile_h0[t] = (int)h;
-    if (h == a.nh - 1) {
-      a.off[a.nh] = o + m;
-      // tiles past the last event start in the last hypercube (they hold no event)
-      for (long long t = (o + m + GV_TILE - 1) / GV_TILE; t < a.n_tiles; ++t)
-        a.tile_h0[t] = (int)h;
-    }
-  }
+  // thread t adds the groups t, t + kT, .. below g and, the CTA t - (kT - kG)
+  // of its group below b
+  long long pre = 0;
+  for (int q = threadIdx.x; q < g; q += kT) pre += __ldcg(a.gsum + q);
+  const int c = threadIdx.x - (kT - kG);
+  if (c >= 0 && g * kG + c < b) pre += __ldcg(a.npart + g * kG + c);
+  long long all, tot;
+  block_exscan(pre, s_scan, &all);  // all: the CTA's first event
+  const long long o = all + block_exscan(m, s_scan, &tot);
+  gv_allow_next_grid();
+  if (h < a.nh) plus_layout_one(a, h, m, o);
 }
 
 namespace gv {
 
-cudaError_t launch_plus_seg(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
-  const long long ranges = (a.cap + GV_PLUS_SEG - 1) / GV_PLUS_SEG;
-  const unsigned nb = (unsigned)((ranges + kT - 1) / kT);
-  return gv_launch(gv_plus_seg_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
-}
-
 cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
   const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
-  return gv_launch(gv_plus_stats_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+  return gv_launch_prio(gv_plus_stats_kernel, dim3(nb), dim3(kT), 0, s, pdl, a.prio, a);
 }
 
 cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
   const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
-  return gv_launch(gv_plus_alloc_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+  return gv_launch_prio(gv_plus_alloc_kernel, dim3(nb), dim3(kT), 0, s, pdl, a.prio, a);
 }
 
 cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
   const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
-  return gv_launch(gv_plus_layout_kernel, dim3(nb), dim3(kT), 0, s, pdl, a);
+  return gv_launch_prio(gv_plus_layout_kernel, dim3(nb), dim3(kT), 0, s, pdl, a.prio, a);
 }
 
 }  // namespace gv

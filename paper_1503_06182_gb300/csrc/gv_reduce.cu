@@ -188,7 +188,7 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
       mean_sigma(__ldcg(a.sums + 2 * lane), __ldcg(a.sums + 2 * lane + 1), a.inv_c, a.inv_cm1,
                  &I, &s);
       rec[0] = I;
-      rec[1] = s;
+      if (!a.plus) rec[1] = s;  // VEGAS+: sigma_k comes from the hypercube statistics
       if (a.host_rec) {
         a.host_rec[(size_t)a.k * stride + 2 * lane] = I;
         a.host_rec[(size_t)a.k * stride + 2 * lane + 1] = s;
@@ -196,6 +196,21 @@ __device__ void finalize_iteration(const GvReduceArgs& a, int tid, int nthr, int
     }
     __syncwarp();
     if (a.last && !a.plus) combine_stage_warp(a.per_iter, stride, a.k + 1, a.inv_m1, st, a.mode != 0);
+    if (a.last && a.plus) {
+      // the hypercube statistics run beside this kernel: the second of the
+      // two to finish the stage's last iteration combines it
+      int t = 0;
+      if (lane == 0) {
+        __threadfence();  // this iteration's I_k before the arrival
+        t = atomicAdd(&st->join, 1);
+      }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t == 1) {
+        __threadfence();  // the statistics' sigma_k, published before their arrival
+        combine_stage_warp(a.per_iter, stride, a.k + 1, a.inv_m1, st, false);
+        if (lane == 0) st->join = 0;
+      }
+    }
     if (lane == 0) {
       const unsigned long long nf = __ldcg(&st->nonfinite_iter);
       st->nonfinite = (a.k == 0 ? 0ull : st->nonfinite) + nf;

@@ -1,9 +1,10 @@
 """GPU VEGAS+ (adaptive stratified sampling) against the oracle, through the C ABI.
 
 Each iteration is compared from the same state (grid, allocation, iteration
-counter): the estimate and its error to 1e-12, the refined grid to 1e-12,
-the per-hypercube variances to 1e-11 plus 1e-13 of their scale (the variance
-formula cancels where a hypercube's values are nearly equal).  The next
+counter): the estimate to 1e-12, the refined grid to 1e-12, the
+per-hypercube variances to 1e-11 plus 1e-13 of their scale (the variance
+formula cancels where a hypercube's values are nearly equal), and the error
+sigma_k to the bound those variances' tolerance puts on it.  The next
 allocation is the oracle's allocation rule applied to the GPU's own
 variances, exactly; against the oracle's own allocation it differs by at most
 one event in few hypercubes (those whose weights the small variance
@@ -44,6 +45,23 @@ def var_agrees(got, ref, alloc):
     assert np.all(np.abs(got - ref.var) <= 1e-11 * ref.var + 1e-13 * scale)
 
 
+def per_agrees(per, ref, alloc):
+    """(I_k, sigma_k) of one iteration: I_k to 1e-12 (exact sums rounded
+    once); sigma_k^2 = sum_h v_h/n_h / NH^2 to the sum of the variances' own
+    bound (var_agrees) over n_h NH^2.  The GPU adds a hypercube's values in
+    4-event segments where the definition adds them one by one, and v_h's
+    cancellation turns those few-ulp differences into 1e-11 of sigma_k where
+    a hypercube's values are nearly equal (one axis, 262144 strata)."""
+    per = np.asarray(per, float).reshape(-1, 2)[-1]
+    rp = np.asarray(ref.per_iter, float).reshape(-1, 2)[-1]
+    assert abs(per[0] - rp[0]) <= 1e-12 * abs(rp[0])
+    n = np.asarray(alloc, float)
+    nh = len(n)
+    dv = 1e-11 * ref.var + 1e-13 * ref.mean ** 2 * n / (n - 1)
+    bound = np.sum(dv / n) / float(nh) ** 2
+    assert abs(per[1] ** 2 - rp[1] ** 2) <= bound + 1e-12 * rp[1] ** 2
+
+
 def gpu_state(iid, params, ndim, nbins, ncall, warm, *, precision="fp64", **opts):
     g = v.Vegas(ndim, nbins, 1234, precision=precision)
     for k, val in opts.items():
@@ -68,7 +86,7 @@ def test_plus_iterations_match_oracle(name, ncall):
             ref = oracle.iterate_plus(ndim, nbins, 1234, ncall, 1, iid, params, edges=edges,
                                       alloc=alloc, iteration=k)
             assert s == s2 == ref.nstrat
-            assert rel(per, ref.per_iter) < 1e-12, k
+            per_agrees(per, ref, alloc)
             assert np.max(np.abs(g.grid - ref.edges)) < 1e-12, k
             var_agrees(var, ref, alloc)
             # the allocation rule on the GPU's own variances, exactly (the FP32
@@ -99,7 +117,7 @@ def test_plus_first_stage_and_combination_match_oracle():
     finally:
         g.close()
     ref = oracle.iterate_plus(ndim, nbins, 1234, 50_000, 1, iid, params)
-    assert rel(per[0], ref.per_iter[0]) < 1e-12
+    per_agrees(per[0], ref, np.full(len(ref.var), 50_000 // len(ref.var)))
     Io, eo, co = oracle.combine(per[:, 0], per[:, 1])
     assert rel(I, Io) < 1e-12 and rel(e, eo) < 1e-12 and abs(c - co) < 1e-10 * max(co, 1)
 
@@ -159,7 +177,7 @@ def test_plus_strat_set_and_validation():
         I, e, c, per, _ = g.iterate(4000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS)
         ref = oracle.iterate_plus(2, 20, 3, 4000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS, alloc=counts,
                                   adapt=False)
-        assert rel(per, ref.per_iter) < 1e-12
+        per_agrees(per, ref, counts)
         with pytest.raises(v.VegasError):  # no histogram with VEGAS+
             g.hist_set(10, 0.0, 1.0)
             g.iterate(4000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS)
@@ -216,7 +234,7 @@ def test_plus_extreme_shapes_match_oracle(ndim, ncall):
     ref = oracle.iterate_plus(ndim, nbins, 1234, ncall, 1, iid, params, edges=edges, alloc=alloc,
                               iteration=2)
     assert s == ref.nstrat and len(alloc) == s ** ndim
-    assert rel(per, ref.per_iter) < 1e-12
+    per_agrees(per, ref, alloc)
     var_agrees(var, ref, alloc)
     assert np.array_equal(alloc2, oracle.plus_allocate(ncall, var))
 
@@ -234,7 +252,7 @@ def test_plus_damping_values_match_oracle(beta):
         g.close()
     ref = oracle.iterate_plus(ndim, nbins, 1234, 20_000, 1, iid, params, edges=edges, alloc=alloc,
                               iteration=2, beta=beta)
-    assert rel(per, ref.per_iter) < 1e-12
+    per_agrees(per, ref, alloc)
     var_agrees(var, ref, alloc)
     assert np.array_equal(alloc2, oracle.plus_allocate(20_000, var, beta=beta))
     if beta == 0.0:  # every hypercube weighs the same: the allocation stays uniform
