@@ -60,10 +60,10 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 82_944
+FILL_TRAFFIC_BYTES = 82_176
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "b3f77f4bf15475a9fdff658f70dec529ef87a84cb622883be74dfdc9936e7f41"
+FILL_SOURCES_SHA256 = "866d250c911d397b6e1f5b2d6f26025904e3a0ec302870c49114ce136e75a7a0"
 # HBM copy bandwidth measured by the driver on the GB300s (used when
 # MEASURED_PEAKS.json is absent: the profiling recipe's fallback)
 HBM_FALLBACK_GBS = 6800.0
