@@ -61,6 +61,11 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # the fill's sources are the ones captured (their SHA-256 below); otherwise the
 # traffic is reported as unknown (null).
 FILL_TRAFFIC_BYTES = 82_176
+# warp instructions of that launch (smsp__inst_executed.sum, same capture and
+# validity): the fill is issue-bound, so its instruction rate against one warp
+# instruction per cycle per SM sub-partition (4 per SM) is its binding roofline
+FILL_WARP_INSTRUCTIONS = 21_418_973
+SMSP_PER_SM = 4
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
 FILL_SOURCES_SHA256 = "866d250c911d397b6e1f5b2d6f26025904e3a0ec302870c49114ce136e75a7a0"
@@ -69,7 +74,7 @@ FILL_SOURCES_SHA256 = "866d250c911d397b6e1f5b2d6f26025904e3a0ec302870c49114ce136
 HBM_FALLBACK_GBS = 6800.0
 
 
-def _fill_traffic():
+def _fill_sources_captured():
     import hashlib
 
     h = hashlib.sha256()
@@ -78,8 +83,26 @@ def _fill_traffic():
             with open(os.path.join(ROOT, "paper_1503_06182_gb300", "csrc", f), "rb") as fh:
                 h.update(fh.read())
     except OSError:
+        return False
+    return h.hexdigest() == FILL_SOURCES_SHA256
+
+
+def _fill_traffic():
+    return FILL_TRAFFIC_BYTES if _fill_sources_captured() else None
+
+
+def _fill_issue(fill_avg_ms, sm_mhz):
+    """The fill's warp-instruction issue rate against its peak (None if the
+    sources changed since the capture)."""
+    if not _fill_sources_captured() or not fill_avg_ms:
         return None
-    return FILL_TRAFFIC_BYTES if h.hexdigest() == FILL_SOURCES_SHA256 else None
+    achieved = FILL_WARP_INSTRUCTIONS / (fill_avg_ms * 1e-3) / 1e12
+    peak = SM_COUNT * SMSP_PER_SM * sm_mhz * 1e6 / 1e12
+    return {"unit": "T warp instructions/s", "warp_instructions_per_launch": FILL_WARP_INSTRUCTIONS,
+            "instructions_per_event": FILL_WARP_INSTRUCTIONS * 32 / NCALL, "achieved": achieved,
+            "peak": peak, "frac": achieved / peak,
+            "peak_source": "derived: 152 SMs x 4 sub-partitions x 1 warp instruction per cycle "
+                           "at the median SM clock of the timed region"}
 
 
 def _fp32_peak_derived_tflops():
@@ -362,6 +385,7 @@ def run_gpu(args):
                      "peak_derived": _fp32_peak_derived_tflops(),
                      "frac_of_derived": achieved / _fp32_peak_derived_tflops(),
                      "flops_per_event": FLOPS_PER_EVENT_FP32,
+                     "issue": _fill_issue(fill_avg, (clocks or {}).get("sm_mhz") or SM_MAX_MHZ),
                      "reduce": {"kernel": "gv_reduce_slots_kernel (sums, refinement, record)",
                                 "bound": "latency", "algorithmic_bytes": red_bytes,
                                 "achieved_gbs": red_gbs, "peak_gbs": hbm,
