@@ -183,17 +183,32 @@ def _params_fast(params) -> np.ndarray:
     return _params(params)
 
 
+_PARAM_PTR = [None, 0]  # the last parameter array passed and its data address
+
+
+def _params_ptr(params):
+    """A float64 parameter array and its address; the address of the array
+    object passed last is kept (an array's data does not move)."""
+    if params is _PARAM_PTR[0]:
+        return params, _PARAM_PTR[1]
+    p = _params_fast(params)
+    a = p.ctypes.data
+    if p is params:
+        _PARAM_PTR[0], _PARAM_PTR[1] = p, a
+    return p, a
+
+
 def vegas_iterate(h, ncall: int, itmx: int, integrand_id: int, params, allow_nonfinite=False):
     """Returns (integral, error, chi2_dof, per_iter[itmx, 2], status).  This is
     the per-stage call, so it passes raw pointers (no per-call argument
-    checking by ctypes)."""
-    p = _params_fast(params)
-    out = (C.c_double * 3)()
-    per = np.empty((itmx, 2))
-    st = _raw().vegas_iterate(h, ncall, itmx, integrand_id, p.ctypes.data, p.shape[0], out,
-                              C.byref(out, 8), C.byref(out, 16), per.ctypes.data)
+    checking by ctypes); the three scalars and the records share one buffer."""
+    p, pa = _params_ptr(params)
+    buf = np.empty(3 + 2 * itmx)
+    a = buf.ctypes.data
+    st = _raw().vegas_iterate(h, ncall, itmx, integrand_id, pa, p.shape[0], a, a + 8, a + 16,
+                              a + 24)
     _check(st, "vegas_iterate", (VEGAS_ENONFINITE,) if allow_nonfinite else ())
-    return out[0], out[1], out[2], per, st
+    return float(buf[0]), float(buf[1]), float(buf[2]), buf[3:].reshape(itmx, 2), st
 
 
 def vegas_launch(h, ncall: int, itmx: int, integrand_id: int, params) -> None:
@@ -393,6 +408,7 @@ class Vegas:
         self.ndim, self.nbins, self.seed = ndim, nbins, seed
         self.h = vegas_init(ndim, nbins, seed)
         self._ws = None
+        self._ws_for = None  # the (ncall, itmx) the workspace was last checked for
         self._torch_ws = torch_workspace
         self.set(VEGAS_OPT_PRECISION, 1 if precision == "fp32" else 0)
         self.set(VEGAS_OPT_ALPHA, alpha)
@@ -401,14 +417,16 @@ class Vegas:
 
     def set(self, key: int, value: float) -> "Vegas":
         vegas_set_option(self.h, key, value)
+        self._ws_for = None  # options can change the workspace a stage needs
         return self
 
     def _workspace(self, ncall: int, itmx: int):
-        if not self._torch_ws:
+        if not self._torch_ws or (ncall, itmx) == self._ws_for:
             return
         import torch
 
         need = vegas_workspace_size(self.h, ncall, itmx)
+        self._ws_for = (ncall, itmx)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
             ptr = self._ws.data_ptr()
@@ -455,6 +473,7 @@ class Vegas:
         (nbins = 0: none)."""
         vegas_hist_set(self.h, nbins, lo, hi)
         self._hist_n = int(nbins)
+        self._ws_for = None
         return self
 
     def strat(self):
