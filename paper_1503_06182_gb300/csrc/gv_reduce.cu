@@ -376,7 +376,15 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
     const int chunk = (N + 31) / 32;
     const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
     double part = 0.0;
-    for (int i = i0; i < i1; ++i) part += r[i];
+    if (chunk <= 4) {
+      // a fixed pairwise tree over the chunk (zeros past its end add exactly)
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = i0 + k < i1 ? r[i0 + k] : 0.0;
+      part = (v[0] + v[1]) + (v[2] + v[3]);
+    } else {
+      for (int i = i0; i < i1; ++i) part += r[i];
+    }
     double* tr = s_tree[q];
     tr[lane] = part;
     __syncwarp();
@@ -385,7 +393,10 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
       if (lane < m) tr[lane] = tr[lane] + tr[lane + m];
       __syncwarp();
     }
-    if (lane == 0) s_inv[q] = tr[0] > 0.0 ? __drcp_rn(tr[0]) : 0.0;
+    if (lane == 0) {
+      const double t = tr[0];
+      s_inv[q] = !(t > 0.0) ? 0.0 : (t > 0x1p-1000 && t < 0x1p1000) ? gv_rcp_nr(t) : __drcp_rn(t);
+    }
   }
   gv_bar(bar, nthr);
   const double inv = s_inv[q];
@@ -405,8 +416,19 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
     if (wid == 0) {
       const int chunk = (N + 31) / 32;
       const int i0 = min(N, lane * chunk), i1 = min(N, i0 + chunk);
+      // the chunk's own running sums (in order), formed before the scan so
+      // that each C below is one addition away from its chunk's base
+      double lp[4];
       double local = 0.0;
-      for (int i = i0; i < i1; ++i) local += r[i];
+      if (chunk <= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          local = i0 + k < i1 ? local + r[i0 + k] : local;
+          lp[k] = local;
+        }
+      } else {
+        for (int i = i0; i < i1; ++i) local += r[i];
+      }
       // inclusive prefix sums of the 32 chunk sums (Hillis-Steele in shared
       // memory), then each chunk's exclusive prefix
       double* tr = s_tree[q];
@@ -421,9 +443,15 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
       }
       double run = lane > 0 ? tr[lane - 1] : 0.0;  // exclusive prefix of this lane's chunk
       if (lane == 0) C[0] = 0.0;
-      for (int i = i0; i < i1; ++i) {
-        run += r[i];
-        C[i + 1] = run;
+      if (chunk <= 4) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i0 + k < i1) C[i0 + k + 1] = run + lp[k];
+      } else {
+        for (int i = i0; i < i1; ++i) {
+          run += r[i];
+          C[i + 1] = run;
+        }
       }
       __syncwarp();
       if (lane == 0) s_step[q] = C[N] * a.inv_nbins;
