@@ -31,6 +31,7 @@
 #include <algorithm>
 
 #include "gv_combine.cuh"
+#include "gv_ff.cuh"
 #include "gv_integrands.cuh"
 
 struct u192 {
@@ -326,6 +327,41 @@ __device__ __forceinline__ double compress(double rho, double alpha) {
   return pow(om * __drcp_rn(L), alpha);
 }
 
+// The compressed value r = ((1 - rho)/(-ln rho))^(3/2) (alpha = 3/2) and the
+// slope de / r in FP32 pairs (gv_ff.cuh), for 2^-100 < rho <= 3/5 and
+// 2^-100 < de <= 1.  -ln rho by the table reduction of gv_log_pos: rho =
+// 2^k m, r' = m R_j - 1 (|r'| < 2^-7), ln rho = k ln2 + L_j + ln(1 + r'),
+// with ln(1 + r') = r' + r'^2 P(r'), P = -1/2 + r'/3 - r'^2/4 + ... + r'^5/7
+// (truncation below 2^-60); the leading -1/2 and r' P's product are paired,
+// the rest of P (scaled by r'^3 < 2^-21) is FP32.
+__device__ __forceinline__ void compress15_ff(double rho, double de, double& rv, double& sl) {
+  const long long b = __double_as_longlong(rho);
+  const int k = (int)(b >> 52) - 1023;
+  const int j = (int)((b >> 45) & 127);
+  const GvFF m = gv_ff_from_double(
+      __longlong_as_double((b & 0xFFFFFFFFFFFFFll) | 0x3FF0000000000000ll));
+  const double2 RL = __ldg(reinterpret_cast<const double2*>(gv_log_tab) + j);
+  const GvFF p = gv_ff_mul(m, gv_ff_from_double(RL.x));
+  const GvFF r = gv_two_sum(__fsub_rn(p.hi, 1.0f), p.lo);  // p.hi - 1 is exact
+  const float x = r.hi;
+  float Q = __fmaf_rn(x, 1.0f / 7.0f, -1.0f / 6.0f);
+  Q = __fmaf_rn(Q, x, 0.2f);
+  Q = __fmaf_rn(Q, x, -0.25f);
+  Q = __fmaf_rn(Q, x, 1.0f / 3.0f);
+  const GvFF P = gv_two_sum(-0.5f, __fmul_rn(x, Q));
+  const GvFF l1p = gv_ff_add(r, gv_ff_mul(gv_ff_mul(r, r), P));
+  // ln 2 = 0x1.62e43p-1 + (-0x1.05c61p-29), to 9e-17
+  const GvFF kln2 = gv_ff_mul_f(GvFF{0x1.62e43p-1f, -0x1.05c61p-29f}, (float)k);
+  const GvFF lnrho = gv_ff_add(gv_ff_add(kln2, gv_ff_from_double(RL.y)), l1p);
+  const GvFF L = {-lnrho.hi, -lnrho.lo};
+  const GvFF R = gv_ff_from_double(rho);
+  const GvFF om = gv_ff_add(GvFF{1.0f, 0.0f}, GvFF{-R.hi, -R.lo});
+  const GvFF q = gv_ff_div(om, L);
+  const GvFF c = gv_ff_mul(q, gv_ff_sqrt(q));
+  rv = gv_ff_to_double(c);
+  sl = gv_ff_to_double(gv_ff_div(gv_ff_from_double(de), c));
+}
+
 // alpha values whose compressed values are at least (1/745)^2 > 1e-6 (the
 // reciprocal approximation then sees normal numbers only)
 __device__ __forceinline__ bool fast_alpha(double alpha) {
@@ -406,8 +442,13 @@ __device__ __forceinline__ void refine_axis(const GvReduceArgs& a, int ax, doubl
       double rv = 0.0, sl = 0.0;
       const double s6 = r[i];
       if (s6 > 0.0) {
-        rv = compress(s6 * inv, a.alpha);
-        if (rv > 0.0) sl = (e[i + 1] - e[i]) * (fast ? gv_rcp_nr(rv) : __drcp_rn(rv));
+        const double rho = s6 * inv, de = e[i + 1] - e[i];
+        if (a.alpha == 1.5 && rho > 0x1p-100 && rho <= 0.6 && de > 0x1p-100 && de <= 1.0) {
+          compress15_ff(rho, de, rv, sl);
+        } else {
+          rv = compress(rho, a.alpha);
+          if (rv > 0.0) sl = de * (fast ? gv_rcp_nr(rv) : __drcp_rn(rv));
+        }
       }
       r[i] = rv;
       slope[i] = sl;
