@@ -412,9 +412,10 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   a.gsum = (long long*)(b + o_gs);
   a.gpart = (double2*)(b + o_gp);
   a.gctr = (int*)(b + o_gc);
-  // 64 bytes: the event count, three scalars
+  // 64 bytes: the event count, three scalars, the fill's used tiles
   a.ncall_dev = (long long*)(b + o_sc);
   a.scal = (double*)(b + o_sc + 8);
+  a.tiles_used = (int*)(b + o_sc + 32);
   c->plus_fill = (GvPlusFill*)(b + o_pf);
   a.inv = (const double*)(b + o_tab);
   a.abtab = (const double2*)(b + o_tab + (size_t)GV_PLUS_NTAB * 8);
@@ -464,6 +465,7 @@ GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
     r.host_st = (GvState*)c->hres_dev;
     r.host_rec = (double*)((char*)c->hres_dev + kHostRecOff);
   }
+  if (p.plus) r.tiles_used = c->pa.tiles_used;
   r.k = k;
   r.last = k == p.itmx - 1;
   r.refine_follows = (p.mode == 0 && c->adapt) ? 1 : 0;
@@ -671,6 +673,7 @@ int ensure_allocation(vegas_ctx* c, const Plan& p) {
   f.ncall = c->pa.ncall_dev;
   f.seg_h = p.seg_h;
   f.seg_r = p.seg_r;
+  f.tiles_used = c->pa.tiles_used;
   // a pageable copy is staged before cudaMemcpyAsync returns
   GV_TRY(cudaMemcpyAsync(c->plus_fill, &f, sizeof f, cudaMemcpyHostToDevice, c->stream));
   if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;

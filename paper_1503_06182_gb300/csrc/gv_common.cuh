@@ -113,6 +113,7 @@ struct GvPlusFill {
   const long long* ncall;
   double2* seg_h;
   double2* seg_r;
+  int* tiles_used;  // written by the fill: the tiles that hold events this iteration
 };
 
 // Arguments of the fill kernels (forward and adjoint).
@@ -192,6 +193,9 @@ struct GvReduceArgs {
   // grid refinement
   double alpha, inv_nbins;
   double* grid;                  // grid pack (refined in place, one axis per CTA)
+  // VEGAS+: the tiles the fill gave events (its grid holds the largest
+  // allocation; the rest left nothing); nullptr: all n_tiles
+  const int* tiles_used = nullptr;
 };
 
 // ----------------------------------------------------------------------------
@@ -513,7 +517,8 @@ struct GvPlusArgs {
   double2* gpart = nullptr;    // [groups] the group's sums of v/n and of the weights
   int* gctr = nullptr;         // [2 groups + 1] arrival counters (zero between uses)
   long long* ncall_dev = nullptr;  // events of the allocation
-  double* scal = nullptr;    // [2] sigma_k^2, the weights' sum D
+  double* scal = nullptr;    // [3] sigma_k^2, the weights' sum D, 1/D
+  int* tiles_used = nullptr; // the fill's tiles with events (the reduce reads no others)
   const double* inv = nullptr;    // [GV_PLUS_NTAB] 1/n (entry 0 unused)
   const double2* abtab = nullptr; // [GV_PLUS_NTAB] ab for n_h = n (C and nh of the allocation)
   int prio = 0;              // launch priority (the most urgent of the device)

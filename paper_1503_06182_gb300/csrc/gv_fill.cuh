@@ -927,16 +927,13 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, 
   }
   gv_wait_prior_grid();  // grid, constants and iteration counter come from earlier kernels
   if constexpr (PLUS) {
-    // VEGAS+ sizes the grid for the most events an allocation can have: a
-    // tile past this iteration's last event only leaves an empty partial
-    const long long t0 = (long long)blockIdx.x * GV_TILE;
-    if (t0 >= *a.plus->ncall) {
-      const size_t ks = a.slot_major ? (size_t)a.n_tiles : (size_t)1;
-      ulonglong2* out = a.part + (a.slot_major ? (size_t)blockIdx.x : (size_t)blockIdx.x * a.nacc);
-      for (int k = threadIdx.x; k < a.nacc; k += B) out[k * ks] = make_ulonglong2(0ull, 0ull);
-      if (threadIdx.x == 0) a.tileE[blockIdx.x] = GV_EMPTY;
-      return;
-    }
+    // VEGAS+ sizes the grid for the most events an allocation can have; the
+    // iteration's events fill the first tiles_used tiles, which alone the
+    // reduce reads, and a tile past them does nothing
+    const long long ncall = *a.plus->ncall;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      *a.plus->tiles_used = (int)((ncall + GV_TILE - 1) / GV_TILE);
+    if ((long long)blockIdx.x * GV_TILE >= ncall) return;
   }
   gv_stage_grid<Real>(a.grid, d, N, reinterpret_cast<double*>(smem + lay.jac),
                       reinterpret_cast<typename GvPair<Real>::T*>(smem + lay.ew), threadIdx.x, B);

@@ -789,13 +789,13 @@ __global__ void __launch_bounds__(256) gv_reduce_slots_kernel(const GvReduceArgs
   const int pw = hw ? 1 : (bin ? 2 : (k & 1) + 1);
   const int empty = bin ? 0 : GV_EMPTY;
   const int ch = k >> 1;
-  const int nt = a.n_tiles;
-  const ulonglong2* src = a.part + (size_t)k * nt;
+  const ulonglong2* src = a.part + (size_t)k * a.n_tiles;  // slot-major: slot stride n_tiles
   if (tid == 0) {
     s_nwon = 0;
     s_fin = 0;
   }
   gv_wait_prior_grid();
+  const int nt = a.tiles_used ? min(a.n_tiles, __ldcg(a.tiles_used)) : a.n_tiles;
   __syncthreads();
   // the slot's largest exponent over all tiles
   const bool cached = nt <= G * GT;  // every partial of a thread fits in registers
