@@ -173,6 +173,10 @@ struct vegas_ctx {
   // before the next fill)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // autotuning: a copy of the grid pack and the state to return to after
+  // trial iterations, and whether trials are running (no results to host)
+  void* tune_backup = nullptr;
+  bool tuning = false;
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -214,6 +218,9 @@ size_t grid_doubles(int d, int N) { return GvGridLayout{d, N}.doubles(); }
 
 // events: the fill's capacity (ncall, or ncall + 2 nh with VEGAS+); plus_f:
 // room for the per-event J g of VEGAS+
+// chained iterations per autotuning trial (iteration records are sized for them)
+constexpr int kTuneIter = 8;
+
 size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhist,
                        bool plus_f = false) {
   const int64_t n_tiles = (ncall + GV_TILE - 1) / GV_TILE;
@@ -223,7 +230,7 @@ size_t workspace_bytes(int d, int N, int64_t ncall, int itmx, int mode, int nhis
   gv::reduce_grid((int)std::min<int64_t>(n_tiles, 0x7fffffff), nacc, &tpc, &gx, &gy);
   size_t b = align256((size_t)n_tiles * nacc * 16);
   b += align256((size_t)n_tiles * nch * 4);
-  b += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
+  b += align256((size_t)std::max(itmx, kTuneIter) * (2 + 2 * GV_NGRAD) * 8);
   b += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
   // VEGAS+: segment sums (16 B) per range and per hypercube (nh <= ncall / 4)
   if (plus_f) b += align256((size_t)(ncall / GV_PLUS_SEG + 1) * 16) + align256((size_t)(ncall / 4 + 1) * 16);
@@ -449,7 +456,7 @@ GvHistArgs hist_args(const vegas_ctx* c, const Plan& p, int k) {
 // over through the mapped block (VEGAS+ finishes its iterations in another
 // kernel, and the adjoint has more channels).
 bool zero_copy(const vegas_ctx* c, const Plan& p) {
-  return c->hres_dev && p.mode == 0 && !p.plus && p.itmx <= kHostRecMax;
+  return c->hres_dev && !c->tuning && p.mode == 0 && !p.plus && p.itmx <= kHostRecMax;
 }
 
 GvReduceArgs reduce_args(const vegas_ctx* c, const Plan& p, int k) {
@@ -515,6 +522,81 @@ cudaError_t launch_fill_plan(const vegas_ctx* c, const Plan& p, int ept, bool pd
 
 // Pick events per thread by timing one fill launch per candidate.  Runs
 // between two setup kernels, so the trial launches leave no trace.
+int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool capture);
+
+// Events per thread for a plain forward stage, by timing what a stage runs:
+// kTuneIter chained iterations (fills and reduces with the refinement, by
+// programmatic launch) per candidate, best of kTuneRep, from the same grid
+// and state each time (saved before, restored after; no result goes to the
+// host).  In a stage, the fills of iterations k > 0 make their Philox words
+// while the previous refinement runs, and a shape whose CTAs are all
+// resident at once does that for every tile: single fill launches, timed
+// alone, miss it.  4 is kept unless another candidate is more than 0.5%
+// faster.
+constexpr int kTuneRep = 5;
+int autotune_chained(vegas_ctx* c, Plan& p, const std::string& key) {
+  const size_t gbytes = grid_doubles(c->ndim, c->nbins) * sizeof(double);
+  if (!c->tune_backup) {
+    if (cudaMalloc(&c->tune_backup, gbytes + sizeof(GvState)) != cudaSuccess) {
+      cudaGetLastError();
+      c->tune_backup = nullptr;
+      return VEGAS_ENOMEM;
+    }
+  }
+  char* bk = (char*)c->tune_backup;
+  GV_TRY(cudaMemcpyAsync(bk, c->grid, gbytes, cudaMemcpyDeviceToDevice, c->stream));
+  GV_TRY(cudaMemcpyAsync(bk + gbytes, c->st, sizeof(GvState), cudaMemcpyDeviceToDevice, c->stream));
+  cudaEvent_t e0, e1;
+  GV_TRY(cudaEventCreate(&e0));
+  GV_TRY(cudaEventCreate(&e1));
+  Plan t = p;
+  t.itmx = kTuneIter;
+  c->tuning = true;
+  int st = VEGAS_OK;
+  float best = 1e30f, t4 = 1e30f;
+  int best_ept = 4;
+  for (const int ept : {1, 2, 4, 8}) {
+    if (c->ndim > 8 && ept == 8) continue;
+    // a shape the device cannot launch (registers, shared memory) is skipped
+    if (launch_fill_plan(c, t, ept) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    t.ept = ept;
+    float best_i = 1e30f;
+    for (int rep = 0; rep <= kTuneRep && !st; ++rep) {  // rep 0 warms up
+      cudaEventRecord(e0, c->stream);
+      st = enqueue_body(c, t, nullptr, false);
+      cudaEventRecord(e1, c->stream);
+      if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = VEGAS_ECUDA;
+      float ms = 0;
+      if (!st && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best_i = std::min(best_i, ms);
+      cudaMemcpyAsync(c->grid, bk, gbytes, cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemcpyAsync(c->st, bk + gbytes, sizeof(GvState), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (st) break;
+    if (ept == 4) t4 = best_i;
+    if (best_i < best) {
+      best = best_i;
+      best_ept = ept;
+    }
+  }
+  c->tuning = false;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) {
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    return st;
+  }
+  GV_TRY(cudaGetLastError());
+  if (best_ept != 4 && t4 < 1e30f && best > 0.995f * t4) best_ept = 4;
+  p.ept = best_ept;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best_ept;
+  return VEGAS_OK;
+}
+
 int autotune(vegas_ctx* c, Plan& p) {
   const std::string key = tune_key(c->device, p.ig, p.fp32, p.mode, c->ndim, c->nbins, p.n_tiles);
   {
@@ -525,6 +607,7 @@ int autotune(vegas_ctx* c, Plan& p) {
       return VEGAS_OK;
     }
   }
+  if (p.mode == 0 && !p.plus && !p.nhist) return autotune_chained(c, p, key);
   const int cands_fwd[] = {1, 2, 4, 8};
   const int cands_adj[] = {1, 2, 4};
   const int* cands = p.mode ? cands_adj : cands_fwd;
@@ -624,7 +707,7 @@ int make_plan(vegas_ctx* c, int64_t ncall, int itmx, int ig, int mode, Plan& p) 
   p.tileE = (int*)w;
   w += align256((size_t)p.n_tiles * p.nch * 4);
   p.per_iter = (double*)w;
-  w += align256((size_t)itmx * (2 + 2 * GV_NGRAD) * 8);
+  w += align256((size_t)std::max(itmx, kTuneIter) * (2 + 2 * GV_NGRAD) * 8);
   p.cpart = (GvSlot*)w;
   if (p.plus) {
     w += align256((size_t)gy * gx * 32 * sizeof(GvSlot));
@@ -723,16 +806,15 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     if (p.plus) {
       // beside the reduce: the hypercubes' statistics from the fill's
       // segments (sigma_k; the stage's combination with the reduce's I_k),
-      // then the next iteration's allocation and its layout; joined before
-      // the next fill
+      // then the next iteration's allocation; joined after the reduce.  The
+      // layout follows on this stream, so that the next fill comes in by
+      // programmatic launch and makes its Philox words while it runs.
       const GvPlusArgs a = plus_args(c, p, k);
       GV_TRY(gv::launch_plus_stats(a, c->side, false));
-      if (c->adapt) {
-        GV_TRY(gv::launch_plus_alloc(a, c->side, pdl));
-        GV_TRY(gv::launch_plus_layout(a, c->side, pdl));
-      }
+      if (c->adapt) GV_TRY(gv::launch_plus_alloc(a, c->side, pdl));
       GV_TRY(cudaEventRecord(c->ev_join, c->side));
       GV_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+      if (c->adapt) GV_TRY(gv::launch_plus_layout(a, c->stream, false));
     }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }
@@ -1052,6 +1134,7 @@ void vegas_free(vegas_ctx* c) {
   if (c->hres) cudaFreeHost(c->hres);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->tune_backup) cudaFree(c->tune_backup);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete c;

@@ -279,12 +279,14 @@ __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(siz
 // The forward fill generates its tile's Philox words before it waits for the
 // previous kernel (the words depend only on the seed, the counter and the
 // event), where the launch overlaps the previous iteration's reduce and
-// refinement; not with VEGAS+ (stratified words), nor beyond 8 axes, nor
-// where the words' shared memory would take the layout past GV_WORDS_SMEM_MAX
-// (the host sets GvFillArgs::hoist accordingly).
+// refinement (VEGAS+: its layout; the stratified fill stratifies the words
+// after the wait); not beyond 8 axes, nor where the words' shared memory
+// would take the layout past GV_WORDS_SMEM_MAX (the host sets
+// GvFillArgs::hoist accordingly).
 #define GV_WORDS_SMEM_MAX (200 * 1024)
 __host__ __device__ inline bool gv_fill_hoistable(bool forward, bool plus, int d) {
-  return forward && !plus && d <= 8;
+  (void)plus;  // the stratified fill stratifies the hoisted words after its wait
+  return forward && d <= 8;
 }
 
 // A tile of GV_TILE events meets at most GV_TILE/2 + 1 hypercubes (each has
@@ -600,7 +602,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
     hbin[k] = 0;
     if (ev < ncall) {
       uint32_t r[MAXD];
-      if (s_words) {  // generated before the wait (by this thread: same local index)
+      if (s_words) {  // generated before the wait (the kernel's barrier precedes this)
 #pragma unroll
         for (int j = 0; j < (MAXD + 3) / 4; ++j) {
           if (4 * j < d) {
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(GV_TILE / EPT, (GvFillBlocks<Real, EPT, MAXD, 
   __shared__ unsigned long long red_u64[NW];
   __shared__ u128 red_128[NW];
   const int d = a.ndim, N = a.nbins;
-  const bool hoist = !PLUS && MAXD <= 8 && a.hoist;  // set by the host (gv_fill_hoistable)
+  const bool hoist = MAXD <= 8 && a.hoist;  // set by the host (gv_fill_hoistable)
   const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, HIST ? a.nhist : 0, PLUS, hoist);
   unsigned* hist = reinterpret_cast<unsigned*>(smem + lay.hist);
   for (int k = threadIdx.x; k < 4 * d * N; k += B) hist[k] = 0u;

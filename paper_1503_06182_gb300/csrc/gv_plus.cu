@@ -367,6 +367,9 @@ __global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_alloc_kernel(const GvP
 __global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_layout_kernel(const GvPlusArgs a) {
   __shared__ long long s_scan[kT / 32];
   gv_wait_prior_grid();  // the counts and their per-CTA and per-group sums
+  // the next fill may come in now: it makes its Philox words, then waits
+  // for this kernel to finish
+  gv_allow_next_grid();
   const int b = blockIdx.x, g = b / kG;
   const long long h = (long long)b * kT + threadIdx.x;
   const long long m = h < a.nh ? (long long)a.n[h] : 0ll;
@@ -379,7 +382,6 @@ __global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_layout_kernel(const Gv
   long long all, tot;
   block_exscan(pre, s_scan, &all);  // all: the CTA's first event
   const long long o = all + block_exscan(m, s_scan, &tot);
-  gv_allow_next_grid();
   if (h < a.nh) plus_layout_one(a, h, m, o);
 }
 
