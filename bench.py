@@ -56,19 +56,20 @@ FLOPS_ADJOINT_FP32 = 110 + 72 + 5
 # operations): 83 + 3 x 21 + 25 + 15 + 3 x 15 + grid map 4 x 5 = 251.
 FP64_OPS_PER_EVENT_DY = 83 + 3 * 21 + 25 + 15 + 3 * 15 + 4 * 5
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes (read + write) of one fill launch of this workload, from the ncu
-# capture summarised in profiles/fill_drell_yan_fp32_ept4_1e6.md, valid while
-# the fill's sources are the ones captured (their SHA-256 below); otherwise the
-# traffic is reported as unknown (null).
-FILL_TRAFFIC_BYTES = 82_176
-# warp instructions of that launch (smsp__inst_executed.sum, same capture and
-# validity): the fill is issue-bound, so its instruction rate against one warp
-# instruction per cycle per SM sub-partition (4 per SM) is its binding roofline
-FILL_WARP_INSTRUCTIONS = 21_418_973
+# Per events-per-thread shape of the FP32 Drell-Yan fill (1e6 calls, 977
+# tiles), from one-kernel ncu captures (profiles/fill_drell_yan_fp32_ept*_1e6.md):
+# the DRAM bytes (read + write) of one launch, and its warp instructions
+# (smsp__inst_executed.sum).  The fill is issue-bound, so its instruction rate
+# against one warp instruction per cycle per SM sub-partition (4 per SM) is its
+# binding roofline.  Valid while the fill's sources are the ones captured
+# (their SHA-256 below) and only for the shape the timed run used; otherwise
+# both are reported as unknown (null).
+FILL_CAPTURES = {4: {"traffic_bytes": 82_432, "warp_instructions": 21_418_973},
+                 8: {"traffic_bytes": 121_856, "warp_instructions": 19_412_189}}
 SMSP_PER_SM = 4
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "866d250c911d397b6e1f5b2d6f26025904e3a0ec302870c49114ce136e75a7a0"
+FILL_SOURCES_SHA256 = "5d8d68412efd1b6772c54ed7ceea6de21a382757cd43fd50cfc894321037ceaf"
 # HBM copy bandwidth measured by the driver on the GB300s (used when
 # MEASURED_PEAKS.json is absent: the profiling recipe's fallback)
 HBM_FALLBACK_GBS = 6800.0
@@ -87,19 +88,25 @@ def _fill_sources_captured():
     return h.hexdigest() == FILL_SOURCES_SHA256
 
 
-def _fill_traffic():
-    return FILL_TRAFFIC_BYTES if _fill_sources_captured() else None
-
-
-def _fill_issue(fill_avg_ms, sm_mhz):
-    """The fill's warp-instruction issue rate against its peak (None if the
-    sources changed since the capture)."""
-    if not _fill_sources_captured() or not fill_avg_ms:
+def _fill_capture(ept, key):
+    """A captured figure of the fill at this events-per-thread shape (None if
+    the sources changed since the capture or the shape was not captured)."""
+    if not _fill_sources_captured():
         return None
-    achieved = FILL_WARP_INSTRUCTIONS / (fill_avg_ms * 1e-3) / 1e12
+    return FILL_CAPTURES.get(ept, {}).get(key)
+
+
+def _fill_issue(fill_avg_ms, sm_mhz, ept):
+    """The fill's warp-instruction issue rate against its peak (None if the
+    sources changed since the capture, or the timed shape was not captured)."""
+    wi = _fill_capture(ept, "warp_instructions")
+    if wi is None or not fill_avg_ms:
+        return None
+    achieved = wi / (fill_avg_ms * 1e-3) / 1e12
     peak = SM_COUNT * SMSP_PER_SM * sm_mhz * 1e6 / 1e12
-    return {"unit": "T warp instructions/s", "warp_instructions_per_launch": FILL_WARP_INSTRUCTIONS,
-            "instructions_per_event": FILL_WARP_INSTRUCTIONS * 32 / NCALL, "achieved": achieved,
+    return {"unit": "T warp instructions/s", "warp_instructions_per_launch": wi,
+            "events_per_thread": ept,
+            "instructions_per_event": wi * 32 / NCALL, "achieved": achieved,
             "peak": peak, "frac": achieved / peak,
             "peak_source": "derived: 152 SMs x 4 sub-partitions x 1 warp instruction per cycle "
                            "at the median SM clock of the timed region"}
@@ -378,14 +385,15 @@ def run_gpu(args):
                              "ms_per_iteration": one_tot / K,
                              "note": "one iteration per step (a stage of its own), L2 flushed"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": _fill_traffic(),
+                     "frac": achieved / peak, "traffic": _fill_capture(ept, "traffic_bytes"),
                      "kernel": "gv_fill_kernel<drell_yan, float>",
                      "kernel_avg_ms": fill_avg, "reduce_refine_avg_ms": kavg[1],
                      "peak_source": "measured in this run: FFMA probe (vegas_pipe_peak)",
                      "peak_derived": _fp32_peak_derived_tflops(),
                      "frac_of_derived": achieved / _fp32_peak_derived_tflops(),
                      "flops_per_event": FLOPS_PER_EVENT_FP32,
-                     "issue": _fill_issue(fill_avg, (clocks or {}).get("sm_mhz") or SM_MAX_MHZ),
+                     "issue": _fill_issue(fill_avg, (clocks or {}).get("sm_mhz") or SM_MAX_MHZ,
+                                          ept),
                      "reduce": {"kernel": "gv_reduce_slots_kernel (sums, refinement, record)",
                                 "bound": "latency", "algorithmic_bytes": red_bytes,
                                 "achieved_gbs": red_gbs, "peak_gbs": hbm,
@@ -421,7 +429,8 @@ def forms(v, stream, seed, peaks, only=None):
     the plain FP64 Gauss case 5 x 1e5; the NLO-shaped 13-axis case 10 x 1e6
     FP32; Drell-Yan 10 x 1e6 FP32 filling a 60-bin m_ll histogram; Drell-Yan
     10 x 1e6 FP32 with VEGAS+ stratification, with its integration efficiency
-    1/(sigma^2 t) against plain VEGAS on the same workload.  Each FP32 form
+    1/(sigma^2 t) against plain VEGAS on the same workload (each arm's time the
+    median of five stages timed like the headline's).  Each FP32 form
     also reports its fill kernel's FP32 roofline fraction (a separate stage
     with per-kernel timing) and its difference from the FP64 form on the same
     events (the FP64 path matches the oracle to 1e-12)."""
@@ -519,14 +528,31 @@ def forms(v, stream, seed, peaks, only=None):
         res[name] = r
     if want("dy_vegasplus_d4_n100_10x1e6_fp32"):
         # VEGAS+ against plain VEGAS: the same workload, events/s and efficiency
+        # Each arm: a warm-up stage (grid and allocation adapt), then five
+        # stages timed like the headline's (device events around the stage's
+        # launch, L2 flushed before it): the time is their median, the result
+        # the first one's.
         plus = {}
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=stream.device)
         for strat, prec in ((0, "fp32"), (1, "fp32"), (1, "fp64")):
             g = v.Vegas(NDIM, NBINS, seed, precision=prec)
             v.vegas_set_stream(g.h, stream.cuda_stream)
             g.set(v.VEGAS_OPT_STRAT, strat)
             try:
-                g.iterate(NCALL, 10, DY, DY_PARAMS)  # warm-up stage: grid and allocation adapt
-                ms, (I, e, c, _, _) = timed(lambda: g.iterate(NCALL, 10, DY, DY_PARAMS))
+                g.iterate(NCALL, 10, DY, DY_PARAMS)
+                ts, first = [], None
+                for _ in range(5):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    with torch.cuda.stream(stream):
+                        flush.fill_(1)
+                        a.record(stream)
+                        g.launch(NCALL, 10, DY, DY_PARAMS)
+                        b.record(stream)
+                    out = g.fetch(10)
+                    ts.append(a.elapsed_time(b))
+                    first = first or out
+                ms = float(np.median(ts))
+                I, e, c = first[0], first[1], first[2]
             finally:
                 g.close()
             plus[(strat, prec)] = (ms, I, e, c)

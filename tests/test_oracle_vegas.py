@@ -138,6 +138,39 @@ def test_refine_concentrates_bins_on_peak(oracle_mod):
     assert inside >= 15  # almost all edges move into the smoothed peak
 
 
+def test_refine_alternating_widths_grow_on_flat_axis(oracle_mod):
+    """First-order response of one refinement on an axis the integrand does
+    not depend on, worked out by hand.  There d_i is proportional to the
+    squared Jacobian factor Delta_i^2; take widths Delta_i = (1 + eps
+    (-1)^i)/N, N even, so d_i = (1 + 2 eps (-1)^i)/N^2 + O(eps^2).
+    - The 3-point mean of the interior gives the alternating part (2 eps/3)
+      (1 - 2)(-1)^i = -(2 eps/3)(-1)^i: the wider bins get the smaller smoothed
+      sums.  The ends' 2-point means have no first-order part, and the total
+      is 1/N.
+    - The compression m(rho) = ((1 - rho)/ln(1/rho))^alpha has the logarithmic
+      slope kappa = alpha (1/ln(1/rho) - rho/(1 - rho)) at rho = 1/N, so
+      inside m_i = mbar (1 - kappa (2 eps/3)(-1)^i), and m_0 = m_{N-1} = mbar.
+    - The sum of m up to old edge j exceeds j mbar by mbar kappa (2 eps/3) for
+      even j >= 2 and equals it for odd j; the N equal shares therefore move
+      each even edge left by kappa (2 eps/3)/N and keep the odd ones.
+    So bin i's new width is (1 + (1 + 2 kappa/3) eps (-1)^i)/N for 1 <= i <=
+    N - 2, and bins 0 and N - 1 keep theirs.  The alternation grows by
+    1 + 2 kappa/3 (1.207 at N = 100) per refinement: the reason a long run of
+    adapting iterations roughens the grid along such an axis."""
+    N, eps, alpha = 100, 1e-5, 1.5
+    sgn = (-1.0) ** np.arange(N)
+    w = (1.0 + eps * sgn) / N
+    edges = np.concatenate([[0.0], np.cumsum(w)])
+    edges[-1] = 1.0
+    new = oracle_mod.refine((w ** 2)[None, :], edges[None, :], alpha)[0]
+    rho = 1.0 / N
+    kappa = alpha * (1.0 / math.log(1.0 / rho) - rho / (1.0 - rho))
+    g = (np.diff(new) * N - 1.0) / (eps * sgn)  # each width's deviation in units of eps
+    # second-order terms are O(eps) of these
+    assert np.max(np.abs(g[1:-1] - (1.0 + 2.0 * kappa / 3.0))) < 1e-4
+    assert abs(g[0] - 1.0) < 1e-4 and abs(g[-1] - 1.0) < 1e-4
+
+
 # ----------------------------------------------------------- VEGAS estimates
 def _two_stage(oracle_mod, ndim, nbins, iid, params, ncall, warm, prod, seed):
     r = oracle_mod.iterate(ndim, nbins, seed, ncall // 4, warm, iid, params)
