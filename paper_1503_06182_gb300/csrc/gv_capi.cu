@@ -381,17 +381,15 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   off = align256(off + (size_t)nh * 8);
   const size_t o_dw = off;
   off = align256(off + (size_t)nh * 8);
-  const size_t o_part = off;
-  off = align256(off + (size_t)nb * 16);
+  const size_t o_tp = off;  // the fill's per-tile sums, then the finishing kernel's per-CTA sums
+  off = align256(off + (size_t)(n_tiles + 16) * 16);
   const size_t o_np = off;
   off = align256(off + (size_t)nb * 8);
   const long long ng = (nb + 31) / 32;
   const size_t o_gs = off;
   off = align256(off + (size_t)ng * 8);
-  const size_t o_gp = off;
-  off = align256(off + (size_t)ng * 16);
   const size_t o_gc = off;
-  off = align256(off + (size_t)(2 * ng + 1) * 4);
+  off = align256(off + (size_t)ng * 4);
   const size_t o_sc = off;
   off = align256(off + 64);
   const size_t o_pf = off;
@@ -414,15 +412,17 @@ int ensure_plus(vegas_ctx* c, long long nh, int n_tiles) {
   a.tile_h0 = (int*)(b + o_t);
   a.var = (double*)(b + o_var);
   a.dw = (double*)(b + o_dw);
-  a.part = (double*)(b + o_part);
+  a.tpart = (double2*)(b + o_tp);
+  a.fpart = a.tpart + n_tiles;
   a.npart = (long long*)(b + o_np);
   a.gsum = (long long*)(b + o_gs);
-  a.gpart = (double2*)(b + o_gp);
   a.gctr = (int*)(b + o_gc);
-  // 64 bytes: the event count, three scalars, the fill's used tiles
+  // 64 bytes: the event count, three scalars, the fill's used tiles, the
+  // finishing kernel's counter
   a.ncall_dev = (long long*)(b + o_sc);
   a.scal = (double*)(b + o_sc + 8);
   a.tiles_used = (int*)(b + o_sc + 32);
+  a.fctr = (int*)(b + o_sc + 36);
   c->plus_fill = (GvPlusFill*)(b + o_pf);
   a.inv = (const double*)(b + o_tab);
   a.abtab = (const double2*)(b + o_tab + (size_t)GV_PLUS_NTAB * 8);
@@ -757,6 +757,11 @@ int ensure_allocation(vegas_ctx* c, const Plan& p) {
   f.seg_h = p.seg_h;
   f.seg_r = p.seg_r;
   f.tiles_used = c->pa.tiles_used;
+  f.var = c->pa.var;
+  f.dw = c->pa.dw;
+  f.tpart = c->pa.tpart;
+  f.inv = c->pa.inv;
+  f.beta_j = c->beta_j;
   // a pageable copy is staged before cudaMemcpyAsync returns
   GV_TRY(cudaMemcpyAsync(c->plus_fill, &f, sizeof f, cudaMemcpyHostToDevice, c->stream));
   if (c->plus_valid && c->plus_C == p.ncall) return VEGAS_OK;
@@ -791,30 +796,33 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k], c->stream, flags));
     GV_TRY(launch_fill_plan(c, p, p.ept, pdl && k > 0, k));
     if (p.plus) {
-      // fork: the hypercube statistics need the fill's segments only
+      // fork: the statistics' completion needs the fill's results only
       GV_TRY(cudaEventRecord(c->ev_fork, c->stream));
       GV_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
     // (VEGAS+: a plain launch, so that its CTAs do not hold the SMs while
-    // they wait for the fill; the more urgent statistics beside it go first)
+    // they wait for the fill; the more urgent kernels beside it go first)
     if (p.slot_major)
       GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl && !p.plus));
     else
       GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
     if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
     if (p.plus) {
-      // beside the reduce: the hypercubes' statistics from the fill's
-      // segments (sigma_k; the stage's combination with the reduce's I_k),
-      // then the next iteration's allocation; joined after the reduce.  The
-      // layout follows on this stream, so that the next fill comes in by
-      // programmatic launch and makes its Philox words while it runs.
+      // beside the reduce: the statistics' completion from the fill's tile
+      // sums and crossing hypercubes (sigma_k; the stage's combination with
+      // the reduce's I_k), then the next iteration's allocation and its
+      // layout; joined after the reduce, before the next fill (which comes in
+      // by programmatic launch after the reduce and makes its Philox words
+      // while the reduce finishes).
       const GvPlusArgs a = plus_args(c, p, k);
-      GV_TRY(gv::launch_plus_stats(a, c->side, false));
-      if (c->adapt) GV_TRY(gv::launch_plus_alloc(a, c->side, pdl));
+      GV_TRY(gv::launch_plus_finish(a, c->side, false));
+      if (c->adapt) {
+        GV_TRY(gv::launch_plus_alloc(a, c->side, pdl));
+        GV_TRY(gv::launch_plus_layout(a, c->side, pdl));
+      }
       GV_TRY(cudaEventRecord(c->ev_join, c->side));
       GV_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-      if (c->adapt) GV_TRY(gv::launch_plus_layout(a, c->stream, false));
     }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 2], c->stream, flags));
   }

@@ -98,9 +98,11 @@ struct GvGridLayout {
 // first hypercube is tile_h0[t]; ab[h] = (C/(nh n_h), sqrt(1/(nh n_h)));
 // *ncall events in all.  Each GV_PLUS_SEG-event range r of the fill sums
 // J g and (J g)^2 over its run of each hypercube, in event order (its
-// segments): a hypercube's first segment goes to seg_h[h], and a segment that
-// continues a hypercube begun in an earlier range (only a range's first can)
-// to seg_r[r].
+// segments).  A tile forms the statistics (var, dw) of every hypercube whose
+// events it holds all of, and the sums of their v/n and weights (tpart[t]);
+// the segments of a hypercube that crosses a tile boundary go to memory for
+// the finishing kernel: its first to seg_h[h], and a range's continuation of
+// it (only a range's first segment can be one) to seg_r[r].
 struct GvPlusFill {
   int s;
   float inv_s;
@@ -114,6 +116,11 @@ struct GvPlusFill {
   double2* seg_h;
   double2* seg_r;
   int* tiles_used;  // written by the fill: the tiles that hold events this iteration
+  double* var;      // [nh] sample variance of J g in each hypercube
+  double* dw;       // [nh] allocation weights v^(beta/2)
+  double2* tpart;   // [tiles] per tile: sums of v/n and of the weights of its hypercubes
+  const double* inv;  // [GV_PLUS_NTAB] 1/n (entry 0 unused)
+  int beta_j;       // damping beta = beta_j / 4
 };
 
 // Arguments of the fill kernels (forward and adjoint).
@@ -510,12 +517,13 @@ struct GvPlusArgs {
   int* tile_h0 = nullptr;    // [n_tiles] hypercube of each tile's first event
   double* var = nullptr;     // [nh] sample variance of J g in each hypercube
   double* dw = nullptr;      // [nh] allocation weights v^(beta/2)
-  double* part = nullptr;    // [CTAs][2] per-CTA sums of v/n and of the weights
+  double2* tpart = nullptr;  // [n_tiles] the fill's per-tile sums of v/n and of the weights
+  double2* fpart = nullptr;  // [16] the finishing kernel's per-CTA sums
+  int* fctr = nullptr;       // its arrival counter (zero between uses)
   // per CTA of kT = 256 hypercubes, per group of 32 CTAs
   long long* npart = nullptr;  // [CTAs] the CTA's events of the next allocation
   long long* gsum = nullptr;   // [groups] the group's events
-  double2* gpart = nullptr;    // [groups] the group's sums of v/n and of the weights
-  int* gctr = nullptr;         // [2 groups + 1] arrival counters (zero between uses)
+  int* gctr = nullptr;         // [groups] arrival counters (zero between uses)
   long long* ncall_dev = nullptr;  // events of the allocation
   double* scal = nullptr;    // [3] sigma_k^2, the weights' sum D, 1/D
   int* tiles_used = nullptr; // the fill's tiles with events (the reduce reads no others)
@@ -527,7 +535,7 @@ struct GvPlusArgs {
 };
 
 namespace gv {
-cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl);
+cudaError_t launch_plus_finish(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_plus_layout(const GvPlusArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_fill_plus(int ig, int fp32, const GvFillArgs& a, int n_tiles, size_t smem,

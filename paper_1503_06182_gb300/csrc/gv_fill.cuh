@@ -38,6 +38,7 @@
 // chip is a small fraction of its FP32 throughput.
 #pragma once
 #include "gv_integrands.cuh"
+#include "gv_plus_stat.cuh"
 
 template <int IG>
 struct GvTraits;
@@ -272,6 +273,9 @@ struct GvPair<double> {
 //   hh   [7][nhist] u32   histogram: w^2 limbs [3], w limbs [3] (the third
 //                         signed), the tile's bin exponents (with a histogram)
 //   po   [GV_PLUS_WIN] i32 hypercube offsets relative to the tile (VEGAS+)
+//   ps   [GV_PLUS_WIN + GV_TILE/GV_PLUS_SEG] double2  the tile's segments
+//                         (VEGAS+): each window hypercube's first, then each
+//                         range's continuation of an earlier hypercube
 //   wd   [ceil(d/4)][GV_TILE] uint4  the tile's Philox words, generated before
 //                         the kernel waits for its predecessor (see below)
 __host__ __device__ inline size_t gv_align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -293,8 +297,10 @@ __host__ __device__ inline bool gv_fill_hoistable(bool forward, bool plus, int d
 // at least 2 events): the window holds their offsets and the next one.
 #define GV_PLUS_WIN (GV_TILE / 2 + 4)
 
+#define GV_PLUS_SEGS (GV_PLUS_WIN + GV_TILE / GV_PLUS_SEG)
+
 struct GvFillSmem {
-  size_t hist, jac, ew, bins, hh, po, wd, total;
+  size_t hist, jac, ew, bins, hh, po, ps, wd, total;
   __host__ __device__ GvFillSmem(int d, int N, int real_bytes, bool forward, bool bins_smem,
                                  int nhist = 0, bool plus = false, bool words = false) {
     const size_t dN = (size_t)d * N;
@@ -304,7 +310,8 @@ struct GvFillSmem {
     bins = gv_align16(ew + dN * 16);
     hh = gv_align16(bins + ((forward && bins_smem) ? (size_t)d * GV_TILE * 2 : 0));
     po = gv_align16(hh + (forward ? (size_t)nhist * 7 * 4 : 0));
-    wd = gv_align16(po + (plus ? (size_t)GV_PLUS_WIN * 4 : 0));
+    ps = gv_align16(po + (plus ? (size_t)GV_PLUS_WIN * 4 : 0));
+    wd = gv_align16(ps + (plus ? (size_t)GV_PLUS_SEGS * 16 : 0));
     total = gv_align16(wd + (words ? (size_t)((d + 3) / 4) * GV_TILE * 16 : 0));
   }
 };
@@ -327,14 +334,68 @@ __device__ __forceinline__ int gv_plus_cube(const int* s_off, int local) {
 
 // A range's segment of window hypercube j (sums s1, s2): the hypercube's
 // first segment if it begins in the range (at or after local event r0),
-// else the range's continuation of it.
+// else the range's continuation of it.  Staged in shared memory (s_seg:
+// first segments by window index, then continuations by the tile's range);
+// the segments of a hypercube that crosses a tile boundary (offsets outside
+// [0, GV_TILE]: the finishing kernel forms its statistics) go to memory too.
 __device__ __forceinline__ void gv_plus_put_segment(const GvPlusFill* pf, const int* s_off,
-                                                    long long h0, int j, long long tile0, int r0,
-                                                    double s1, double s2) {
-  if (s_off[j] >= r0)
-    pf->seg_h[h0 + j] = make_double2(s1, s2);
-  else
-    pf->seg_r[(tile0 + r0) / GV_PLUS_SEG] = make_double2(s1, s2);
+                                                    double2* s_seg, long long h0, int j,
+                                                    long long tile0, int r0, double s1,
+                                                    double s2) {
+  const double2 v = make_double2(s1, s2);
+  const bool crossing = s_off[j] < 0 || s_off[j + 1] > GV_TILE;
+  if (s_off[j] >= r0) {
+    s_seg[j] = v;
+    if (crossing) pf->seg_h[h0 + j] = v;
+  } else {
+    s_seg[GV_PLUS_WIN + r0 / GV_PLUS_SEG] = v;
+    if (crossing) pf->seg_r[(tile0 + r0) / GV_PLUS_SEG] = v;
+  }
+}
+
+// The statistics of every hypercube whose events all lie in the tile, from
+// its staged segments in range order (as the finishing kernel adds a crossing
+// hypercube's), and the tile's sums of their v/n and weights: thread t takes
+// window hypercubes t, t + B, .. in order; then warp 0's lane l adds threads
+// (B/32) l .. (B/32)(l + 1) - 1 in order, and a butterfly adds the lanes.
+// Few FP64 instructions, one chain.  Written by thread 0 to tpart[tile].
+template <int B>
+__device__ __forceinline__ void gv_plus_tile_stats(const GvPlusFill* pf, const int* s_off,
+                                                   const double2* s_seg, long long h0,
+                                                   long long tile, double2* s_red) {
+  const int tid = threadIdx.x;
+  double vn = 0.0, dd = 0.0;
+  for (int j = tid; j < GV_PLUS_WIN - 1; j += B) {
+    const int o = s_off[j], e = s_off[j + 1];
+    if (o < 0 || e > GV_TILE || h0 + j >= pf->nh) continue;  // crossing, or past the last
+    double s1 = s_seg[j].x, s2 = s_seg[j].y;
+    for (int r = o / GV_PLUS_SEG + 1; r <= (e - 1) / GV_PLUS_SEG; ++r) {
+      s1 += s_seg[GV_PLUS_WIN + r].x;
+      s2 += s_seg[GV_PLUS_WIN + r].y;
+    }
+    const GvPlusStat st = gv_plus_stat(s1, s2, e - o, pf->inv, pf->beta_j);
+    pf->var[h0 + j] = st.v;
+    pf->dw[h0 + j] = st.w;
+    vn += st.vn;
+    dd += st.w;
+  }
+  constexpr int L = B / 32;
+  s_red[tid] = make_double2(vn, dd);
+  __syncthreads();
+  if (tid < 32) {
+    double2 r = s_red[L * tid];
+#pragma unroll
+    for (int i = 1; i < L; ++i) {
+      r.x += s_red[L * tid + i].x;
+      r.y += s_red[L * tid + i].y;
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      r.x += __shfl_xor_sync(0xffffffffu, r.x, m);
+      r.y += __shfl_xor_sync(0xffffffffu, r.y, m);
+    }
+    if (tid == 0) pf->tpart[tile] = r;
+  }
 }
 
 // The base-s digits c_a of hypercube h (h < 2^22 is exact in FP32: h / s
@@ -543,6 +604,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   const GvFillSmem lay(d, N, (int)sizeof(Real), true, MAXD > 4, hb, PLUS);
   unsigned* hh = reinterpret_cast<unsigned*>(smem + lay.hh);  // [6][hb] limbs
   const int* s_off = reinterpret_cast<const int*>(smem + lay.po);
+  double2* s_seg = reinterpret_cast<double2*>(smem + lay.ps);
   const GvPlusFill* pf = a.plus;
   const long long ncall = PLUS ? *pf->ncall : a.ncall;
   const long long h0 = PLUS ? pf->tile_h0[tile] : 0;
@@ -619,7 +681,8 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
       if constexpr (PLUS) {
         while (jc + 1 < GV_PLUS_WIN && s_off[jc + 1] <= local) ++jc;
         if (jc != jcur) {  // a new hypercube: close the previous segment
-          if (jcur >= 0) gv_plus_put_segment(pf, s_off, h0, jcur, tile0, tid * EPT, sg1, sg2);
+          if (jcur >= 0)
+            gv_plus_put_segment(pf, s_off, s_seg, h0, jcur, tile0, tid * EPT, sg1, sg2);
           jcur = jc;
           sg1 = 0.0;
           sg2 = 0.0;
@@ -718,7 +781,7 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
   }
   if constexpr (PLUS) {
     // the range's last segment and its first hypercube
-    if (jcur >= 0) gv_plus_put_segment(pf, s_off, h0, jcur, tile0, tid * EPT, sg1, sg2);
+    if (jcur >= 0) gv_plus_put_segment(pf, s_off, s_seg, h0, jcur, tile0, tid * EPT, sg1, sg2);
   }
   // the tile's scale (the barrier also orders ebin)
   int E;
@@ -820,6 +883,12 @@ __device__ __forceinline__ void gv_fill_tile(const GvFillArgs& a, long long tile
         }
       }
     }
+  }
+  if constexpr (PLUS) {
+    // the hypercubes this tile holds whole (the barrier of the tile's scale
+    // ordered the staged segments)
+    __shared__ double2 s_pr[PLUS ? B : 1];
+    gv_plus_tile_stats<B>(pf, s_off, s_seg, h0, tile, s_pr);
   }
   const u128 t1 = gv_block_sum128<NW>(s1, red_128);
   const u128 t2 = gv_block_sum128<NW>(s2, red_128);

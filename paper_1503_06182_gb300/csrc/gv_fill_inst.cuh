@@ -2,9 +2,13 @@
 #pragma once
 #include "gv_fill.cuh"
 
+// Above 48 KB of shared memory a kernel must opt in; the fills' static
+// shared memory (at most ~4.2 KB: the stratified fill's per-thread sums and
+// the reduction scratch) counts toward it, so any launch within 8 KB of the
+// default opts in.
 template <typename KernelT>
 static cudaError_t gv_prepare(KernelT k, size_t smem) {
-  if (smem > 48 * 1024)
+  if (smem + 8 * 1024 > 48 * 1024)
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }

@@ -1,107 +1,39 @@
 // gv_plus.cu -- VEGAS+ (adaptive stratified sampling on the VEGAS map;
 // Lepage, J. Comput. Phys. 439 (2021) 110386, a later form of the VEGAS
 // method cited in Section 2.1) after each iteration.  The stratified fill has
-// left the sums of J g and its square over each GV_PLUS_SEG-event range's run
-// of each hypercube (its segments, in event order): a hypercube's first
-// segment at its index, a range's continuation of an earlier one at the
-// range's.
-//   stats:  one thread per hypercube adds its segments in range order, then
-//           forms its sample variance v_h, v_h/n_h and the allocation weight
-//           v_h^(beta/2) (divisions by n and n - 1 as products with tabulated
-//           reciprocals: FP64 division is a long sequence on the FP64 pipe);
-//           the CTA that completes the grid (ticket) forms
-//           sigma_k^2 = sum v_h/n_h / nh^2 and D = sum of the weights and
-//           writes sigma_k; at the stage's last iteration, of this CTA and the
-//           reduce (which runs beside these kernels) the second to arrive
-//           combines the stage;
+// formed the statistics of every hypercube whose events lie in one tile, with
+// each tile's sums of their v_h/n_h and weights, and left the segments (sums
+// of J g and its square over a range's run of a hypercube, in event order) of
+// the hypercubes that cross a tile boundary:
+//   finish: 16 CTAs add the tiles' sums in tile order and form the
+//           statistics of the crossing hypercubes (gv_plus_stat.cuh: the
+//           sample variance v_h, v_h/n_h and the allocation weight
+//           v_h^(beta/2)), then sigma_k^2 = sum v_h/n_h / nh^2 and D = sum
+//           of the weights (the last CTA to arrive adds the CTAs' sums in
+//           order), and writes sigma_k; at the stage's last
+//           iteration, of this kernel and the reduce (which runs beside it)
+//           the second to arrive combines the stage;
 //   alloc:  n_h = max(2, floor(C d_h / D)) (floor(C/nh) if D = 0 or for the
 //           uniform start), per-CTA event counts; the completing CTA scans
 //           them (exact integers);
 //   layout: the offsets of the hypercubes, (C/(nh n_h), sqrt(1/(nh n_h))) (in
 //           FP64 and rounded to FP32, for the two forms' fills) and each
 //           tile's first hypercube for the next fill.
-// Every sum over hypercubes has a shape fixed by nh alone, every count is an
-// integer, and no CTA waits for another: the last one to arrive does the rest.
+// Every sum over hypercubes has a shape fixed by the allocation alone, every
+// count is an integer, and no CTA waits for another: the last one to arrive
+// does the rest.
 #include "gv_combine.cuh"
+#include "gv_plus_stat.cuh"
 
 namespace {
 
-constexpr int kT = 256;  // threads per CTA, one hypercube each
+constexpr int kT = 256;  // threads per CTA of the allocation and layout, one hypercube each
 // 8 CTAs per SM (at most 32 registers): 1216 resident CTAs on 152 SMs hold a
 // million-event iteration's 234,256 hypercubes (916 CTAs) in one wave; at 6
 // (38 registers) its last four CTAs ran as a second wave, a whole CTA
 // lifetime later
 constexpr int kMinBlocks = 8;
 constexpr int kG = 32;  // CTAs per group of the two-level completion counters
-
-// v^(j/8) (beta = j/4) from correctly rounded operations only: v = t 2^(8q)
-// with t in [1/2, 128) rounded to FP32, three FP32 square roots, j - 1 FP32
-// products, and 2^(q j) exactly.
-// The exponent split, the FP32 rounding of t, the widening of the FP32
-// result and the final scaling are exact bit operations here (frexp, a
-// conversion to nearest, a widening and ldexp, written with integers: their
-// library and hardware forms run on the FP64 pipe, which this chip has little
-// of); a subnormal v takes the library path.
-__device__ __forceinline__ double plus_weight(double v, int j) {
-  const long long bits = __double_as_longlong(v);
-  if (j == 0) return 1.0;
-  if (bits <= 0) return 0.0;  // +0 (v is finite and not negative)
-  const int eb = (int)(bits >> 52);  // biased exponent
-  int e, q, r;
-  unsigned tb;  // FP32 bits of t = m 2^r in [1/2, 128), m in [1/2, 1)
-  if (eb == 0) {
-    const double m = frexp(v, &e);
-    q = e >= 0 ? e / 8 : -((-e + 7) / 8);
-    r = e - 8 * q;
-    tb = __float_as_uint(__double2float_rn(ldexp(m, r)));
-  } else {
-    e = eb - 1022;  // v = m 2^e
-    q = e >= 0 ? e / 8 : -((-e + 7) / 8);
-    r = e - 8 * q;
-    // round the 52-bit mantissa to 23 bits, to nearest, ties to even (a carry
-    // runs into the exponent, as it should)
-    const unsigned long long M = (unsigned long long)bits & 0x000FFFFFFFFFFFFFull;
-    tb = ((unsigned)(126 + r) << 23) | (unsigned)(M >> 29);
-    const unsigned half = (unsigned)(M >> 28) & 1u;
-    const unsigned sticky = (M & ((1ull << 28) - 1ull)) != 0ull ? 1u : 0u;
-    tb += half & (sticky | (tb & 1u));
-  }
-  const float t = __uint_as_float(tb);
-  const float y = __fsqrt_rn(__fsqrt_rn(__fsqrt_rn(t)));
-  float p = y;
-  for (int k = 1; k < j; ++k) p = __fmul_rn(p, y);
-  // (double)p 2^(q j): p is normal and so is the product (|q j| <= 540)
-  const unsigned pb = __float_as_uint(p);
-  const long long db = ((long long)(((pb >> 23) & 0xFFu) - 127 + 1023) << 52) |
-                       ((long long)(pb & 0x7FFFFFu) << 29);
-  return __longlong_as_double(db + ((long long)(q * j) << 52));
-}
-
-// Two sums over the CTA in a fixed order, with few FP64 instructions (this
-// chip's FP64 pipe is narrow) and one latency chain for both: warp 0's lane l
-// adds the values of threads 8l..8l+7 in order, then a butterfly over the
-// warp.  The result is valid in thread 0.
-__device__ __forceinline__ double2 block_sum2(double2 v, double2* s) {
-  s[threadIdx.x] = v;
-  __syncthreads();
-  double2 r = make_double2(0.0, 0.0);
-  if (threadIdx.x < 32) {
-    const double2* q = s + 8 * threadIdx.x;
-    r = q[0];
-#pragma unroll
-    for (int i = 1; i < 8; ++i) {
-      r.x += q[i].x;
-      r.y += q[i].y;
-    }
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      r.x += __shfl_xor_sync(0xffffffffu, r.x, m);
-      r.y += __shfl_xor_sync(0xffffffffu, r.y, m);
-    }
-  }
-  __syncthreads();
-  return r;
-}
 
 // Exclusive prefix sum over the CTA (integers: any order is exact).
 __device__ __forceinline__ long long block_exscan(long long v, long long* s, long long* total) {
@@ -126,42 +58,33 @@ __device__ __forceinline__ long long block_exscan(long long v, long long* s, lon
   return base + x - v;
 }
 
-// 1/n and 1/(n - 1) beyond the tables (kept out of line, so that the common
-// path does not carry two FP64 divisions)
-__device__ __noinline__ void plus_recips(double n, double* inv_n, double* inv_m1) {
-  *inv_n = 1.0 / n;
-  *inv_m1 = 1.0 / (n - 1.0);
-}
+constexpr int kFC = 16;   // CTAs of the finishing kernel
+constexpr int kTF = 256;  // their threads
 
-// Per-CTA values a completing CTA's thread holds in registers (up to kT kR
-// CTAs: all loads in flight at once; more are read in a loop).
-constexpr int kR = 4;
-
-// The completing CTA: the sums of nb per-CTA pairs in CTA order, each thread
-// taking a contiguous run, then the fixed tree.
-__device__ __forceinline__ double2 sum_parts2(const double2* part, int nb, double2* s) {
-  const int chunk = (nb + kT - 1) / kT;
-  const int i0 = threadIdx.x * chunk, i1 = min(nb, i0 + chunk);
-  double2 v = make_double2(0.0, 0.0);
-  if (chunk <= kR) {
-    double2 p[kR];
+// Two sums over a CTA of kTF threads in a fixed order, with few FP64
+// instructions (this chip's FP64 pipe is narrow) and one latency chain for
+// both: warp 0's lane l adds the values of threads 8l..8l+7 in order, then a
+// butterfly over the warp.  The result is valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* s) {
+  constexpr int L = kTF / 32;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  if (threadIdx.x < 32) {
+    const double2* q = s + L * threadIdx.x;
+    r = q[0];
 #pragma unroll
-    for (int q = 0; q < kR; ++q) p[q] = i0 + q < i1 ? __ldcg(part + i0 + q) : make_double2(0.0, 0.0);
-#pragma unroll
-    for (int q = 0; q < kR; ++q) {
-      if (i0 + q < i1) {
-        v.x += p[q].x;
-        v.y += p[q].y;
-      }
+    for (int i = 1; i < L; ++i) {
+      r.x += q[i].x;
+      r.y += q[i].y;
     }
-  } else {
-    for (int i = i0; i < i1; ++i) {
-      const double2 p = __ldcg(part + i);
-      v.x += p.x;
-      v.y += p.y;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      r.x += __shfl_xor_sync(0xffffffffu, r.x, m);
+      r.y += __shfl_xor_sync(0xffffffffu, r.y, m);
     }
   }
-  return block_sum2(v, s);
+  return r;
 }
 
 // floor(x / D) with x / D rounded to nearest, as the allocation rule states
@@ -188,75 +111,73 @@ __device__ __forceinline__ long long floor_quotient(double x, double D, double r
 
 }  // namespace
 
-__global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_stats_kernel(const GvPlusArgs a) {
-  __shared__ double2 s_red[kT];
+__global__ void __launch_bounds__(kTF) gv_plus_finish_kernel(const GvPlusArgs a) {
+  __shared__ double2 s_red[kTF];
   __shared__ int s_last;
-  gv_wait_prior_grid();  // the fill's segments and the reduce's I_k
-  const long long h = (long long)blockIdx.x * kT + threadIdx.x;
-  double vn = 0.0, dd = 0.0;
-  if (h < a.nh) {
-    const long long o = a.off[h];
-    const int m = a.n[h];
-    // the hypercube's segments in event order: its first, then the
-    // continuations of every later range it reaches
-    double2 sg = a.seg_h[h];
-    const long long r0 = o / GV_PLUS_SEG, r1 = (o + m - 1) / GV_PLUS_SEG;
-    double s1 = sg.x, s2 = sg.y;
-    for (long long r = r0 + 1; r <= r1; ++r) {
-      sg = a.seg_r[r];
-      s1 += sg.x;
-      s2 += sg.y;
-    }
-    const double nd = (double)m;
-    double inv_n, inv_m1;
-    if (m < GV_PLUS_NTAB) {
-      inv_n = __ldg(a.inv + m);
-      inv_m1 = __ldg(a.inv + m - 1);
-    } else {
-      plus_recips(nd, &inv_n, &inv_m1);
-    }
-    double v = (s2 - s1 * s1 * inv_n) * inv_m1;
-    v = __double_as_longlong(v) > 0ll ? v : 0.0;  // negative (rounding) or -0 -> 0
-    a.var[h] = v;
-    vn = v * inv_n;
-    dd = plus_weight(v, a.beta_j);
-    a.dw[h] = dd;
-  }
+  gv_wait_prior_grid();  // the fill's tile sums and crossing segments
   gv_allow_next_grid();
+  const long long T = (__ldcg(a.ncall_dev) + GV_TILE - 1) / GV_TILE;  // tiles with events
+  // CTA c takes the c-th of kFC equal runs of the tiles and of the
+  // boundaries, and each of its threads a contiguous run of those
+  const long long c = blockIdx.x, t = threadIdx.x;
+  double vn = 0.0, dd = 0.0;
+  // the tiles' sums, in tile order
+  {
+    const long long run = (T + kFC - 1) / kFC, lo = min(T, c * run), hi = min(T, lo + run);
+    const long long per = (run + kTF - 1) / kTF;
+    const long long b0 = min(hi, lo + t * per), b1 = min(hi, b0 + per);
+    for (long long q = b0; q < b1; ++q) {
+      const double2 p = __ldcg(a.tpart + q);
+      vn += p.x;
+      dd += p.y;
+    }
+  }
+  // the hypercubes that cross a tile boundary, each at the first boundary b
+  // (between tiles b - 1 and b, 1 <= b < T) it crosses: the one holding tile
+  // b's first event when it began in tile b - 1.  Its segments in event
+  // order: its first, then the continuations of every later range it reaches.
+  {
+    const long long run = (T - 1 + kFC - 1) / kFC;
+    const long long lo = min(T, 1 + c * run), hi = min(T, lo + run);
+    const long long per = (run + kTF - 1) / kTF;
+    const long long b0 = min(hi, lo + t * per), b1 = min(hi, b0 + per);
+    for (long long b = b0; b < b1; ++b) {
+      const long long h = __ldcg(a.tile_h0 + b);
+      const long long o = __ldcg(a.off + h);
+      if (o >= b * GV_TILE || o < (b - 1) * GV_TILE) continue;
+      const long long e = __ldcg(a.off + h + 1);
+      double2 sg = __ldcg(a.seg_h + h);
+      double s1 = sg.x, s2 = sg.y;
+      for (long long r = o / GV_PLUS_SEG + 1; r <= (e - 1) / GV_PLUS_SEG; ++r) {
+        sg = __ldcg(a.seg_r + r);
+        s1 += sg.x;
+        s2 += sg.y;
+      }
+      const GvPlusStat st = gv_plus_stat(s1, s2, (int)(e - o), a.inv, a.beta_j);
+      a.var[h] = st.v;
+      a.dw[h] = st.w;
+      vn += st.vn;
+      dd += st.w;
+    }
+  }
   const double2 sums = block_sum2(make_double2(vn, dd), s_red);
-  // two-level completion: the last CTA of each group of kG adds the group's
-  // sums (in CTA order, a fixed tree); the last group adds the groups'
-  const int b = blockIdx.x, nb = gridDim.x;
-  const int g = b / kG, ng = (nb + kG - 1) / kG, gsize = min(kG, nb - g * kG);
+  // the last CTA to arrive adds the CTAs' sums in CTA order
   if (threadIdx.x == 0) {
-    reinterpret_cast<double2*>(a.part)[b] = sums;
+    a.fpart[c] = sums;
     __threadfence();
-    s_last = atomicAdd(a.gctr + g, 1) == gsize - 1;
+    s_last = atomicAdd(a.fctr, 1) == kFC - 1;
   }
   __syncthreads();
   if (!s_last) return;
-  if (threadIdx.x < 32) {
-    __threadfence();  // the group's sums, published before their arrivals
-    double2 v = threadIdx.x < gsize ? __ldcg(reinterpret_cast<const double2*>(a.part) + g * kG + threadIdx.x)
-                                    : make_double2(0.0, 0.0);
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
-      v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
-    }
-    if (threadIdx.x == 0) {
-      a.gpart[g] = v;
-      a.gctr[g] = 0;
-      __threadfence();
-      s_last = atomicAdd(a.gctr + ng, 1) == ng - 1;
-    }
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();  // the groups' sums, published before their arrivals
-  const double2 VD = sum_parts2(a.gpart, ng, s_red);
   if (threadIdx.x == 0) {
-    a.gctr[ng] = 0;
+    __threadfence();  // the CTAs' sums, published before their arrivals
+    *a.fctr = 0;
+    double2 VD = __ldcg(a.fpart);
+    for (int q = 1; q < kFC; ++q) {
+      const double2 p = __ldcg(a.fpart + q);
+      VD.x += p.x;
+      VD.y += p.y;
+    }
     const double var_k = VD.x * a.inv_nh2;
     const double D = VD.y;
     a.scal[0] = var_k;
@@ -343,7 +264,7 @@ __global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_alloc_kernel(const GvP
   long long tot;
   block_exscan(m, s_scan, &tot);
   const int g = b / kG, gsize = min(kG, nb - g * kG);
-  int* ctr = a.gctr + ((nb + kG - 1) / kG) + 1 + g;
+  int* ctr = a.gctr + g;
   if (threadIdx.x == 0) {
     a.npart[b] = tot;
     __threadfence();
@@ -387,9 +308,8 @@ __global__ void __launch_bounds__(kT, kMinBlocks) gv_plus_layout_kernel(const Gv
 
 namespace gv {
 
-cudaError_t launch_plus_stats(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
-  const unsigned nb = (unsigned)((a.nh + kT - 1) / kT);
-  return gv_launch_prio(gv_plus_stats_kernel, dim3(nb), dim3(kT), 0, s, pdl, a.prio, a);
+cudaError_t launch_plus_finish(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
+  return gv_launch_prio(gv_plus_finish_kernel, dim3(kFC), dim3(kTF), 0, s, pdl, a.prio, a);
 }
 
 cudaError_t launch_plus_alloc(const GvPlusArgs& a, cudaStream_t s, bool pdl) {
