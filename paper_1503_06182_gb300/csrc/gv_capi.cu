@@ -801,13 +801,24 @@ int enqueue_body(vegas_ctx* c, const Plan& p, std::vector<cudaEvent_t>* ev, bool
       GV_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     }
     if (ev) GV_TRY(cudaEventRecordWithFlags((*ev)[3 * k + 1], c->stream, flags));
+    // the previous iteration's histogram estimates, beside this fill, have
+    // read the bin sums this reduce overwrites
+    if (p.nhist && k > 0) GV_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     // (VEGAS+: a plain launch, so that its CTAs do not hold the SMs while
     // they wait for the fill; the more urgent kernels beside it go first)
     if (p.slot_major)
       GV_TRY(gv::launch_reduce_slots(reduce_args(c, p, k), rsmem, c->stream, pdl && !p.plus));
     else
       GV_TRY(gv::launch_reduce(reduce_args(c, p, k), rsmem, c->stream, pdl));
-    if (p.nhist) GV_TRY(gv::launch_hist(hist_args(c, p, k), c->stream, pdl));
+    if (p.nhist) {
+      // the histogram's estimates on the side stream: the next fill reads
+      // nothing they touch, so it follows the reduce alone
+      GV_TRY(cudaEventRecord(c->ev_fork, c->stream));
+      GV_TRY(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+      GV_TRY(gv::launch_hist(hist_args(c, p, k), c->side, false));
+      GV_TRY(cudaEventRecord(c->ev_join, c->side));
+      if (k == p.itmx - 1) GV_TRY(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    }
     if (p.plus) {
       // beside the reduce: the statistics' completion from the fill's tile
       // sums and crossing hypercubes (sigma_k; the stage's combination with
@@ -869,6 +880,8 @@ int enqueue_stage(vegas_ctx* c, int64_t ncall, int itmx, int ig, const double* p
   if (p.plus) {
     st = ensure_allocation(c, p);
     if (st) return st;
+  }
+  if (p.plus || p.nhist) {
     st = ensure_side(c);
     if (st) return st;
   }
