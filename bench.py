@@ -64,12 +64,12 @@ SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # binding roofline.  Valid while the fill's sources are the ones captured
 # (their SHA-256 below) and only for the shape the timed run used; otherwise
 # both are reported as unknown (null).
-FILL_CAPTURES = {4: {"traffic_bytes": 82_432, "warp_instructions": 21_418_973},
-                 8: {"traffic_bytes": 121_856, "warp_instructions": 19_412_189}}
+FILL_CAPTURES = {4: {"traffic_bytes": 83_456, "warp_instructions": 21_418_973},
+                 8: {"traffic_bytes": 121_600, "warp_instructions": 19_412_189}}
 SMSP_PER_SM = 4
 FILL_SOURCES = ("gv_fill.cuh", "gv_fill_inst.cuh", "gv_fill_dy_f32.cu", "gv_integrands.cuh",
                 "gv_common.cuh")
-FILL_SOURCES_SHA256 = "5d8d68412efd1b6772c54ed7ceea6de21a382757cd43fd50cfc894321037ceaf"
+FILL_SOURCES_SHA256 = "b6e6780f442ab04756baca4c51db64638d12551e4734af9a48e958c1e9bed140"
 # HBM copy bandwidth measured by the driver on the GB300s (used when
 # MEASURED_PEAKS.json is absent: the profiling recipe's fallback)
 HBM_FALLBACK_GBS = 6800.0
