@@ -185,6 +185,34 @@ def test_plus_strat_set_and_validation():
         g.close()
 
 
+def test_plus_hypercube_across_several_tiles():
+    """One hypercube of 2500 events spans four fill tiles (1024 events each),
+    beside many 2- and 3-event ones of which some straddle a tile boundary.
+    A tile forms the statistics of the hypercubes it holds whole; the others
+    come from their segments in every tile they reach, formed once, at the
+    first boundary they cross.  sigma_k and the variances agree with the
+    oracle on the same allocation, and the next allocation is the rule
+    applied to the GPU's variances, exactly."""
+    s = oracle.plus_nstrat(2, 4000)
+    nh = s * s
+    counts = np.full(nh, 2, np.int32)
+    counts[::97] += 1
+    counts[300] = 2500
+    assert counts.sum() <= 4000 + 2 * nh and counts[:300].sum() < 1024 < counts[:301].sum() - 2048
+    g = v.Vegas(2, 20, 3)
+    try:
+        g.strat_set(4000, counts)
+        g.set(v.VEGAS_OPT_STRAT, 1)
+        I, e, c, per, _ = g.iterate(4000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS)
+        ref = oracle.iterate_plus(2, 20, 3, 4000, 1, v.VEGAS_GAUSS, GAUSS_PARAMS, alloc=counts)
+        per_agrees(per, ref, counts)
+        _, alloc2, var = g.strat()
+        var_agrees(var, ref, counts)
+        assert np.array_equal(alloc2, oracle.plus_allocate(4000, var))
+    finally:
+        g.close()
+
+
 def test_plus_reduces_the_variance_on_the_gpu():
     iid, params, ndim, nbins = CASES["gauss_d2"]
     errs = []
